@@ -1,0 +1,286 @@
+"""FP64 CPU oracle (ctypes binding of cbct_oracle.c) -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+may import this package.  The product library (``paper_1002_3675_b300``) never does;
+the oracle and the CUDA path share no code.
+
+Arrays are float64 NumPy: volumes [nz][ny][nx], projection stacks [na][nv][nu].  A
+geometry is the plain dict produced by ``synth.geometry_for``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cbct_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no fast-math, OpenMP) if needed."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared",
+                               _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Geom(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("hx", C.c_double), ("hy", C.c_double), ("hz", C.c_double),
+                ("nu", C.c_int), ("nv", C.c_int), ("du", C.c_double), ("dv", C.c_double),
+                ("dso", C.c_double), ("dsd", C.c_double),
+                ("na", C.c_int), ("angles", C.POINTER(C.c_double))]
+
+
+class _Vol(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("hx", C.c_double), ("hy", C.c_double), ("hz", C.c_double)]
+
+
+_lib = None
+_D = C.POINTER(C.c_double)
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(build())
+        G, V = C.POINTER(_Geom), C.POINTER(_Vol)
+        sig = {
+            "or_project": (None, [G, _D, _D]),
+            "or_backproject": (None, [G, _D, _D]),
+            "or_backproject_voxel": (C.c_double, [G, _D, C.c_int, C.c_int, C.c_int]),
+            "or_project_ray": (C.c_double, [G, _D, C.c_int, C.c_int, C.c_int]),
+            "or_ray_segments": (C.c_int, [G, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_long), _D, C.c_int]),
+            "or_ray_voxel_length": (C.c_double, [G] + [C.c_int] * 6),
+            "or_count_nnz": (C.c_longlong, [G]),
+            "or_tv": (C.c_double, [V, _D, C.c_double]),
+            "or_tv_grad": (None, [V, _D, C.c_double, _D]),
+            "or_tv_lipschitz": (C.c_double, [V, C.c_double]),
+            "or_prox": (None, [V, _D, _D, C.c_double, C.c_double, C.c_int, C.c_int, C.c_double, _D]),
+            "or_gamma": (C.c_double, [G, C.c_double]),
+            "or_default_eps": (C.c_double, [G]),
+            "or_energy": (None, [G, _D, _D, C.c_double, C.c_double, _D, _D]),
+            "or_power_iteration": (C.c_double, [G, C.c_int]),
+            "or_auto_beta": (C.c_double, [G, C.c_double, C.c_int]),
+            "or_fbs": (None, [G, _D, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
+                              C.c_double, C.c_int, _D, _D]),
+            "or_restrict_sino": (None, [C.c_int, C.c_int, C.c_int, _D, _D]),
+            "or_prolong_vol": (None, [C.c_int, C.c_int, C.c_int, _D, C.c_int, C.c_int, C.c_int, _D]),
+            "or_level_geom": (None, [G, C.c_int, G]),
+            "or_reconstruct": (None, [G, _D, C.c_double, C.c_int, C.c_int, _D, C.c_double, C.c_int,
+                                      C.c_int, C.c_int, _D, _D]),
+            "or_num_threads": (C.c_int, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_D) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class _GeomHolder:
+    """Keeps the angle array alive while the C struct points into it."""
+
+    def __init__(self, geom: dict):
+        self.angles = _f64(geom["angles"])
+        self.s = _Geom(geom["nx"], geom["ny"], geom["nz"], geom["hx"], geom["hy"], geom["hz"],
+                       geom["nu"], geom["nv"], geom["du"], geom["dv"], geom["dso"], geom["dsd"],
+                       len(self.angles), _ptr(self.angles))
+
+
+def _g(geom):
+    return _GeomHolder(geom)
+
+
+def _vol(shape, h):
+    nz, ny, nx = shape
+    return _Vol(nx, ny, nz, float(h[0]), float(h[1]), float(h[2]))
+
+
+def vol_shape(geom):
+    return (geom["nz"], geom["ny"], geom["nx"])
+
+
+def sino_shape(geom):
+    return (len(geom["angles"]), geom["nv"], geom["nu"])
+
+
+def spacing(geom):
+    return (geom["hx"], geom["hy"], geom["hz"])
+
+
+def num_threads() -> int:
+    return _load().or_num_threads()
+
+
+# --- projector and adjoint (problem statement, Eq. 1; transpose before Eq. 2) --------
+
+def project(geom, f):
+    f = _f64(f)
+    y = np.empty(sino_shape(geom))
+    h = _g(geom)
+    _load().or_project(C.byref(h.s), _ptr(f), _ptr(y))
+    return y
+
+
+def backproject(geom, y):
+    y = _f64(y)
+    f = np.empty(vol_shape(geom))
+    h = _g(geom)
+    _load().or_backproject(C.byref(h.s), _ptr(y), _ptr(f))
+    return f
+
+
+def backproject_voxel(geom, y, i, j, k):
+    y = _f64(y)
+    h = _g(geom)
+    return _load().or_backproject_voxel(C.byref(h.s), _ptr(y), i, j, k)
+
+
+def project_ray(geom, f, ia, b, a):
+    f = _f64(f)
+    h = _g(geom)
+    return _load().or_project_ray(C.byref(h.s), _ptr(f), ia, b, a)
+
+
+def ray_segments(geom, ia, b, a):
+    cap = geom["nx"] + geom["ny"] + geom["nz"] + 8
+    idx = np.empty(cap, dtype=np.int64)
+    ln = np.empty(cap)
+    h = _g(geom)
+    m = _load().or_ray_segments(C.byref(h.s), ia, b, a, idx.ctypes.data_as(C.POINTER(C.c_long)), _ptr(ln), cap)
+    return idx[:m].copy(), ln[:m].copy()
+
+
+def ray_voxel_length(geom, ia, b, a, i, j, k):
+    h = _g(geom)
+    return _load().or_ray_voxel_length(C.byref(h.s), ia, b, a, i, j, k)
+
+
+def count_nnz(geom) -> int:
+    h = _g(geom)
+    return int(_load().or_count_nnz(C.byref(h.s)))
+
+
+# --- TV (E1) and the step-2 prox ------------------------------------------------------
+
+def tv(f, h, eps):
+    f = _f64(f)
+    v = _vol(f.shape, h)
+    return _load().or_tv(C.byref(v), _ptr(f), eps)
+
+
+def tv_grad(f, h, eps):
+    f = _f64(f)
+    out = np.empty_like(f)
+    v = _vol(f.shape, h)
+    _load().or_tv_grad(C.byref(v), _ptr(f), eps, _ptr(out))
+    return out
+
+
+def tv_lipschitz(h, eps):
+    v = _vol((1, 1, 1), h)
+    return _load().or_tv_lipschitz(C.byref(v), eps)
+
+
+def prox(g, f0, h, beta, eps, M, clamp_mode=0, tv_weight=1.0, return_phi=False):
+    g = _f64(g)
+    f = _f64(f0).copy() if f0 is not None else np.zeros_like(g)
+    phi = np.empty(M + 1) if return_phi else None
+    v = _vol(g.shape, h)
+    _load().or_prox(C.byref(v), _ptr(g), _ptr(f), beta, eps, M, clamp_mode, tv_weight, _ptr(phi))
+    return (f, phi) if return_phi else f
+
+
+# --- energy, step size, Algorithm A1, multigrid ---------------------------------------
+
+def gamma(geom, mu):
+    h = _g(geom)
+    return _load().or_gamma(C.byref(h.s), mu)
+
+
+def default_eps(geom):
+    h = _g(geom)
+    return _load().or_default_eps(C.byref(h.s))
+
+
+def energy(geom, Y, f, mu, eps, return_residual=False):
+    Y, f = _f64(Y), _f64(f)
+    out = np.empty(3)
+    r = np.empty(sino_shape(geom)) if return_residual else None
+    h = _g(geom)
+    _load().or_energy(C.byref(h.s), _ptr(Y), _ptr(f), mu, eps, _ptr(out), _ptr(r))
+    return (out, r) if return_residual else out
+
+
+def power_iteration(geom, K=30):
+    h = _g(geom)
+    return _load().or_power_iteration(C.byref(h.s), K)
+
+
+def auto_beta(geom, mu, K=30):
+    h = _g(geom)
+    return _load().or_auto_beta(C.byref(h.s), mu, K)
+
+
+def fbs(geom, Y, mu, beta, eps, M, iters, f0=None, clamp_mode=0, tv_weight=1.0):
+    Y = _f64(Y)
+    f = _f64(f0).copy() if f0 is not None else np.zeros(vol_shape(geom))
+    trace = np.empty((iters, 3))
+    h = _g(geom)
+    _load().or_fbs(C.byref(h.s), _ptr(Y), mu, beta, eps, M, clamp_mode, tv_weight, iters, _ptr(f), _ptr(trace))
+    return f, trace
+
+
+def restrict_sino(y):
+    y = _f64(y)
+    na, nv, nu = y.shape
+    out = np.empty((na, (nv + 1) // 2, (nu + 1) // 2))
+    _load().or_restrict_sino(na, nv, nu, _ptr(y), _ptr(out))
+    return out
+
+
+def prolong_vol(fc, shape):
+    fc = _f64(fc)
+    nzc, nyc, nxc = fc.shape
+    nz, ny, nx = shape
+    out = np.empty(shape)
+    _load().or_prolong_vol(nxc, nyc, nzc, _ptr(fc), nx, ny, nz, _ptr(out))
+    return out
+
+
+def level_geom(geom, level):
+    h = _g(geom)
+    out = _Geom()
+    _load().or_level_geom(C.byref(h.s), level, C.byref(out))
+    g2 = dict(geom)
+    for k in ("nx", "ny", "nz", "hx", "hy", "hz", "nu", "nv", "du", "dv"):
+        g2[k] = getattr(out, k)
+    return g2
+
+
+def reconstruct(geom, Y, mu, iters, levels, betas=None, eps=0.0, M=10, clamp_mode=0, K_pi=30):
+    Y = _f64(Y)
+    f = np.empty(vol_shape(geom))
+    trace = np.empty((levels, iters, 3))
+    b = _f64(betas) if betas is not None else None
+    h = _g(geom)
+    _load().or_reconstruct(C.byref(h.s), _ptr(Y), mu, iters, levels, _ptr(b), eps, M, clamp_mode,
+                           K_pi, _ptr(f), _ptr(trace))
+    return f, trace

@@ -1,0 +1,696 @@
+/*
+ * FP64 CPU oracle for TV-regularised cone-beam CT reconstruction by forward-backward
+ * splitting (Jia, Lou, Li, Song, Jiang, "GPU-based fast cone beam CT reconstruction
+ * from undersampled and noisy projection data via total variation", 2010).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plainly written reference that
+ * the CUDA path is checked against.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load it; the product library never does, and it
+ * shares no code, header or table with the CUDA sources.
+ *
+ * Everything is double precision.  Readings of points the paper leaves open:
+ *   - geometry: circular orbit about z, source (dso cos t, dso sin t, 0), flat imager
+ *     at distance dsd from the source, one ray per pixel centre; the volume is centred
+ *     on the origin, voxels are half-open boxes.  Volumes are [nz][ny][nx], projection
+ *     stacks [na][nv][nu].
+ *   - P^theta (problem statement before Eq. 1) is the exact intersection-length
+ *     projector: (Pf)_ray = sum_j |ray ∩ box_j| f_j, computed by merging the ray's
+ *     plane crossings (Siddon's parametric method).
+ *   - the adjoint used in step 1 of Algorithm A1 is the exact matrix transpose named
+ *     in the paragraph before Eq. 2; here it is a scatter over the same crossings.
+ *   - E1 (Eq. 1) is the isotropic TV with forward differences, Neumann boundary,
+ *     smoothed as sqrt(|grad f|^2 + eps^2).
+ *   - step 2 of Algorithm A1 ("simple gradient descent") is projected gradient on
+ *     TV_eps(f) + beta/2 |f - g|^2 over f >= 0 from f0 = f_k, step 1/(beta + L_TV),
+ *     L_TV = (4/eps) sum_d h_d^-2; clamp_mode 1 instead descends from g without the
+ *     bound and clamps afterwards (step 3 taken literally).
+ *   - discrete scaling: Nv E = TV_eps + (gamma/2)|Pf - Y|^2, gamma = 2 mu Nv/(na Np);
+ *     step 1 becomes g = f - (gamma/beta) P^T (Pf - Y).
+ *   - multigrid (cited method [20]): coarse-to-fine cascade; 2x2 detector binning,
+ *     cell-centred trilinear prolongation with edge replication.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    int nx, ny, nz;
+    double hx, hy, hz;
+    int nu, nv;
+    double du, dv;
+    double dso, dsd;
+    int na;
+    const double *angles;
+} or_geom;
+
+/* ------------------------------------------------------------------------------ */
+/* Rays                                                                            */
+/* ------------------------------------------------------------------------------ */
+
+/* Source and pixel-centre position of ray (ia, b, a). */
+static void ray_endpoints(const or_geom *g, int ia, int b, int a, double S[3], double P[3])
+{
+    double c = cos(g->angles[ia]), s = sin(g->angles[ia]);
+    double ua = (a - 0.5 * (g->nu - 1)) * g->du;
+    double vb = (b - 0.5 * (g->nv - 1)) * g->dv;
+    S[0] = g->dso * c;
+    S[1] = g->dso * s;
+    S[2] = 0.0;
+    P[0] = S[0] - g->dsd * c - ua * s;
+    P[1] = S[1] - g->dsd * s + ua * c;
+    P[2] = vb;
+}
+
+/*
+ * Siddon enumeration: every voxel the segment S->P crosses, with its intersection
+ * length in mm.  Writes at most cap entries; returns the count.
+ */
+static int ray_segments(const or_geom *g, const double S[3], const double P[3],
+                        long *idx, double *len, int cap, double *scratch)
+{
+    const int n[3] = {g->nx, g->ny, g->nz};
+    const double h[3] = {g->hx, g->hy, g->hz};
+    double lo[3], d[3];
+    double amin = 0.0, amax = 1.0;
+    for (int ax = 0; ax < 3; ++ax) {
+        lo[ax] = -0.5 * n[ax] * h[ax];
+        d[ax] = P[ax] - S[ax];
+        double hi = lo[ax] + n[ax] * h[ax];
+        if (d[ax] != 0.0) {
+            double a1 = (lo[ax] - S[ax]) / d[ax], a2 = (hi - S[ax]) / d[ax];
+            double e = a1 < a2 ? a1 : a2, x = a1 < a2 ? a2 : a1;
+            if (e > amin) amin = e;
+            if (x < amax) amax = x;
+        } else if (S[ax] < lo[ax] || S[ax] >= hi) {
+            return 0;  /* parallel to this axis' planes and outside the half-open slab */
+        }
+    }
+    if (!(amax > amin)) return 0;
+    double dlen = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+
+    /*
+     * Plane crossings strictly inside (amin, amax), one increasing list per axis, and
+     * the number of each axis' planes already crossed at amin.  A segment's voxel index
+     * along an axis is fixed by how many of that axis' planes the ray has crossed, so
+     * it follows from the same crossing values that delimit the segments.
+     */
+    int cnt[3] = {0, 0, 0}, before[3] = {0, 0, 0};
+    double *lists[3] = {scratch, scratch + n[0] + 1, scratch + n[0] + n[1] + 2};
+    long fixed[3] = {0, 0, 0};
+    for (int ax = 0; ax < 3; ++ax) {
+        if (d[ax] == 0.0) {
+            fixed[ax] = (long)floor((S[ax] - lo[ax]) / h[ax]);
+            continue;
+        }
+        for (int q = 0; q <= n[ax]; ++q) {
+            int p = d[ax] > 0 ? q : n[ax] - q;  /* visit planes in increasing alpha */
+            double al = (lo[ax] + p * h[ax] - S[ax]) / d[ax];
+            if (al <= amin) before[ax]++;
+            else if (al < amax) lists[ax][cnt[ax]++] = al;
+        }
+    }
+    /* Merge the three sorted lists between amin and amax. */
+    int pos[3] = {0, 0, 0};
+    double prev = amin;
+    int out = 0;
+    for (;;) {
+        double next = amax;
+        int which = -1;
+        for (int ax = 0; ax < 3; ++ax)
+            if (pos[ax] < cnt[ax] && lists[ax][pos[ax]] < next) {
+                next = lists[ax][pos[ax]];
+                which = ax;
+            }
+        if (next > prev) {
+            long ijk[3];
+            for (int ax = 0; ax < 3; ++ax) {
+                long crossed = before[ax] + pos[ax];
+                long v = d[ax] == 0.0 ? fixed[ax] : (d[ax] > 0 ? crossed - 1 : n[ax] - crossed);
+                if (v < 0) v = 0;
+                if (v > n[ax] - 1) v = n[ax] - 1;
+                ijk[ax] = v;
+            }
+            if (out < cap) {
+                idx[out] = (ijk[2] * g->ny + ijk[1]) * (long)g->nx + ijk[0];
+                len[out] = (next - prev) * dlen;
+                ++out;
+            }
+        }
+        if (which < 0) break;
+        pos[which]++;
+        prev = next;
+    }
+    return out;
+}
+
+static int seg_cap(const or_geom *g) { return g->nx + g->ny + g->nz + 8; }
+
+int or_ray_segments(const or_geom *g, int ia, int b, int a, long *idx, double *len, int cap)
+{
+    double S[3], P[3];
+    double *scr = (double *)malloc(sizeof(double) * seg_cap(g));
+    ray_endpoints(g, ia, b, a, S, P);
+    int m = ray_segments(g, S, P, idx, len, cap, scr);
+    free(scr);
+    return m;
+}
+
+/* Forward projection: y[ia][b][a] = sum over crossed voxels of length * f. */
+void or_project(const or_geom *g, const double *f, double *y)
+{
+    const long nrays = (long)g->na * g->nv * g->nu;
+#pragma omp parallel
+    {
+        int cap = seg_cap(g);
+        long *idx = (long *)malloc(sizeof(long) * cap);
+        double *len = (double *)malloc(sizeof(double) * 2 * cap);
+        double *scr = len + cap;
+#pragma omp for schedule(dynamic, 64)
+        for (long r = 0; r < nrays; ++r) {
+            int a = (int)(r % g->nu), b = (int)((r / g->nu) % g->nv), ia = (int)(r / ((long)g->nu * g->nv));
+            double S[3], P[3];
+            ray_endpoints(g, ia, b, a, S, P);
+            int m = ray_segments(g, S, P, idx, len, cap, scr);
+            double acc = 0.0;
+            for (int t = 0; t < m; ++t) acc += len[t] * f[idx[t]];
+            y[r] = acc;
+        }
+        free(idx);
+        free(len);
+    }
+}
+
+double or_project_ray(const or_geom *g, const double *f, int ia, int b, int a)
+{
+    int cap = seg_cap(g);
+    long *idx = (long *)malloc(sizeof(long) * cap);
+    double *len = (double *)malloc(sizeof(double) * 2 * cap);
+    double *scr = len + cap;
+    double S[3], P[3];
+    ray_endpoints(g, ia, b, a, S, P);
+    int m = ray_segments(g, S, P, idx, len, cap, scr);
+    double acc = 0.0;
+    for (int t = 0; t < m; ++t) acc += len[t] * f[idx[t]];
+    free(idx);
+    free(len);
+    return acc;
+}
+
+/* Number of (ray, voxel) pairs with positive intersection length. */
+long long or_count_nnz(const or_geom *g)
+{
+    const long nrays = (long)g->na * g->nv * g->nu;
+    long long total = 0;
+#pragma omp parallel reduction(+ : total)
+    {
+        int cap = seg_cap(g);
+        long *idx = (long *)malloc(sizeof(long) * cap);
+        double *len = (double *)malloc(sizeof(double) * 2 * cap);
+        double *scr = len + cap;
+#pragma omp for schedule(dynamic, 64)
+        for (long r = 0; r < nrays; ++r) {
+            int a = (int)(r % g->nu), b = (int)((r / g->nu) % g->nv), ia = (int)(r / ((long)g->nu * g->nv));
+            double S[3], P[3];
+            ray_endpoints(g, ia, b, a, S, P);
+            total += ray_segments(g, S, P, idx, len, cap, scr);
+        }
+        free(idx);
+        free(len);
+    }
+    return total;
+}
+
+/*
+ * Adjoint (exact transpose of or_project): f[j] = sum over rays of length * y[ray].
+ * Scatter over the same crossings; angles are split over private accumulators that
+ * are summed in a fixed order.
+ */
+void or_backproject(const or_geom *g, const double *y, double *f)
+{
+    const long nv = (long)g->nx * g->ny * g->nz;
+    int nbuf = 1;
+#ifdef _OPENMP
+    nbuf = omp_get_max_threads();
+#endif
+    if (nbuf > g->na) nbuf = g->na;
+    long maxbuf = (long)(4.0e9 / (8.0 * (double)nv));
+    if (maxbuf < 1) maxbuf = 1;
+    if (nbuf > maxbuf) nbuf = (int)maxbuf;
+    double *acc = (double *)calloc((size_t)nbuf * nv, sizeof(double));
+#pragma omp parallel for schedule(static, 1) num_threads(nbuf)
+    for (int bi = 0; bi < nbuf; ++bi) {
+        int cap = seg_cap(g);
+        long *idx = (long *)malloc(sizeof(long) * cap);
+        double *len = (double *)malloc(sizeof(double) * 2 * cap);
+        double *scr = len + cap;
+        double *mine = acc + (size_t)bi * nv;
+        for (int ia = bi; ia < g->na; ia += nbuf)
+            for (int b = 0; b < g->nv; ++b)
+                for (int a = 0; a < g->nu; ++a) {
+                    double S[3], P[3];
+                    ray_endpoints(g, ia, b, a, S, P);
+                    int m = ray_segments(g, S, P, idx, len, cap, scr);
+                    double val = y[((long)ia * g->nv + b) * g->nu + a];
+                    for (int t = 0; t < m; ++t) mine[idx[t]] += len[t] * val;
+                }
+        free(idx);
+        free(len);
+    }
+#pragma omp parallel for schedule(static)
+    for (long j = 0; j < nv; ++j) {
+        double s = 0.0;
+        for (int bi = 0; bi < nbuf; ++bi) s += acc[(size_t)bi * nv + j];
+        f[j] = s;
+    }
+    free(acc);
+}
+
+/*
+ * Length of the segment S->P inside the half-open box [lo, hi): the slab method,
+ * written independently of the Siddon enumeration above.
+ */
+static double box_length(const double S[3], const double P[3], const double lo[3], const double hi[3])
+{
+    double t0 = 0.0, t1 = 1.0, d2 = 0.0;
+    for (int ax = 0; ax < 3; ++ax) {
+        double d = P[ax] - S[ax];
+        d2 += d * d;
+        if (d == 0.0) {
+            if (S[ax] < lo[ax] || S[ax] >= hi[ax]) return 0.0;
+            continue;
+        }
+        double a = (lo[ax] - S[ax]) / d, b = (hi[ax] - S[ax]) / d;
+        if (a > b) { double t = a; a = b; b = t; }
+        if (a > t0) t0 = a;
+        if (b < t1) t1 = b;
+    }
+    return t1 > t0 ? (t1 - t0) * sqrt(d2) : 0.0;
+}
+
+/* One voxel of the adjoint by brute force over every ray (slab test per ray). */
+double or_backproject_voxel(const or_geom *g, const double *y, int i, int j, int k)
+{
+    double lo[3] = {(-0.5 * g->nx + i) * g->hx, (-0.5 * g->ny + j) * g->hy, (-0.5 * g->nz + k) * g->hz};
+    double hi[3] = {lo[0] + g->hx, lo[1] + g->hy, lo[2] + g->hz};
+    double total = 0.0;
+#pragma omp parallel for reduction(+ : total) schedule(static)
+    for (int ia = 0; ia < g->na; ++ia)
+        for (int b = 0; b < g->nv; ++b)
+            for (int a = 0; a < g->nu; ++a) {
+                double S[3], P[3];
+                ray_endpoints(g, ia, b, a, S, P);
+                double L = box_length(S, P, lo, hi);
+                if (L > 0.0) total += L * y[((long)ia * g->nv + b) * g->nu + a];
+            }
+    return total;
+}
+
+/* Length of ray (ia, b, a) inside voxel (i, j, k), by the slab method. */
+double or_ray_voxel_length(const or_geom *g, int ia, int b, int a, int i, int j, int k)
+{
+    double lo[3] = {(-0.5 * g->nx + i) * g->hx, (-0.5 * g->ny + j) * g->hy, (-0.5 * g->nz + k) * g->hz};
+    double hi[3] = {lo[0] + g->hx, lo[1] + g->hy, lo[2] + g->hz};
+    double S[3], P[3];
+    ray_endpoints(g, ia, b, a, S, P);
+    return box_length(S, P, lo, hi);
+}
+
+/* ------------------------------------------------------------------------------ */
+/* Total variation (E1 of Eq. 1)                                                   */
+/* ------------------------------------------------------------------------------ */
+
+typedef struct {
+    int nx, ny, nz;
+    double hx, hy, hz;
+} or_vol;
+
+#define VIDX(v, i, j, k) ((((long)(k)) * (v)->ny + (j)) * (long)(v)->nx + (i))
+
+/* Forward differences / h with zero difference at the last index (Neumann). */
+static void grad_at(const or_vol *v, const double *f, int i, int j, int k, double out[3])
+{
+    double c = f[VIDX(v, i, j, k)];
+    out[0] = i < v->nx - 1 ? (f[VIDX(v, i + 1, j, k)] - c) / v->hx : 0.0;
+    out[1] = j < v->ny - 1 ? (f[VIDX(v, i, j + 1, k)] - c) / v->hy : 0.0;
+    out[2] = k < v->nz - 1 ? (f[VIDX(v, i, j, k + 1)] - c) / v->hz : 0.0;
+}
+
+/* TV_eps(f) = sum_j sqrt(|grad f|_j^2 + eps^2). */
+double or_tv(const or_vol *v, const double *f, double eps)
+{
+    double total = 0.0;
+#pragma omp parallel for reduction(+ : total) schedule(static)
+    for (int k = 0; k < v->nz; ++k)
+        for (int j = 0; j < v->ny; ++j)
+            for (int i = 0; i < v->nx; ++i) {
+                double gr[3];
+                grad_at(v, f, i, j, k, gr);
+                total += sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2] + eps * eps);
+            }
+    return total;
+}
+
+/*
+ * Gradient of TV_eps: sum_d D_d^T (D_d f / |grad f|_eps), with
+ * (D_d^T p)_i = (p_{i-1} [i > 0] - p_i [i < n-1]) / h_d.
+ */
+void or_tv_grad(const or_vol *v, const double *f, double eps, double *out)
+{
+    const long n = (long)v->nx * v->ny * v->nz;
+    double *p = (double *)malloc(sizeof(double) * 3 * n);
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < v->nz; ++k)
+        for (int j = 0; j < v->ny; ++j)
+            for (int i = 0; i < v->nx; ++i) {
+                double gr[3];
+                grad_at(v, f, i, j, k, gr);
+                double nrm = sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2] + eps * eps);
+                long q = VIDX(v, i, j, k);
+                p[3 * q + 0] = gr[0] / nrm;
+                p[3 * q + 1] = gr[1] / nrm;
+                p[3 * q + 2] = gr[2] / nrm;
+            }
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < v->nz; ++k)
+        for (int j = 0; j < v->ny; ++j)
+            for (int i = 0; i < v->nx; ++i) {
+                long q = VIDX(v, i, j, k);
+                double s = 0.0;
+                s += ((i > 0 ? p[3 * VIDX(v, i - 1, j, k) + 0] : 0.0) - (i < v->nx - 1 ? p[3 * q + 0] : 0.0)) / v->hx;
+                s += ((j > 0 ? p[3 * VIDX(v, i, j - 1, k) + 1] : 0.0) - (j < v->ny - 1 ? p[3 * q + 1] : 0.0)) / v->hy;
+                s += ((k > 0 ? p[3 * VIDX(v, i, j, k - 1) + 2] : 0.0) - (k < v->nz - 1 ? p[3 * q + 2] : 0.0)) / v->hz;
+                out[q] = s;
+            }
+    free(p);
+}
+
+/* Lipschitz bound of grad TV_eps: (4/eps) sum_d h_d^-2. */
+double or_tv_lipschitz(const or_vol *v, double eps)
+{
+    return 4.0 / eps * (1.0 / (v->hx * v->hx) + 1.0 / (v->hy * v->hy) + 1.0 / (v->hz * v->hz));
+}
+
+/*
+ * Step 2 (and 3) of Algorithm A1: M gradient steps on
+ *   Phi(f) = w TV_eps(f) + beta/2 |f - g|^2,  step s = 1/(beta + w L_TV).
+ * clamp_mode 0: start from f (the previous iterate, given in f), project onto f >= 0
+ *               after every step.
+ * clamp_mode 1: start from g, no bound during the descent, clamp once at the end.
+ * w is the TV weight (1 for the method; 0 reduces the step to a projection).
+ * If phi is non-null it receives Phi at the start and after each step (M + 1 values).
+ */
+void or_prox(const or_vol *v, const double *g, double *f, double beta, double eps, int M,
+             int clamp_mode, double w, double *phi)
+{
+    const long n = (long)v->nx * v->ny * v->nz;
+    double s = 1.0 / (beta + w * or_tv_lipschitz(v, eps));
+    double *grad = (double *)malloc(sizeof(double) * n);
+    if (clamp_mode == 1) memcpy(f, g, sizeof(double) * n);
+    for (int m = 0; m <= M; ++m) {
+        if (phi) {
+            double q = 0.0;
+            for (long j = 0; j < n; ++j) q += (f[j] - g[j]) * (f[j] - g[j]);
+            phi[m] = w * or_tv(v, f, eps) + 0.5 * beta * q;
+        }
+        if (m == M) break;
+        or_tv_grad(v, f, eps, grad);
+#pragma omp parallel for schedule(static)
+        for (long j = 0; j < n; ++j) {
+            double x = f[j] - s * (w * grad[j] + beta * (f[j] - g[j]));
+            f[j] = (clamp_mode == 0 && x < 0.0) ? 0.0 : x;
+        }
+    }
+    if (clamp_mode == 1)
+        for (long j = 0; j < n; ++j)
+            if (f[j] < 0.0) f[j] = 0.0;
+    free(grad);
+}
+
+/* ------------------------------------------------------------------------------ */
+/* Energy, step size and Algorithm A1                                              */
+/* ------------------------------------------------------------------------------ */
+
+static or_vol vol_of(const or_geom *g)
+{
+    or_vol v = {g->nx, g->ny, g->nz, g->hx, g->hy, g->hz};
+    return v;
+}
+
+/* gamma = 2 mu Nv / (na Np): the data weight once Eq. 1 is multiplied by Nv. */
+double or_gamma(const or_geom *g, double mu)
+{
+    double nvox = (double)g->nx * g->ny * g->nz;
+    double nray = (double)g->na * g->nu * g->nv;
+    return 2.0 * mu * nvox / nray;
+}
+
+/* Default TV smoothing: 1e-3 * 0.02 mm^-1 / min voxel size. */
+double or_default_eps(const or_geom *g)
+{
+    double h = g->hx;
+    if (g->hy < h) h = g->hy;
+    if (g->hz < h) h = g->hz;
+    return 1e-3 * 0.02 / h;
+}
+
+/*
+ * Energy of Eq. 1 on the grid: E = TV_eps/Nv + mu/(na Np) |Pf - Y|^2.
+ * out = {E, E1, E2-term}; r (optional, size na*nv*nu) receives Pf - Y.
+ */
+void or_energy(const or_geom *g, const double *Y, const double *f, double mu, double eps,
+               double *out, double *r_opt)
+{
+    const long nr = (long)g->na * g->nv * g->nu;
+    double *r = r_opt ? r_opt : (double *)malloc(sizeof(double) * nr);
+    or_project(g, f, r);
+    double q = 0.0;
+    for (long t = 0; t < nr; ++t) {
+        r[t] -= Y[t];
+        q += r[t] * r[t];
+    }
+    or_vol v = vol_of(g);
+    double e1 = or_tv(&v, f, eps) / ((double)g->nx * g->ny * g->nz);
+    double e2 = mu * q / (double)nr;
+    out[0] = e1 + e2;
+    out[1] = e1;
+    out[2] = e2;
+    if (!r_opt) free(r);
+}
+
+/*
+ * lambda_max(P^T P) by K power iterations from the all-ones vector; the estimate is
+ * the Rayleigh quotient <x, P^T P x> of the last normalised iterate.
+ */
+double or_power_iteration(const or_geom *g, int K)
+{
+    const long nvox = (long)g->nx * g->ny * g->nz;
+    const long nr = (long)g->na * g->nv * g->nu;
+    double *x = (double *)malloc(sizeof(double) * nvox);
+    double *y = (double *)malloc(sizeof(double) * nvox);
+    double *p = (double *)malloc(sizeof(double) * nr);
+    double inv = 1.0 / sqrt((double)nvox);
+    for (long j = 0; j < nvox; ++j) x[j] = inv;
+    double lam = 0.0;
+    for (int it = 0; it < K; ++it) {
+        or_project(g, x, p);
+        or_backproject(g, p, y);
+        double xy = 0.0, yy = 0.0;
+        for (long j = 0; j < nvox; ++j) {
+            xy += x[j] * y[j];
+            yy += y[j] * y[j];
+        }
+        lam = xy;
+        double s = 1.0 / sqrt(yy);
+        for (long j = 0; j < nvox; ++j) x[j] = y[j] * s;
+    }
+    free(x);
+    free(y);
+    free(p);
+    return lam;
+}
+
+/* beta = max(10 mu, 1.05 gamma lambda_hat). */
+double or_auto_beta(const or_geom *g, double mu, int K)
+{
+    double b = 1.05 * or_gamma(g, mu) * or_power_iteration(g, K);
+    return b > 10.0 * mu ? b : 10.0 * mu;
+}
+
+/*
+ * Algorithm A1 for `iters` iterations from the volume in f (updated in place).
+ * trace (optional, 3 * iters): {E, E1, E2-term} of the iterate entering each iteration.
+ */
+void or_fbs(const or_geom *g, const double *Y, double mu, double beta, double eps, int M,
+            int clamp_mode, double tv_weight, int iters, double *f, double *trace)
+{
+    const long nvox = (long)g->nx * g->ny * g->nz;
+    const long nr = (long)g->na * g->nv * g->nu;
+    or_vol v = vol_of(g);
+    double gamma = or_gamma(g, mu);
+    double *r = (double *)malloc(sizeof(double) * nr);
+    double *bp = (double *)malloc(sizeof(double) * nvox);
+    double *gv = (double *)malloc(sizeof(double) * nvox);
+    for (int it = 0; it < iters; ++it) {
+        /* step 1: g = f - (gamma/beta) P^T (P f - Y) */
+        or_project(g, f, r);
+        double q = 0.0;
+        for (long t = 0; t < nr; ++t) {
+            r[t] -= Y[t];
+            q += r[t] * r[t];
+        }
+        if (trace) {
+            double e1 = or_tv(&v, f, eps) / (double)nvox;
+            double e2 = mu * q / (double)nr;
+            trace[3 * it + 0] = e1 + e2;
+            trace[3 * it + 1] = e1;
+            trace[3 * it + 2] = e2;
+        }
+        or_backproject(g, r, bp);
+        double c = gamma / beta;
+        for (long j = 0; j < nvox; ++j) gv[j] = f[j] - c * bp[j];
+        /* steps 2 and 3 */
+        or_prox(&v, gv, f, beta, eps, M, clamp_mode, tv_weight, NULL);
+    }
+    free(r);
+    free(bp);
+    free(gv);
+}
+
+/* ------------------------------------------------------------------------------ */
+/* Multigrid transfers and the coarse-to-fine cascade                              */
+/* ------------------------------------------------------------------------------ */
+
+/* Mean over the existing pixels of each 2x2 block: [na][nv][nu] -> [na][ceil nv/2][ceil nu/2]. */
+void or_restrict_sino(int na, int nv, int nu, const double *y, double *yc)
+{
+    int nvc = (nv + 1) / 2, nuc = (nu + 1) / 2;
+    for (int ia = 0; ia < na; ++ia)
+        for (int b = 0; b < nvc; ++b)
+            for (int a = 0; a < nuc; ++a) {
+                double s = 0.0;
+                int c = 0;
+                for (int db = 0; db < 2; ++db)
+                    for (int da = 0; da < 2; ++da) {
+                        int bb = 2 * b + db, aa = 2 * a + da;
+                        if (bb < nv && aa < nu) {
+                            s += y[((long)ia * nv + bb) * nu + aa];
+                            ++c;
+                        }
+                    }
+                yc[((long)ia * nvc + b) * nuc + a] = s / c;
+            }
+}
+
+/* Coarse coordinate of fine index i (cell-centred grids, spacing ratio 2). */
+static void prolong_weights(int i, int n, int nc, int *i0, int *i1, double *w)
+{
+    double c = (i - 0.5 * (n - 1)) * 0.5 + 0.5 * (nc - 1);
+    double fl = floor(c);
+    *w = c - fl;
+    int a = (int)fl, b = a + 1;
+    if (a < 0) a = 0;
+    if (a > nc - 1) a = nc - 1;
+    if (b < 0) b = 0;
+    if (b > nc - 1) b = nc - 1;
+    *i0 = a;
+    *i1 = b;
+}
+
+/* Trilinear, cell-centred, x2 prolongation with edge replication. */
+void or_prolong_vol(int nxc, int nyc, int nzc, const double *fc, int nx, int ny, int nz, double *f)
+{
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k) {
+        int k0, k1;
+        double wk;
+        prolong_weights(k, nz, nzc, &k0, &k1, &wk);
+        for (int j = 0; j < ny; ++j) {
+            int j0, j1;
+            double wj;
+            prolong_weights(j, ny, nyc, &j0, &j1, &wj);
+            for (int i = 0; i < nx; ++i) {
+                int i0, i1;
+                double wi;
+                prolong_weights(i, nx, nxc, &i0, &i1, &wi);
+#define FC(ii, jj, kk) fc[((long)(kk) * nyc + (jj)) * nxc + (ii)]
+                double c00 = (1 - wi) * FC(i0, j0, k0) + wi * FC(i1, j0, k0);
+                double c10 = (1 - wi) * FC(i0, j1, k0) + wi * FC(i1, j1, k0);
+                double c01 = (1 - wi) * FC(i0, j0, k1) + wi * FC(i1, j0, k1);
+                double c11 = (1 - wi) * FC(i0, j1, k1) + wi * FC(i1, j1, k1);
+#undef FC
+                double c0 = (1 - wj) * c00 + wj * c10;
+                double c1 = (1 - wj) * c01 + wj * c11;
+                f[((long)k * ny + j) * nx + i] = (1 - wk) * c0 + wk * c1;
+            }
+        }
+    }
+}
+
+/* Geometry of multigrid level l: sizes ceil(n / 2^l), spacings 2^l h. */
+void or_level_geom(const or_geom *g, int l, or_geom *out)
+{
+    *out = *g;
+    int s = 1 << l;
+    out->nx = (g->nx + s - 1) / s;
+    out->ny = (g->ny + s - 1) / s;
+    out->nz = (g->nz + s - 1) / s;
+    out->hx = g->hx * s;
+    out->hy = g->hy * s;
+    out->hz = g->hz * s;
+    out->nu = (g->nu + s - 1) / s;
+    out->nv = (g->nv + s - 1) / s;
+    out->du = g->du * s;
+    out->dv = g->dv * s;
+}
+
+/*
+ * Coarse-to-fine cascade: f = 0 on the coarsest level, `iters` iterations of A1 per
+ * level, prolongation to the next finer level.  betas (optional, one per level, index
+ * = level, 0 finest) fixes beta; otherwise beta = or_auto_beta(level, mu, K_pi).
+ * eps <= 0 takes the per-level default.  trace (optional) gets 3 * iters values per
+ * level, coarsest level first.  f_out is the finest volume.
+ */
+void or_reconstruct(const or_geom *g, const double *Y, double mu, int iters, int levels,
+                    const double *betas, double eps, int M, int clamp_mode, int K_pi,
+                    double *f_out, double *trace)
+{
+    or_geom *lg = (or_geom *)malloc(sizeof(or_geom) * levels);
+    double **Ys = (double **)malloc(sizeof(double *) * levels);
+    for (int l = 0; l < levels; ++l) or_level_geom(g, l, &lg[l]);
+    Ys[0] = (double *)Y;
+    for (int l = 1; l < levels; ++l) {
+        Ys[l] = (double *)malloc(sizeof(double) * (size_t)g->na * lg[l].nv * lg[l].nu);
+        or_restrict_sino(g->na, lg[l - 1].nv, lg[l - 1].nu, Ys[l - 1], Ys[l]);
+    }
+    double *f = NULL;
+    for (int l = levels - 1; l >= 0; --l) {
+        long nvox = (long)lg[l].nx * lg[l].ny * lg[l].nz;
+        double *fl = (double *)calloc(nvox, sizeof(double));
+        if (f) {
+            or_prolong_vol(lg[l + 1].nx, lg[l + 1].ny, lg[l + 1].nz, f, lg[l].nx, lg[l].ny, lg[l].nz, fl);
+            free(f);
+        }
+        f = fl;
+        double beta = betas ? betas[l] : or_auto_beta(&lg[l], mu, K_pi);
+        double e = eps > 0 ? eps : or_default_eps(&lg[l]);
+        double *tr = trace ? trace + 3 * iters * (levels - 1 - l) : NULL;
+        or_fbs(&lg[l], Ys[l], mu, beta, e, M, clamp_mode, 1.0, iters, f, tr);
+    }
+    memcpy(f_out, f, sizeof(double) * (size_t)g->nx * g->ny * g->nz);
+    free(f);
+    for (int l = 1; l < levels; ++l) free(Ys[l]);
+    free(Ys);
+    free(lg);
+}
+
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,421 @@
+"""Pins of the FP64 oracle to facts that do not come from the oracle itself.
+
+Each test names the passage of Jia et al. (2010) it pins and the independent fact used:
+closed forms, a brute-force system matrix, invariants, a library optimiser, exact
+hand-derived lengths, and the paper's own Eq. 2.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle.brute_matrix import ray_endpoints, system_matrix, tiny_geometry
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _box_chord(S, P, lo, hi):
+    """Closed-form length of the segment S->P inside the box [lo, hi] (slab method)."""
+    d = P - S
+    t0, t1 = 0.0, 1.0
+    for ax in range(3):
+        if d[ax] == 0.0:
+            if not (lo[ax] <= S[ax] < hi[ax]):
+                return 0.0
+            continue
+        a, b = (lo[ax] - S[ax]) / d[ax], (hi[ax] - S[ax]) / d[ax]
+        t0, t1 = max(t0, min(a, b)), min(t1, max(a, b))
+    return max(t1 - t0, 0.0) * float(np.linalg.norm(d))
+
+
+# ---------------------------------------------------------------------------------
+# Projector P^theta (problem statement, Eq. 1)
+# ---------------------------------------------------------------------------------
+
+def test_P_of_ones_is_box_chord():
+    """f = 1 on the volume: every line integral is the ray's chord through the box."""
+    g = tiny_geometry(n=8, h=4.0, nu=10, nv=7, du=7.0, dv=9.0, n_angles=5, theta0=0.3)
+    y = oracle.project(g, np.ones((8, 8, 8)))
+    S, P = ray_endpoints(g)
+    half = np.array([16.0, 16.0, 16.0])
+    ref = np.array([[[_box_chord(S[ia], P[ia, b, a], -half, half) for a in range(10)]
+                     for b in range(7)] for ia in range(5)])
+    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert (ref > 0).sum() > 100
+
+
+def test_P_single_voxel_indicator():
+    """f = e_j: the projection is the ray's intersection length with voxel j's box."""
+    g = tiny_geometry(n=6, h=5.0, nu=9, nv=9, du=6.0, dv=6.0, n_angles=3, theta0=0.1)
+    S, P = ray_endpoints(g)
+    for (i, j, k) in [(0, 0, 0), (2, 3, 1), (5, 5, 5), (3, 2, 4)]:
+        f = np.zeros((6, 6, 6))
+        f[k, j, i] = 1.0
+        y = oracle.project(g, f)
+        lo = np.array([(i - 3) * 5.0, (j - 3) * 5.0, (k - 3) * 5.0])
+        ref = np.array([[[_box_chord(S[ia], P[ia, b, a], lo, lo + 5.0) for a in range(9)]
+                         for b in range(9)] for ia in range(3)])
+        assert np.abs(y - ref).max() <= 1e-12 * 5.0
+
+
+def test_P_and_PT_equal_brute_force_matrix():
+    """8^3 volume, 8x8 imager, 6 views: P = A and P^T = A^T for a dense A built by
+    testing every ray against every voxel box."""
+    g = tiny_geometry()
+    A = system_matrix(g)
+    rng = np.random.default_rng(1)
+    for _ in range(3):
+        f = rng.uniform(-1, 1, size=(8, 8, 8))
+        y = rng.normal(size=(6, 8, 8))
+        Pf = oracle.project(g, f)
+        assert np.abs(Pf.ravel() - A @ f.ravel()).max() <= 1e-12 * np.abs(A @ f.ravel()).max()
+        PTy = oracle.backproject(g, y)
+        assert np.abs(PTy.ravel() - A.T @ y.ravel()).max() <= 1e-12 * np.abs(A.T @ y.ravel()).max()
+    assert oracle.count_nnz(g) == int((A > 0).sum())
+
+
+def test_degenerate_rays_match_brute_force():
+    """Odd imager sizes put central rays exactly in voxel planes (d_y = 0, d_z = 0 at
+    theta = 0); the half-open voxel convention decides their voxel.  Compared with the
+    brute-force matrix, which applies the same convention by slab tests."""
+    g = tiny_geometry(n=8, h=4.0, nu=9, nv=9, du=8.0, dv=8.0, n_angles=4)
+    A = system_matrix(g)
+    rng = np.random.default_rng(2)
+    f = rng.uniform(size=(8, 8, 8))
+    assert np.abs(oracle.project(g, f).ravel() - A @ f.ravel()).max() <= 1e-12 * 100
+    y = rng.normal(size=(4, 9, 9))
+    assert np.abs(oracle.backproject(g, y).ravel() - A.T @ y.ravel()).max() <= 1e-12 * 100
+    # the central ray at theta = 0 lies in y = 0 and z = 0 and belongs to j = 4, k = 4
+    idx, ln = oracle.ray_segments(g, 0, 4, 4)
+    ks, js = idx // 64, (idx // 8) % 8
+    assert set(ks.tolist()) == {4} and set(js.tolist()) == {4}
+    assert abs(ln.sum() - 32.0) < 1e-12
+
+
+def test_golden_hand_derived_rays():
+    with open(os.path.join(GOLDEN, "hand_rays.json")) as fh:
+        cases = json.load(fh)["cases"]
+    for case in cases:
+        g = dict(case["geom"])
+        g["angles"] = np.array(g["angles"], dtype=np.float64)
+        ia, b, a = case["ray"]
+        idx, ln = oracle.ray_segments(g, ia, b, a)
+        got = {int(q): float(L) for q, L in zip(idx, ln) if L > 0}
+        want = {(k * g["ny"] + j) * g["nx"] + i: L for i, j, k, L in case["voxels"]}
+        assert set(got) == set(want), case["name"]
+        for q in want:
+            assert abs(got[q] - want[q]) <= 1e-14 * 4, case["name"]
+
+
+def test_P_converges_to_analytic_chords():
+    """Voxelised ellipsoid phantom: P f_h tends to the exact line integrals as h -> 0
+    (error falling with h, about first order overall)."""
+    errs = []
+    for n in (16, 32, 64, 128):
+        h = 128.0 / n
+        g = dict(nx=n, ny=n, nz=n, hx=h, hy=h, hz=h, nu=40, nv=30, du=6.0, dv=6.0,
+                 dso=1000.0, dsd=1500.0, angles=2 * math.pi * np.arange(4) / 4 + 0.2)
+        ells = synth.make_ellipsoids(g, np.random.default_rng(5), n=4)
+        exact = synth.analytic_sinogram(ells, g)
+        f = synth.voxelize(ells, g, ss=4)
+        errs.append(np.linalg.norm(oracle.project(g, f) - exact) / np.linalg.norm(exact))
+    assert errs[0] > errs[1] > errs[2] > errs[3]
+    assert errs[3] < 0.15 * errs[0]     # 8x finer grid, first-order convergence
+    assert errs[3] < 0.012
+
+
+def test_P_rotation_symmetry():
+    """With nx = ny and hx = hy, the view at theta + 90 deg of the volume rotated by
+    90 deg about z equals the view at theta of the original volume."""
+    n = 10
+    base = dict(nx=n, ny=n, nz=6, hx=3.0, hy=3.0, hz=4.0, nu=12, nv=8, du=5.0, dv=5.0, dso=150.0, dsd=240.0)
+    rng = np.random.default_rng(3)
+    f = rng.uniform(size=(6, n, n))
+    th = np.array([0.37, 1.1])
+    y0 = oracle.project(dict(base, angles=th), f)
+    # rotation (x, y) -> (-y, x): f'[k, J, I] = f[k, n-1-I, J]
+    fr = f[:, ::-1, :].transpose(0, 2, 1)
+    y1 = oracle.project(dict(base, angles=th + math.pi / 2), fr)
+    assert np.abs(y0 - y1).max() <= 1e-12 * np.abs(y0).max()
+
+
+# ---------------------------------------------------------------------------------
+# Adjoint (matrix transpose before Eq. 2; Eq. 2 itself)
+# ---------------------------------------------------------------------------------
+
+def test_adjoint_identity():
+    case = synth.make_case("small")
+    g = case["geom"]
+    rng = np.random.default_rng(4)
+    f = rng.uniform(size=(64, 64, 64))
+    y = rng.normal(size=(20, 48, 64))
+    Pf = oracle.project(g, f)
+    lhs = float(np.sum(Pf * y))
+    rhs = float(np.sum(f * oracle.backproject(g, y)))
+    assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(Pf) * np.linalg.norm(y)
+
+
+def test_scatter_adjoint_equals_voxel_brute_force():
+    """The scatter adjoint at sampled voxels of the 64^3 workload equals a per-voxel
+    sum over every ray of its slab-test length (no Siddon walk involved)."""
+    g = synth.geometry_for(synth.CONFIGS["small"])
+    rng = np.random.default_rng(6)
+    y = rng.normal(size=(20, 48, 64))
+    bt = oracle.backproject(g, y)
+    for _ in range(6):
+        i, j, k = rng.integers(0, 64, size=3)
+        v = oracle.backproject_voxel(g, y, int(i), int(j), int(k))
+        assert abs(v - bt[k, j, i]) <= 1e-11 * max(1.0, abs(v))
+
+
+def test_adjoint_matches_eq2_jacobian():
+    """Eq. 2: the variation of E2 weighs the residual at (u*, v*) by 2 L^3/(L0 l^2).
+    Summed over a voxel's rays, the exact transpose of 1 therefore approaches
+    sum_theta dV L^3 / (L0 l^2 du dv) when the imager samples the voxel finely."""
+    n, h = 12, 4.0
+    g = dict(nx=n, ny=n, nz=n, hx=h, hy=h, hz=h, nu=200, nv=200, du=0.6, dv=0.6,
+             dso=300.0, dsd=450.0, angles=2 * math.pi * np.arange(8) / 8 + 0.05)
+    bt = oracle.backproject(g, np.ones((8, 200, 200)))
+    ratios = []
+    for k in range(3, 9):
+        for j in range(3, 9):
+            for i in range(3, 9):
+                x = np.array([(i - (n - 1) / 2) * h, (j - (n - 1) / 2) * h, (k - (n - 1) / 2) * h])
+                ref = 0.0
+                for th in g["angles"]:
+                    S = np.array([g["dso"] * math.cos(th), g["dso"] * math.sin(th), 0.0])
+                    w = np.array([-math.cos(th), -math.sin(th), 0.0])     # central-ray direction
+                    d = x - S
+                    l = np.linalg.norm(d)
+                    L = l * g["dsd"] / float(d @ w)                       # source to (u*, v*)
+                    ref += h ** 3 * L ** 3 / (g["dsd"] * l * l * g["du"] * g["dv"])
+                ratios.append(bt[k, j, i] / ref)
+    ratios = np.array(ratios)
+    assert abs(ratios.mean() - 1.0) < 0.01
+    assert np.abs(ratios - 1.0).max() < 0.05
+
+
+# ---------------------------------------------------------------------------------
+# E1 and the step-2 prox (Algorithm A1 steps 2 and 3)
+# ---------------------------------------------------------------------------------
+
+H = (1.3, 0.7, 2.1)
+
+
+def test_tv_gradient_matches_finite_differences():
+    rng = np.random.default_rng(7)
+    f = rng.uniform(size=(5, 6, 7))
+    eps = 0.05
+    gr = oracle.tv_grad(f, H, eps)
+    step = 1e-6
+    for _ in range(20):
+        k, j, i = rng.integers(0, 5), rng.integers(0, 6), rng.integers(0, 7)
+        fp, fm = f.copy(), f.copy()
+        fp[k, j, i] += step
+        fm[k, j, i] -= step
+        fd = (oracle.tv(fp, H, eps) - oracle.tv(fm, H, eps)) / (2 * step)
+        assert abs(fd - gr[k, j, i]) <= 1e-7 * max(1.0, abs(fd))
+
+
+def test_tv_of_constant_and_of_a_step():
+    eps = 0.01
+    f = np.full((4, 5, 6), 3.0)
+    assert abs(oracle.tv(f, H, eps) - f.size * eps) <= 1e-12 * f.size * eps
+    assert np.abs(oracle.tv_grad(f, H, eps)).max() == 0.0
+    # a step of height 0.7 along x between i = 2 and i = 3: TV_0 = ny nz 0.7 / hx
+    s = np.zeros((4, 5, 6))
+    s[:, :, 3:] = 0.7
+    assert abs(oracle.tv(s, H, 0.0) - 4 * 5 * 0.7 / H[0]) <= 1e-12
+
+
+def test_tv_matches_autograd_definition():
+    """TV_eps and its gradient against an independent torch autograd statement."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(8)
+    f = rng.uniform(size=(6, 5, 7))
+    eps = 0.02
+    t = torch.tensor(f, requires_grad=True, dtype=torch.float64)
+    dz = torch.nn.functional.pad(torch.diff(t, dim=0), (0, 0, 0, 0, 0, 1)) / H[2]
+    dy = torch.nn.functional.pad(torch.diff(t, dim=1), (0, 0, 0, 1)) / H[1]
+    dx = torch.nn.functional.pad(torch.diff(t, dim=2), (0, 1)) / H[0]
+    val = torch.sqrt(dx * dx + dy * dy + dz * dz + eps * eps).sum()
+    val.backward()
+    assert abs(val.item() - oracle.tv(f, H, eps)) <= 1e-12 * val.item()
+    assert np.abs(t.grad.numpy() - oracle.tv_grad(f, H, eps)).max() <= 1e-10
+
+
+def test_prox_limits_and_monotonicity():
+    rng = np.random.default_rng(9)
+    g = rng.normal(size=(6, 7, 8))
+    f0 = np.maximum(rng.normal(size=g.shape), 0.0)
+    eps = 0.05
+    # beta -> infinity: the prox is the projection max(g, 0)
+    f = oracle.prox(g, f0, H, 1e9, eps, 60)
+    assert np.abs(f - np.maximum(g, 0)).max() < 1e-6
+    # Phi = TV_eps + beta/2 |f - g|^2 never increases; f >= 0 exactly
+    f, phi = oracle.prox(g, f0, H, 3.0, eps, 25, return_phi=True)
+    assert np.all(np.diff(phi) <= 1e-12 * np.abs(phi[:-1]))
+    assert (f >= 0).all()
+    # paper-literal clamp (descend from g, clamp once): still non-negative
+    f1 = oracle.prox(g, None, H, 3.0, eps, 25, clamp_mode=1)
+    assert (f1 >= 0).all() and np.any(f1 == 0)
+
+
+# ---------------------------------------------------------------------------------
+# Algorithm A1 (FBS) and the energy of Eq. 1
+# ---------------------------------------------------------------------------------
+
+def test_fbs_energy_monotone_small_workload():
+    case = synth.make_case("small")
+    g = case["geom"]
+    beta = oracle.auto_beta(g, case["mu"])
+    eps = oracle.default_eps(g)
+    f, tr = oracle.fbs(g, case["Y"], case["mu"], beta, eps, 10, 20)
+    E = list(tr[:, 0]) + [oracle.energy(g, case["Y"], f, case["mu"], eps)[0]]
+    for a, b in zip(E[:-1], E[1:]):
+        assert b <= a * (1 + 1e-12)
+    assert E[-1] < 0.2 * E[0]
+    assert (f >= 0).all()
+
+
+def test_fbs_fixed_point():
+    """f* constant and Y = P f*: E1 = eps (TV_eps / Nv), E2 = 0 and f stays at f*."""
+    g = tiny_geometry(n=8, h=4.0, nu=10, nv=10, du=7.0, dv=7.0, n_angles=5)
+    fstar = np.full((8, 8, 8), 0.013)
+    Y = oracle.project(g, fstar)
+    eps = 1e-3
+    E = oracle.energy(g, Y, fstar, 2.0, eps)
+    assert abs(E[1] - eps) <= 1e-15 and E[2] == 0.0
+    f, _ = oracle.fbs(g, Y, 2.0, 50.0, eps, 5, 3, f0=fstar)
+    assert np.abs(f - fstar).max() <= 1e-15
+
+
+def test_fbs_without_tv_is_projected_landweber():
+    """Removing the TV term (weight 0, one inner step of length 1/beta) reduces
+    Algorithm A1 to f <- max(0, f - (gamma/beta) A^T (A f - Y)) on the dense matrix."""
+    g = tiny_geometry()
+    A = system_matrix(g)
+    rng = np.random.default_rng(10)
+    Y = rng.uniform(0, 3, size=(6, 8, 8))
+    mu, beta = 1.5, 4000.0
+    f, _ = oracle.fbs(g, Y, mu, beta, 1e-3, 1, 15, tv_weight=0.0)
+    gam = 2 * mu * 512 / (6 * 64)
+    x = np.zeros(512)
+    for _ in range(15):
+        x = np.maximum(0.0, x - gam / beta * (A.T @ (A @ x - Y.ravel())))
+    assert np.abs(f.ravel() - x).max() <= 1e-12 * max(1.0, np.abs(x).max())
+
+
+@pytest.mark.slow
+def test_fbs_converges_to_lbfgsb_minimiser():
+    """On 8^3 the FBS limit equals SciPy's L-BFGS-B minimiser of the same objective
+    Nv E = TV_eps + (gamma/2)|A f - Y|^2 over f >= 0 (TV via torch autograd)."""
+    torch = pytest.importorskip("torch")
+    from scipy.optimize import minimize
+
+    g = tiny_geometry(n=8, h=4.0, nu=10, nv=10, du=6.0, dv=6.0, n_angles=8)
+    A = system_matrix(g)
+    rng = np.random.default_rng(11)
+    ftrue = np.zeros((8, 8, 8))
+    ftrue[2:6, 2:6, 2:6] = 0.02
+    ftrue[3:5, 3:5, 1:4] += 0.01
+    Y = oracle.project(g, ftrue) + rng.normal(scale=0.01, size=(8, 10, 10))
+    mu, eps = 0.5, 2e-3
+    gam = 2 * mu * 512 / (8 * 100)
+
+    def obj(x):
+        t = torch.tensor(x.reshape(8, 8, 8), requires_grad=True, dtype=torch.float64)
+        dz = torch.nn.functional.pad(torch.diff(t, dim=0), (0, 0, 0, 0, 0, 1)) / 4.0
+        dy = torch.nn.functional.pad(torch.diff(t, dim=1), (0, 0, 0, 1)) / 4.0
+        dx = torch.nn.functional.pad(torch.diff(t, dim=2), (0, 1)) / 4.0
+        r = torch.tensor(A) @ t.reshape(-1) - torch.tensor(Y.ravel())
+        val = torch.sqrt(dx * dx + dy * dy + dz * dz + eps * eps).sum() + 0.5 * gam * (r * r).sum()
+        val.backward()
+        return val.item(), t.grad.numpy().ravel().copy()
+
+    res = minimize(obj, np.zeros(512), jac=True, method="L-BFGS-B", bounds=[(0, None)] * 512,
+                   options=dict(maxiter=20000, ftol=1e-16, gtol=1e-13, maxcor=30))
+    beta = oracle.auto_beta(g, mu)
+    f, _ = oracle.fbs(g, Y, mu, beta, eps, 50, 1500)
+    fo = res.x.reshape(8, 8, 8)
+    assert np.linalg.norm(f - fo) / np.linalg.norm(fo) < 1e-5
+    assert obj(f.ravel())[0] <= res.fun * (1 + 1e-9)
+
+
+def test_power_iteration_bounds_spectrum():
+    """lambda_hat from 30 power iterations is within 1% below the largest eigenvalue
+    of A^T A (numpy eigvalsh on the dense matrix)."""
+    g = tiny_geometry()
+    A = system_matrix(g)
+    lmax = np.linalg.eigvalsh(A.T @ A)[-1]
+    lam = oracle.power_iteration(g, 30)
+    assert lam <= lmax * (1 + 1e-12) and lam >= 0.99 * lmax
+
+
+# ---------------------------------------------------------------------------------
+# Multigrid transfers and the cascade
+# ---------------------------------------------------------------------------------
+
+def test_prolongation_reproduces_constants_and_linears():
+    fc = np.full((3, 4, 5), 0.25)
+    assert np.abs(oracle.prolong_vol(fc, (6, 8, 10)) - 0.25).max() <= 1e-16
+    # linear function sampled at coarse cell centres -> exact at fine interior centres
+    nz, ny, nx = 6, 8, 10
+    kc, jc, ic = np.meshgrid(np.arange(3), np.arange(4), np.arange(5), indexing="ij")
+    lin = lambda x, y, z: 0.3 * x - 0.7 * y + 1.1 * z + 2.0  # noqa: E731
+    fcl = lin((ic - 2.0) * 2, (jc - 1.5) * 2, (kc - 1.0) * 2)
+    f = oracle.prolong_vol(fcl, (nz, ny, nx))
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    ref = lin(i - 4.5, j - 3.5, k - 2.5)
+    inner = (slice(1, -1), slice(1, -1), slice(1, -1))
+    assert np.abs(f[inner] - ref[inner]).max() <= 1e-13
+
+
+def test_restriction_is_block_mean():
+    rng = np.random.default_rng(12)
+    y = rng.normal(size=(3, 7, 9))
+    yc = oracle.restrict_sino(y)
+    assert yc.shape == (3, 4, 5)
+    assert abs(yc[1, 2, 3] - y[1, 4:6, 6:8].mean()) <= 1e-15
+    assert abs(yc[2, 3, 4] - y[2, 6, 8]) <= 1e-15           # corner bin: one pixel
+    assert abs(yc[0, 3, 1] - y[0, 6, 2:4].mean()) <= 1e-15  # edge bin: two pixels
+
+
+def test_single_level_cascade_equals_fbs():
+    case = synth.make_case("small")
+    g = case["geom"]
+    beta = 7.5e4
+    eps = oracle.default_eps(g)
+    f1, tr1 = oracle.reconstruct(g, case["Y"], case["mu"], 4, 1, betas=[beta], M=5)
+    f2, tr2 = oracle.fbs(g, case["Y"], case["mu"], beta, eps, 5, 4)
+    assert np.array_equal(f1, f2)
+    assert np.array_equal(tr1[0], tr2)
+
+
+def test_two_level_cascade_runs_and_descends():
+    case = synth.make_case("small")
+    g = case["geom"]
+    f, tr = oracle.reconstruct(g, case["Y"], case["mu"], 5, 2, M=5)
+    assert f.shape == (64, 64, 64) and (f >= 0).all()
+    assert np.all(np.diff(tr[0, :, 0]) <= 1e-12 * tr[0, :-1, 0])
+    assert np.all(np.diff(tr[1, :, 0]) <= 1e-12 * tr[1, :-1, 0])
+    lg = oracle.level_geom(g, 1)
+    assert (lg["nx"], lg["nu"], lg["nv"], lg["hx"], lg["du"]) == (32, 32, 24, 8.0, 16.0)
+
+
+# ---------------------------------------------------------------------------------
+# Synthetic data (inputs only)
+# ---------------------------------------------------------------------------------
+
+def test_poisson_noise_statistics():
+    rng = np.random.default_rng(13)
+    Y = np.full(200000, 1.5)
+    I0 = 1e4
+    N = np.exp(-synth.poisson_log(Y, I0, rng)) * I0
+    lam = I0 * math.exp(-1.5)
+    assert abs(N.mean() - lam) < 3 * math.sqrt(lam / N.size)
+    assert abs(N.var() / lam - 1.0) < 3 * math.sqrt(2.0 / N.size)
