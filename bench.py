@@ -1,0 +1,328 @@
+"""Benchmark: FBS iterations/s of the full multigrid reconstruction on one B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload medium]
+    python -m torch.distributed.run --nproc-per-node N ... bench.py --gpus N
+
+A step is one complete ``cbct_reconstruct`` call (Algorithm A1 on every multigrid
+level: forward projection + residual, adjoint gather + gradient step, M TV-prox
+sweeps with f >= 0, float64 energies; the automatic beta's power iterations; the
+2x2 data binning and the prolongations) on seeded synthetic data of the workload's
+shape.  Inputs are resident in HBM when the timed region starts; L2 is flushed
+(256 MiB write) between steps, outside the timed events.  Each GPU runs independent
+reconstructions (no data-path collective; weak scaling).
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead, on
+the host cores, one Algorithm A1 iteration of the finest level per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD_TEXT = {
+    "small": "64^3 @ 4 mm, 20 views 64x48 @ 8 mm, noise-free, 1 level x 20 FBS iterations",
+    "medium": "256x256x64 @ 1x1x2.5 mm, 40 views 256x192 @ 1.6 mm, Poisson I0=1e5, 2-level multigrid "
+              "x 50 FBS iterations per level",
+    "large": "512x512x96 @ 0.5x0.5x2.5 mm, 40 views 512x384 @ 0.8 mm, Poisson I0=2.5e4, 3-level multigrid "
+             "x 50 FBS iterations per level",
+}
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+# Lane-operations per nonzero that no implementation of the exact-length operators can
+# avoid ("Roofline"): adjoint 8 (two z-crossings: 2 sub + 2 mul, clip:
+# 1 max + 1 min, length: 1 sub, accumulate: 1 fma); projector 4 (pick next crossing:
+# 1 min, length: 1 sub, accumulate: 1 fma, advance the crossing: 1 fma).
+OPS_PER_NNZ = {"backproject": 8.0, "project": 4.0}
+
+
+def load_nnz(workload):
+    with open(os.path.join(ROOT, "tests", "golden", "nnz.json")) as fh:
+        return [lv["nnz"] for lv in json.load(fh)[workload]]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={CLOCK_QUERY}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[5 + q].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_oracle_iterations(case, n_iter):
+    """Time n_iter Algorithm A1 iterations of the oracle on the finest level."""
+    import oracle
+    g = case["geom"]
+    mu = case["mu"]
+    eps = oracle.default_eps(g)
+    beta = 1.05 * oracle.gamma(g, mu) * 1.6e4  # fixed value of the right size; not timed work
+    Y = np.asarray(case["Y"], dtype=np.float64)
+    f0 = np.zeros((g["nz"], g["ny"], g["nx"]))
+    t0 = time.perf_counter()
+    oracle.fbs(g, Y, mu, beta, eps, 10, n_iter, f0=f0)
+    return time.perf_counter() - t0, oracle.num_threads()
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    case = synth.make_case(args.workload)
+    for _ in range(args.warmup):
+        cpu_oracle_iterations(case, 1)
+    times = []
+    for _ in range(args.steps):
+        dt, cores = cpu_oracle_iterations(case, 1)
+        times.append(dt)
+    tot = sum(times)
+    value = args.steps / tot
+    sample = (f"1 Algorithm A1 iteration (P, P^T, 10 prox sweeps) of the finest level per step "
+              f"({WORKLOAD_TEXT[args.workload].split(',')[0]}), {args.steps} steps")
+    line = {"impl": "reference", "metric": "FBS iterations/s", "value": value, "unit": "iter/s",
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded ellipsoid phantom, analytic line integrals, Poisson/log noise)",
+            "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "host_cores": os.cpu_count()},
+            "cpu_baseline": {"value": value, "unit": "iter/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, world, rank, local):
+    import torch
+
+    from paper_1002_3675_b300 import cbct
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = synth.CONFIGS[args.workload]
+    case = synth.make_case(args.workload)
+    G = cbct.cbct_geometry_create(case["geom"])
+    levels, iters, mu = cfg["levels"], cfg["iters"], cfg["mu"]
+    Y_host = torch.tensor(np.asarray(case["Y"], dtype=np.float32)).pin_memory()
+    Y = Y_host.to(dev)
+    f = torch.empty((cfg["vol"][2], cfg["vol"][1], cfg["vol"][0]), dtype=torch.float32, device=dev)
+    f_host = torch.empty(f.shape, dtype=torch.float32).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(kernel_times):
+        return cbct.cbct_reconstruct(G, Y, mu, iters, levels, f_out=f, kernel_times=kernel_times)
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region --------------------------------------------
+    sampler = ClockSampler(local) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    step_ms, kms, klaunch = [], {}, {}
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, info = step(True)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        for k, v in info["kernel_ms"].items():
+            kms[k] = kms.get(k, 0.0) + v
+        for k, v in info["kernel_launches"].items():
+            klaunch[k] = klaunch.get(k, 0) + v
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    tot_ms = max_over_ranks(sum(step_ms), world)
+    n_iter = levels * iters
+    value = world * args.steps * n_iter / (tot_ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers ---------------------------
+    barrier(world)
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Y.copy_(Y_host, non_blocking=True)
+        step(False)
+        f_host.copy_(f, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_tot = max_over_ranks(sum(e2e_ms), world)
+    e2e_value = world * args.steps * n_iter / (e2e_tot / 1e3)
+
+    if rank != 0:
+        return
+
+    # ---- roofline of the dominant kernel --------------------------------------------
+    peaks, peak_kind = measured_peaks()
+    nnz = load_nnz(args.workload)
+    K_pi = 30
+    units = {  # nonzeros processed per reconstruction by each operator
+        "project": sum(n * (iters + K_pi) for n in nnz),
+        "backproject": sum(n * (iters + K_pi) for n in nnz),
+    }
+    dom = max(("project", "backproject", "tv"), key=lambda k: kms.get(k, 0.0))
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clock_mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") \
+        or peaks.get("sm_max_mhz", 2032.0)
+    alu_peak = sm_count * 128 * clock_mhz * 1e6 / 1e12      # T lane-ops/s (FP32 pipes x clock)
+    per_kernel = {}
+    for k in ("project", "backproject"):
+        t = kms[k] / 1e3
+        per_kernel[k] = {"ms_per_step": kms[k] / args.steps, "launches_per_step": klaunch[k] / args.steps,
+                         "gnnz_per_s": units[k] * args.steps / t / 1e9,
+                         "alu_tops": units[k] * args.steps * OPS_PER_NNZ[k] / t / 1e12}
+    nvox = [np.prod([(n + (1 << l) - 1) >> l for n in cfg["vol"]]) for l in range(levels)]
+    tv_bytes = sum(12.0 * v * iters * 10 for v in nvox) * args.steps   # read f, read g, write f per sweep
+    per_kernel["tv"] = {"ms_per_step": kms["tv"] / args.steps,
+                        "gbs": tv_bytes / (kms["tv"] / 1e3) / 1e9, "launches_per_step": klaunch["tv"] / args.steps}
+    if dom in ("project", "backproject"):
+        ach = per_kernel[dom]["alu_tops"]
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tlane-op/s",
+                "frac": ach / alu_peak, "traffic": None,
+                "basis": f"{OPS_PER_NNZ[dom]:.0f} lane-ops per nonzero x exact nnz; peak = {sm_count} SMs x 128 "
+                         f"FP32 lanes x {clock_mhz:.0f} MHz (median SM clock in the timed region)"}
+    else:
+        ach = per_kernel["tv"]["gbs"]
+        roof = {"kernel": "tv", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None}
+    roof["peak_source"] = peak_kind
+
+    # ---- CPU baseline: the oracle on a bounded sample ---------------------------------
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        n_cpu = 2
+        dt, cores = cpu_oracle_iterations(case, n_cpu)
+        cpu = {"value": n_cpu / dt, "unit": "iter/s", "cores": cores, "kind": "oracle",
+               "sample": f"{n_cpu} Algorithm A1 iterations (P, P^T, 10 prox sweeps) of the finest level of the "
+                         f"same workload, FP64 C oracle with OpenMP; fixed beta, no power iteration"}
+
+    launches = int(sum(klaunch.values()))
+    line = {
+        "metric": "FBS iterations/s", "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded ellipsoid phantom, analytic line integrals, Poisson/log noise); "
+                "stands in for the paper's NCAT/CatPhan data",
+        "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "inner_iters": 10,
+                   "beta": "auto per level (30 power iterations, recomputed every step)",
+                   "fbs_iterations_per_step": n_iter, "l2": "flushed between steps (256 MiB write, untimed)",
+                   "parallelism": f"replicas x{world}"},
+        "recon_s": tot_ms / args.steps / 1e3,
+        "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": int(Y_host.numel() * 4),
+                "d2h_bytes_per_step": int(f_host.numel() * 4)},
+        "roofline": roof,
+        "kernels": per_kernel,
+        "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="medium", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

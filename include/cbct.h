@@ -1,0 +1,196 @@
+/*
+ * cbct.h -- C ABI of the B300 (sm_103a) TV-regularised cone-beam CT reconstruction
+ * library.  The method is that of Jia, Lou, Li, Song and Jiang (2010): minimise
+ * E[f] = E1[f] + mu E2[f] subject to f >= 0 (Eq. 1) by forward-backward splitting
+ * (Algorithm A1) inside a coarse-to-fine multigrid.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  Units       millimetres; angles in radians; attenuation in mm^-1, so line
+ *              integrals are dimensionless.
+ *  Geometry    circular orbit about z.  Source at (dso cos t, dso sin t, 0); flat
+ *              imager at distance dsd from the source, centred on the central ray,
+ *              axes u = (-sin t, cos t, 0) and v = (0, 0, 1); one ray per pixel
+ *              centre.  The volume grid is centred on the origin; voxels are
+ *              half-open boxes.
+ *  Layouts     volumes   float32 [nz][ny][nx]   (x fastest)
+ *              sinograms float32 [n_angles][nv][nu] (u fastest)
+ *  Memory      every pointer named *_dev is a CUDA device pointer, 16-byte aligned,
+ *              owned by the caller and not retained after the call returns.
+ *              *_host pointers are host memory, read (or written) during the call.
+ *              Handles (cbct_geometry, cbct_server) and the device workspaces
+ *              behind them are owned by the library and freed by the matching
+ *              destroy call.
+ *  Streams     work is enqueued on `stream` (0 = legacy default stream) and is
+ *              asynchronous unless stated; a handle must not be used by two
+ *              host threads at the same time.
+ *  Errors      every call returns a cbct_status; no exception or abort crosses the
+ *              ABI.  cbct_last_error() gives a message for the calling thread.
+ *              Invalid arguments are rejected before any work is enqueued.  CUDA
+ *              errors raised by the enqueued work are reported by the call that
+ *              observes them (CBCT_ERR_CUDA).
+ *  Precision   bulk arithmetic float32; global reductions (energies, norms,
+ *              step-size estimate) float64.
+ */
+#ifndef CBCT_H
+#define CBCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CBCT_OK = 0,
+    CBCT_ERR_INVALID_ARG = 1,  /* bad pointer, size, alignment or parameter      */
+    CBCT_ERR_OOM = 2,          /* a library workspace could not be allocated     */
+    CBCT_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed    */
+    CBCT_ERR_TIMEOUT = 4,      /* a bounded wait expired                         */
+    CBCT_ERR_UNSUPPORTED = 5,  /* option combination not implemented            */
+    CBCT_ERR_BUSY = 6          /* admission refused (budget or slots exhausted)  */
+} cbct_status;
+
+/* Scan and grid description (problem statement before Eq. 1: P^theta maps f onto
+ * an imager at angle theta).  All sizes >= 1; spacings, dso, dsd > 0; the source
+ * circle must clear the volume (dso > half diagonal of the xy extent) and the
+ * imager must lie beyond it (dsd - dso > half diagonal).  nx*ny*nz and
+ * n_angles*nu*nv must each be below 2^31. */
+typedef struct {
+    int nx, ny, nz;      /* voxels                                    */
+    double hx, hy, hz;   /* voxel size, mm                            */
+    int nu, nv;          /* imager pixels                             */
+    double du, dv;       /* pixel pitch, mm                           */
+    double dso, dsd;     /* source-to-axis, source-to-imager (L0), mm */
+} cbct_geometry_desc;
+
+typedef struct cbct_geometry cbct_geometry;
+
+/* Solver options for cbct_reconstruct.  A zero-initialised struct selects the
+ * defaults given in brackets. */
+typedef struct {
+    double beta;          /* Algorithm A1's beta for every level; 0 -> per level
+                             max(10 mu, 1.05 gamma lambda_max(P^T P)) [auto]      */
+    const double *betas;  /* optional host [levels], index 0 = finest; overrides beta */
+    double eps;           /* TV smoothing, mm^-2; 0 -> 2e-5 / min(h) per level    */
+    int inner_iters;      /* M gradient steps of step 2; 0 -> 10                  */
+    int clamp_mode;       /* 0: f >= 0 enforced in every inner step from f_k [default];
+                             1: step 2 descends from g without the bound and step 3
+                             clamps afterwards (Algorithm A1 read literally)      */
+    int sino_fp16;        /* 1: keep the projection data in half precision on the
+                             device (the input stays float32)                    */
+    int power_iters;      /* power iterations for the automatic beta; 0 -> 30     */
+    int start_level;      /* resume: first (coarsest) level to run; 0 -> levels-1
+                             with f_init ignored; otherwise f_init seeds it        */
+    const float *f_init_dev; /* optional initial volume of level start_level, in
+                             that level's [nz][ny][nx] layout (see cbct_level_dims) */
+    int use_graphs;       /* 1: replay each FBS iteration as a captured CUDA graph */
+    double *energy_trace; /* optional host out [levels][iters][3]: E, E1, mu*E2 of
+                             the iterate entering each iteration, coarsest level
+                             first; levels not run are left untouched.  Filling it
+                             synchronises the stream once per level.              */
+    double *beta_out;     /* optional host out [levels]: beta used per level      */
+    float *kernel_ms;     /* optional host out [CBCT_NUM_KERNEL_CLASSES]: summed
+                             device time per kernel class, measured with CUDA events
+                             on `stream` (synchronises at the end of the call)    */
+    int *kernel_launches; /* optional host out [CBCT_NUM_KERNEL_CLASSES]          */
+} cbct_options;
+
+/* Kernel classes reported through cbct_options.kernel_ms. */
+enum {
+    CBCT_K_PROJECT = 0,     /* forward projection + residual          */
+    CBCT_K_BACKPROJECT = 1, /* adjoint gather + gradient step         */
+    CBCT_K_TV = 2,          /* TV prox sweeps with f >= 0             */
+    CBCT_K_REDUCE = 3,      /* float64 reductions and small kernels   */
+    CBCT_K_TRANSFER = 4,    /* multigrid transfers and layout changes */
+    CBCT_NUM_KERNEL_CLASSES = 5
+};
+
+/* Create a geometry for the given angles (host, radians, n_angles >= 1) on the
+ * current CUDA device.  Device tables derived from it (ray parameters per view and
+ * detector column, per detector pixel) are computed in float64 on the host and
+ * stored in float32.  On success *out owns them. */
+cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, const double *angles_host,
+                                 int n_angles, cbct_geometry **out);
+void cbct_geometry_destroy(cbct_geometry *geom);
+
+/* Sizes of multigrid level `level` (0 = the geometry itself): n_l = ceil(n / 2^l),
+ * spacing 2^l h, imager ceil(nu / 2^l) x ceil(nv / 2^l) at pitch 2^l du.  dims_out
+ * receives {nx, ny, nz, nu, nv}. */
+cbct_status cbct_level_dims(const cbct_geometry *geom, int level, int dims_out[5]);
+
+/* Forward projection P^theta for every angle (problem statement before Eq. 1):
+ * y = P f with P the exact intersection-length (Siddon) operator, y[ray] =
+ * sum_j |ray ∩ voxel_j| f_j.  f_dev: volume; y_dev: sinogram (written). */
+cbct_status cbct_project(cbct_geometry *geom, const float *f_dev, float *y_dev, cudaStream_t stream);
+
+/* Adjoint f = P^T y: the exact matrix transpose of cbct_project, i.e. the
+ * sum over theta of P^theta^T named before Eq. 2, computed voxel by voxel as a
+ * gather over the rays that meet each voxel (the voxel-driven form of Eq. 2) with
+ * the same intersection lengths, in a fixed order and without atomics.
+ * y_dev: sinogram; f_dev: volume (written). */
+cbct_status cbct_backproject(cbct_geometry *geom, const float *y_dev, float *f_dev, cudaStream_t stream);
+
+/* Steps 2 and 3 of Algorithm A1 on the geometry's grid: inner_iters projected
+ * gradient steps on TV_eps(f) + beta/2 |f - g|^2 over f >= 0, starting from the
+ * volume in f_inout_dev, step 1/(beta + (4/eps) sum_d h_d^-2).  TV_eps is the
+ * isotropic forward-difference TV with Neumann boundary, sqrt(|grad f|^2 + eps^2)
+ * per voxel (E1 of Eq. 1).  Every output voxel is >= +0.0.  g_dev: volume. */
+cbct_status cbct_tv_prox(cbct_geometry *geom, const float *g_dev, float *f_inout_dev, double beta,
+                         double eps, int inner_iters, cudaStream_t stream);
+
+/* Algorithm A1 on a single grid (the geometry's own), `iters` iterations from the
+ * volume in f_inout_dev:
+ *   g = f - (gamma/beta) P^T (P f - Y),  gamma = 2 mu Nv / (n_angles nu nv)
+ *   f = step 2 and 3 as in cbct_tv_prox (clamp_mode as in cbct_options)
+ * beta must be > 0 (no automatic choice here).  Y_dev: measured sinogram.
+ * energy_trace: optional host [iters][3] (E, E1, mu*E2 of each entering iterate;
+ * synchronises the stream once at the end). */
+cbct_status cbct_fbs(cbct_geometry *geom, const float *Y_dev, double mu, double beta, double eps,
+                     int inner_iters, int clamp_mode, int iters, float *f_inout_dev,
+                     double *energy_trace, cudaStream_t stream);
+
+/* Largest eigenvalue of P^T P by `iters` power iterations from the all-ones volume;
+ * the estimate is the Rayleigh quotient of the last normalised iterate.  Writes
+ * *lambda_out (host) and synchronises the stream. */
+cbct_status cbct_power_iteration(cbct_geometry *geom, int iters, double *lambda_out, cudaStream_t stream);
+
+/* Energy of Eq. 1 on the grid, float64: out_host = {E, E1, mu*E2} with
+ * E1 = TV_eps(f) / Nv and E2 = |P f - Y|^2 / (n_angles nu nv).  Synchronises. */
+cbct_status cbct_energy(cbct_geometry *geom, const float *Y_dev, const float *f_dev, double mu,
+                        double eps, double out_host[3], cudaStream_t stream);
+
+/* Full reconstruction (Eq. 1 by Algorithm A1 with multigrid): for level
+ * l = levels-1 .. 0 (coarsest first) the data are the 2x2-binned sinogram of the
+ * finer level, the start is 0 on the coarsest level and the cell-centred trilinear
+ * prolongation of the coarser result elsewhere, and `iters` iterations of A1 run
+ * per level.  angles_host must equal the geometry's angles (n_angles of them).
+ * Y_dev: measured sinogram of the finest level; f_out_dev: volume (written).
+ * levels >= 1 with n >= 2^(levels-1) on every axis of volume and imager. */
+cbct_status cbct_reconstruct(cbct_geometry *geom, const float *Y_dev, const double *angles_host,
+                             int n_angles, double mu, int iters, int levels, const cbct_options *opts,
+                             float *f_out_dev, cudaStream_t stream);
+
+/* Multigrid transfers on caller buffers (layouts as above).
+ * cbct_restrict_sino: y_coarse[t][b][a] = mean of y over the existing pixels of
+ *   the 2x2 block {2b, 2b+1} x {2a, 2a+1}; output [n_angles][ceil nv/2][ceil nu/2].
+ * cbct_prolong_vol: cell-centred trilinear interpolation of the coarse volume
+ *   (spacing 2h) at the fine voxel centres, indices clamped at the edges. */
+cbct_status cbct_restrict_sino(int n_angles, int nv, int nu, const float *y_dev, float *y_coarse_dev,
+                               cudaStream_t stream);
+cbct_status cbct_prolong_vol(int nxc, int nyc, int nzc, const float *fc_dev, int nx, int ny, int nz,
+                             float *f_dev, cudaStream_t stream);
+
+/* Thread-local description of the last error on the calling thread. */
+const char *cbct_last_error(void);
+
+/* Library version string. */
+const char *cbct_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CBCT_H */

@@ -295,16 +295,22 @@ double or_backproject_voxel(const or_geom *g, const double *y, int i, int j, int
 {
     double lo[3] = {(-0.5 * g->nx + i) * g->hx, (-0.5 * g->ny + j) * g->hy, (-0.5 * g->nz + k) * g->hz};
     double hi[3] = {lo[0] + g->hx, lo[1] + g->hy, lo[2] + g->hz};
-    double total = 0.0;
-#pragma omp parallel for reduction(+ : total) schedule(static)
-    for (int ia = 0; ia < g->na; ++ia)
+    double *per_view = (double *)calloc(g->na, sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int ia = 0; ia < g->na; ++ia) {
+        double s = 0.0;
         for (int b = 0; b < g->nv; ++b)
             for (int a = 0; a < g->nu; ++a) {
                 double S[3], P[3];
                 ray_endpoints(g, ia, b, a, S, P);
                 double L = box_length(S, P, lo, hi);
-                if (L > 0.0) total += L * y[((long)ia * g->nv + b) * g->nu + a];
+                if (L > 0.0) s += L * y[((long)ia * g->nv + b) * g->nu + a];
             }
+        per_view[ia] = s;
+    }
+    double total = 0.0;
+    for (int ia = 0; ia < g->na; ++ia) total += per_view[ia];
+    free(per_view);
     return total;
 }
 
@@ -338,18 +344,24 @@ static void grad_at(const or_vol *v, const double *f, int i, int j, int k, doubl
     out[2] = k < v->nz - 1 ? (f[VIDX(v, i, j, k + 1)] - c) / v->hz : 0.0;
 }
 
-/* TV_eps(f) = sum_j sqrt(|grad f|_j^2 + eps^2). */
+/* TV_eps(f) = sum_j sqrt(|grad f|_j^2 + eps^2), summed slice by slice in a fixed order. */
 double or_tv(const or_vol *v, const double *f, double eps)
 {
-    double total = 0.0;
-#pragma omp parallel for reduction(+ : total) schedule(static)
-    for (int k = 0; k < v->nz; ++k)
+    double *slice = (double *)calloc(v->nz, sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < v->nz; ++k) {
+        double s = 0.0;
         for (int j = 0; j < v->ny; ++j)
             for (int i = 0; i < v->nx; ++i) {
                 double gr[3];
                 grad_at(v, f, i, j, k, gr);
-                total += sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2] + eps * eps);
+                s += sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2] + eps * eps);
             }
+        slice[k] = s;
+    }
+    double total = 0.0;
+    for (int k = 0; k < v->nz; ++k) total += slice[k];
+    free(slice);
     return total;
 }
 

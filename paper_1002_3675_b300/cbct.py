@@ -1,0 +1,258 @@
+"""Thin Python binding of the C ABI in ``include/cbct.h`` (argument marshalling only).
+
+Every function has the name of the C entry point it calls.  Tensors are torch CUDA
+float32 tensors in the ABI's layouts (volumes [nz][ny][nx], sinograms
+[n_angles][nv][nu]); work is enqueued on torch's current CUDA stream.  A non-OK
+status raises ``CbctError`` carrying ``cbct_last_error()``.  There is no fallback:
+if the shared library cannot be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "cbct.h")
+
+NUM_KERNEL_CLASSES = 5
+KERNEL_CLASSES = ("project", "backproject", "tv", "reduce", "transfer")
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "UNSUPPORTED", 6: "BUSY"}
+
+
+class CbctError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"cbct status {status} ({STATUS.get(status, '?')}): {msg}")
+        self.status = status
+
+
+class GeometryDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("hx", C.c_double), ("hy", C.c_double), ("hz", C.c_double),
+                ("nu", C.c_int), ("nv", C.c_int), ("du", C.c_double), ("dv", C.c_double),
+                ("dso", C.c_double), ("dsd", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("beta", C.c_double), ("betas", C.POINTER(C.c_double)), ("eps", C.c_double),
+                ("inner_iters", C.c_int), ("clamp_mode", C.c_int), ("sino_fp16", C.c_int),
+                ("power_iters", C.c_int), ("start_level", C.c_int), ("f_init_dev", C.c_void_p),
+                ("use_graphs", C.c_int), ("energy_trace", C.POINTER(C.c_double)),
+                ("beta_out", C.POINTER(C.c_double)), ("kernel_ms", C.POINTER(C.c_float)),
+                ("kernel_launches", C.POINTER(C.c_int))]
+
+
+def _load() -> C.CDLL:
+    path = _build.build()          # compiles in-tree if missing or stale; raises on failure
+    return C.CDLL(path)
+
+
+lib = _load()
+_P, _D, _I, _V = C.c_void_p, C.c_double, C.c_int, C.c_void_p
+_SIGS = {
+    "cbct_geometry_create": [C.POINTER(GeometryDesc), C.POINTER(C.c_double), _I, C.POINTER(C.c_void_p)],
+    "cbct_geometry_destroy": [_P],
+    "cbct_level_dims": [_P, _I, C.POINTER(C.c_int)],
+    "cbct_project": [_P, _P, _P, _V],
+    "cbct_backproject": [_P, _P, _P, _V],
+    "cbct_tv_prox": [_P, _P, _P, _D, _D, _I, _V],
+    "cbct_fbs": [_P, _P, _D, _D, _D, _I, _I, _I, _P, C.POINTER(C.c_double), _V],
+    "cbct_power_iteration": [_P, _I, C.POINTER(C.c_double), _V],
+    "cbct_energy": [_P, _P, _P, _D, _D, C.POINTER(C.c_double), _V],
+    "cbct_reconstruct": [_P, _P, C.POINTER(C.c_double), _I, _D, _I, _I, C.POINTER(Options), _P, _V],
+    "cbct_restrict_sino": [_I, _I, _I, _P, _P, _V],
+    "cbct_prolong_vol": [_I, _I, _I, _P, _I, _I, _I, _P, _V],
+    "cbct_last_error": [],
+    "cbct_version": [],
+}
+for _name, _args in _SIGS.items():
+    _fn = getattr(lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = C.c_char_p if _name in ("cbct_last_error", "cbct_version") else (
+        None if _name == "cbct_geometry_destroy" else C.c_int)
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions declared in the C header."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cbct_[a-z0-9_]+)\s*\(", text)))
+
+
+def cbct_last_error() -> str:
+    return lib.cbct_last_error().decode()
+
+
+def cbct_version() -> str:
+    return lib.cbct_version().decode()
+
+
+def _check(status: int):
+    if status != 0:
+        raise CbctError(status, cbct_last_error())
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, name):
+    import torch
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Geometry:
+    """Owning wrapper of a ``cbct_geometry`` handle."""
+
+    def __init__(self, handle, desc: GeometryDesc, angles: np.ndarray):
+        self.handle = handle
+        self.desc = desc
+        self.angles = angles
+
+    @property
+    def vol_shape(self):
+        return (self.desc.nz, self.desc.ny, self.desc.nx)
+
+    @property
+    def sino_shape(self):
+        return (len(self.angles), self.desc.nv, self.desc.nu)
+
+    def close(self):
+        if self.handle:
+            lib.cbct_geometry_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_desc(geom: dict) -> GeometryDesc:
+    return GeometryDesc(geom["nx"], geom["ny"], geom["nz"], geom["hx"], geom["hy"], geom["hz"],
+                        geom["nu"], geom["nv"], geom["du"], geom["dv"], geom["dso"], geom["dsd"])
+
+
+def cbct_geometry_create(geom: dict) -> Geometry:
+    desc = make_desc(geom)
+    ang = np.ascontiguousarray(geom["angles"], dtype=np.float64)
+    h = C.c_void_p()
+    _check(lib.cbct_geometry_create(C.byref(desc), ang.ctypes.data_as(C.POINTER(C.c_double)), len(ang),
+                                    C.byref(h)))
+    return Geometry(h, desc, ang)
+
+
+def cbct_level_dims(g: Geometry, level: int):
+    out = (C.c_int * 5)()
+    _check(lib.cbct_level_dims(g.handle, level, out))
+    return tuple(out)
+
+
+def _empty(shape, like=None):
+    import torch
+    return torch.empty(shape, dtype=torch.float32, device="cuda")
+
+
+def cbct_project(g: Geometry, f, y=None):
+    y = _empty(g.sino_shape) if y is None else y
+    _check(lib.cbct_project(g.handle, _ptr(f, "f"), _ptr(y, "y"), _stream()))
+    return y
+
+
+def cbct_backproject(g: Geometry, y, f=None):
+    f = _empty(g.vol_shape) if f is None else f
+    _check(lib.cbct_backproject(g.handle, _ptr(y, "y"), _ptr(f, "f"), _stream()))
+    return f
+
+
+def cbct_tv_prox(g: Geometry, gvol, f, beta: float, eps: float, inner_iters: int):
+    _check(lib.cbct_tv_prox(g.handle, _ptr(gvol, "g"), _ptr(f, "f"), beta, eps, inner_iters, _stream()))
+    return f
+
+
+def cbct_fbs(g: Geometry, Y, mu, beta, eps, inner_iters, clamp_mode, iters, f, trace=False):
+    tr = np.zeros((max(iters, 1), 3)) if trace else None
+    _check(lib.cbct_fbs(g.handle, _ptr(Y, "Y"), mu, beta, eps, inner_iters, clamp_mode, iters, _ptr(f, "f"),
+                        tr.ctypes.data_as(C.POINTER(C.c_double)) if trace else None, _stream()))
+    return (f, tr[:iters]) if trace else f
+
+
+def cbct_power_iteration(g: Geometry, iters: int = 30) -> float:
+    lam = C.c_double()
+    _check(lib.cbct_power_iteration(g.handle, iters, C.byref(lam), _stream()))
+    return lam.value
+
+
+def cbct_energy(g: Geometry, Y, f, mu, eps):
+    out = (C.c_double * 3)()
+    _check(lib.cbct_energy(g.handle, _ptr(Y, "Y"), _ptr(f, "f"), mu, eps, out, _stream()))
+    return np.array(out[:])
+
+
+def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=None, *, beta=0.0,
+                     betas=None, eps=0.0, inner_iters=0, clamp_mode=0, sino_fp16=False, power_iters=0,
+                     f_init=None, start_level=0, use_graphs=False, trace=False, kernel_times=False):
+    """Returns f_out, or (f_out, info) when trace/kernel_times is requested; info holds
+    'trace' [levels][iters][3], 'betas' [levels], 'kernel_ms'/'kernel_launches'."""
+    f_out = _empty(g.vol_shape) if f_out is None else f_out
+    o = Options()
+    o.beta = beta
+    bet = np.ascontiguousarray(betas, dtype=np.float64) if betas is not None else None
+    if bet is not None:
+        o.betas = bet.ctypes.data_as(C.POINTER(C.c_double))
+    o.eps = eps
+    o.inner_iters = inner_iters
+    o.clamp_mode = clamp_mode
+    o.sino_fp16 = int(bool(sino_fp16))
+    o.power_iters = power_iters
+    o.start_level = start_level
+    o.f_init_dev = _ptr(f_init, "f_init") if f_init is not None else None
+    o.use_graphs = int(bool(use_graphs))
+    tr = np.full((levels, max(iters, 1), 3), np.nan) if trace else None
+    if trace:
+        o.energy_trace = tr.ctypes.data_as(C.POINTER(C.c_double))
+    bo = np.zeros(levels)
+    o.beta_out = bo.ctypes.data_as(C.POINTER(C.c_double))
+    km = (C.c_float * NUM_KERNEL_CLASSES)() if kernel_times else None
+    kl = (C.c_int * NUM_KERNEL_CLASSES)() if kernel_times else None
+    if kernel_times:
+        o.kernel_ms = km
+        o.kernel_launches = kl
+    _check(lib.cbct_reconstruct(g.handle, _ptr(Y, "Y"), g.angles.ctypes.data_as(C.POINTER(C.c_double)),
+                                len(g.angles), mu, iters, levels, C.byref(o), _ptr(f_out, "f_out"), _stream()))
+    if not (trace or kernel_times):
+        return f_out
+    info = {"betas": bo}
+    if trace:
+        info["trace"] = tr[:, :iters]
+    if kernel_times:
+        info["kernel_ms"] = dict(zip(KERNEL_CLASSES, list(km)))
+        info["kernel_launches"] = dict(zip(KERNEL_CLASSES, list(kl)))
+    return f_out, info
+
+
+def cbct_restrict_sino(y):
+    import torch
+    na, nv, nu = y.shape
+    out = torch.empty((na, (nv + 1) // 2, (nu + 1) // 2), dtype=torch.float32, device=y.device)
+    _check(lib.cbct_restrict_sino(na, nv, nu, _ptr(y, "y"), _ptr(out, "out"), _stream()))
+    return out
+
+
+def cbct_prolong_vol(fc, shape):
+    import torch
+    nzc, nyc, nxc = fc.shape
+    nz, ny, nx = shape
+    out = torch.empty(shape, dtype=torch.float32, device=fc.device)
+    _check(lib.cbct_prolong_vol(nxc, nyc, nzc, _ptr(fc, "fc"), nx, ny, nz, _ptr(out, "out"), _stream()))
+    return out

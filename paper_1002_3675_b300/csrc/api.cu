@@ -1,0 +1,684 @@
+// C ABI of the library and the solver driver: Algorithm A1 (forward-backward
+// splitting) of Jia et al. (2010) for E1 + mu E2 with f >= 0 (Eq. 1), on each level
+// of a coarse-to-fine multigrid.
+//
+// Discrete scaling (the paper's functional derivatives on the voxel grid): with
+// V = Nv dV and A = Np du dv, multiplying Eq. 1 by Nv gives
+//   Nv E = TV_eps(f) + (gamma / 2) |P f - Y|^2,  gamma = 2 mu Nv / (n_angles Np),
+// and step 1 becomes g = f - (gamma / beta) P^T (P f - Y); the 1/V of E1 and of E3
+// cancel, so beta is the paper's beta.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "cbct_internal.h"
+
+using namespace cbct;
+
+namespace cbct {
+const char *last_error();
+}
+
+namespace {
+
+#define CK(call, what)                                       \
+    do {                                                     \
+        cudaError_t e__ = (call);                            \
+        if (e__ != cudaSuccess) return cuda_fail(e__, what); \
+    } while (0)
+
+#define ST(call)                          \
+    do {                                  \
+        cbct_status s__ = (call);         \
+        if (s__ != CBCT_OK) return s__;   \
+    } while (0)
+
+bool aligned16(const void *p) { return p && (((uintptr_t)p) & 15u) == 0; }
+
+cbct_status need_ptr(const void *p, const char *name) {
+    if (!aligned16(p)) {
+        set_error("%s must be a non-null 16-byte aligned device pointer", name);
+        return CBCT_ERR_INVALID_ARG;
+    }
+    return CBCT_OK;
+}
+
+// Per-call timing of kernel classes with CUDA events on the caller's stream.
+struct Prof {
+    cbct_geometry *G = nullptr;
+    cudaStream_t s = 0;
+    bool on = false;
+    std::vector<int> cls;
+    std::vector<cudaEvent_t> a, b;
+    void begin(int c) {
+        if (!on) return;
+        cudaEvent_t e0 = G->events.get();
+        cudaEventRecord(e0, s);
+        a.push_back(e0);
+        cls.push_back(c);
+    }
+    void end() {
+        if (!on) return;
+        cudaEvent_t e1 = G->events.get();
+        cudaEventRecord(e1, s);
+        b.push_back(e1);
+    }
+    cbct_status collect(float *ms, int *cnt) {
+        if (!on) return CBCT_OK;
+        CK(cudaStreamSynchronize(s), "synchronising for kernel timing");
+        for (int c = 0; c < CBCT_NUM_KERNEL_CLASSES; ++c) {
+            if (ms) ms[c] = 0.f;
+            if (cnt) cnt[c] = 0;
+        }
+        for (size_t q = 0; q < cls.size() && q < b.size(); ++q) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, a[q], b[q]);
+            if (ms) ms[cls[q]] += t;
+            if (cnt) cnt[cls[q]] += 1;
+        }
+        G->events.release_all();
+        return CBCT_OK;
+    }
+};
+
+struct Launch {  // wraps one kernel launch with optional timing
+    Prof &p;
+    int c;
+    Launch(Prof &pp, int cc) : p(pp), c(cc) { p.begin(c); }
+    ~Launch() { p.end(); }
+};
+
+double default_eps(const Level *L) { return 2e-5 / std::min(L->hx, std::min(L->hy, L->hz)); }
+
+double tv_lipschitz(const Level *L, double eps) {
+    return 4.0 / eps * (1.0 / (L->hx * L->hx) + 1.0 / (L->hy * L->hy) + 1.0 / (L->hz * L->hz));
+}
+
+double gamma_of(const Level *L, double mu) {
+    return 2.0 * mu * (double)vol_elems(L->gd) / (double)sino_elems(L->gd);
+}
+
+cbct_status ensure_trace(cbct_geometry *G, size_t n) {
+    if (!G->dscalars) {
+        // layout: [0..63] scalars (lambda etc.), counter separately
+        if (cudaMalloc(&G->dscalars, sizeof(double) * 64) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaMalloc of scalar scratch failed");
+            return CBCT_ERR_OOM;
+        }
+        if (cudaMalloc(&G->dcounter, sizeof(int) * 4) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaMalloc of counter failed");
+            return CBCT_ERR_OOM;
+        }
+    }
+    (void)n;
+    return CBCT_OK;
+}
+
+struct SolveParams {
+    float c;        // gamma / beta
+    float s;        // inner step 1 / (beta + L_TV)
+    float beta;
+    float eps2;
+    int M;
+    int clamp_mode;
+    bool fp16;
+    double inv_nv, mu_over_nr;
+};
+
+TvArgs tv_args(const Level *L, const SolveParams &P) {
+    TvArgs a;
+    a.nx = L->nx;
+    a.ny = L->ny;
+    a.nz = L->nz;
+    a.ihx = (float)(1.0 / L->hx);
+    a.ihy = (float)(1.0 / L->hy);
+    a.ihz = (float)(1.0 / L->hz);
+    a.s = P.s;
+    a.beta = P.beta;
+    a.eps2 = P.eps2;
+    return a;
+}
+
+// Steps 2 and 3: M sweeps from src0 into L->f (ping-pong through A and B).
+// partial_e1 (optional) receives the E1 partials of the first sweep's input.
+cbct_status enqueue_prox(Level *L, const SolveParams &P, const float *src0, double *partial_e1, int *ne1,
+                         Prof &prof, cudaStream_t s) {
+    const TvArgs ta = tv_args(L, P);
+    const float *src = src0;
+    for (int m = 0; m < P.M; ++m) {
+        const bool last = m == P.M - 1;
+        float *dst = last ? L->f : (m % 2 == 0 ? L->A : L->B);
+        if (dst == src) dst = L->A;  // M == 1 in place: go through A
+        const bool clamp = P.clamp_mode == 0 || last;
+        {
+            Launch l(prof, CBCT_K_TV);
+            CK(launch_tv_sweep(ta, src, L->g, dst, clamp, m == 0 ? partial_e1 : nullptr, s, m == 0 ? ne1 : nullptr),
+               "tv sweep");
+        }
+        src = dst;
+    }
+    if (src != L->f) CK(cudaMemcpyAsync(L->f, src, vol_elems(L->gd) * 4, cudaMemcpyDeviceToDevice, s), "copy");
+    return CBCT_OK;
+}
+
+// One iteration of Algorithm A1 on level L (state in L->f).
+cbct_status enqueue_iteration(cbct_geometry *G, Level *L, const SolveParams &P, double *dtrace, Prof &prof,
+                              cudaStream_t s) {
+    const GeoDev &gd = L->gd;
+    double *pp = L->partial;
+    const size_t np = project_partials(gd);
+    double *pt = L->partial + np;
+    int nb_p = 0, nb_t = 0;
+    if (P.clamp_mode == 1) {
+        // the prox starts from g, so E1 of f_k needs its own pass
+        Launch l(prof, CBCT_K_REDUCE);
+        CK(launch_tv_energy(tv_args(L, P), L->f, pt, s, &nb_t), "tv energy");
+    }
+    {
+        Launch l(prof, CBCT_K_PROJECT);
+        CK(launch_project(gd, L->f, P.fp16 ? nullptr : L->Y, P.fp16 ? L->Yh : nullptr, L->rs, pp,
+                          P.fp16 ? PROJ_RESID16 : PROJ_RESID32, s, &nb_p),
+           "projection");
+    }
+    {
+        Launch l(prof, CBCT_K_BACKPROJECT);
+        CK(launch_backproject(gd, L->rs, L->f, L->g, P.c, BP_STEP, s), "backprojection");
+    }
+    ST(enqueue_prox(L, P, P.clamp_mode == 0 ? L->f : L->g, P.clamp_mode == 0 ? pt : nullptr,
+                    P.clamp_mode == 0 ? &nb_t : nullptr, prof, s));
+    {
+        Launch l(prof, CBCT_K_REDUCE);
+        CK(launch_energy_finalize(pp, nb_p, pt, nb_t, P.inv_nv, P.mu_over_nr, dtrace, G->dcounter, s),
+           "energy reduction");
+    }
+    return CBCT_OK;
+}
+
+// `iters` iterations of A1 on level L; trace values land in dtrace[0 .. 3*iters).
+cbct_status run_level(cbct_geometry *G, Level *L, const SolveParams &P, int iters, double *dtrace, bool graphs,
+                      Prof &prof, cudaStream_t s) {
+    CK(cudaMemsetAsync(G->dcounter, 0, sizeof(int), s), "counter reset");
+    if (graphs && !prof.on && s != 0 && iters > 1) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cbct_status st = enqueue_iteration(G, L, P, dtrace, prof, s);
+            cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+            if (st != CBCT_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            if (e2 != cudaSuccess) return cuda_fail(e2, "graph capture");
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            if (e != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                return cuda_fail(e, "graph instantiate");
+            }
+            for (int it = 0; it < iters && e == cudaSuccess; ++it) e = cudaGraphLaunch(exec, s);
+            cudaGraphExecDestroy(exec);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+            return CBCT_OK;
+        }
+        cudaGetLastError();  // capture not possible on this stream: run eagerly
+    }
+    for (int it = 0; it < iters; ++it) ST(enqueue_iteration(G, L, P, dtrace, prof, s));
+    return CBCT_OK;
+}
+
+// lambda_max(P^T P) by K power iterations from the normalised all-ones volume.
+cbct_status power_iteration(cbct_geometry *G, Level *L, int K, double *lam, Prof &prof, cudaStream_t s) {
+    const GeoDev &gd = L->gd;
+    const size_t nv = vol_elems(gd);
+    float *x = L->A, *y = L->B;
+    double *dlam = G->dscalars;
+    float *dscale = (float *)(G->dscalars + 1);
+    {
+        Launch l(prof, CBCT_K_REDUCE);
+        CK(launch_fill(x, (float)(1.0 / sqrt((double)nv)), nv, s), "fill");
+    }
+    for (int it = 0; it < K; ++it) {
+        {
+            Launch l(prof, CBCT_K_PROJECT);
+            CK(launch_project(gd, x, nullptr, nullptr, L->rs, nullptr, PROJ_SCALED, s, nullptr), "projection");
+        }
+        {
+            Launch l(prof, CBCT_K_BACKPROJECT);
+            CK(launch_backproject(gd, L->rs, nullptr, y, 0.f, BP_PLAIN, s), "backprojection");
+        }
+        int nb = 0;
+        Launch l(prof, CBCT_K_REDUCE);
+        CK(launch_dot2(x, y, nv, L->partial, s, &nb), "dot");
+        CK(launch_power_finalize(L->partial, nb, dlam, dscale, s), "power finalize");
+        CK(launch_scale(y, dscale, x, nv, s), "scale");
+    }
+    CK(cudaMemcpyAsync(lam, dlam, sizeof(double), cudaMemcpyDeviceToHost, s), "lambda copy");
+    CK(cudaStreamSynchronize(s), "power iteration");
+    return CBCT_OK;
+}
+
+cbct_status check_geometry_desc(const cbct_geometry_desc *d) {
+    if (!d) {
+        set_error("desc is null");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1 || d->nu < 1 || d->nv < 1) {
+        set_error("sizes must be >= 1");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    if (!(d->hx > 0) || !(d->hy > 0) || !(d->hz > 0) || !(d->du > 0) || !(d->dv > 0) || !(d->dso > 0) ||
+        !(d->dsd > 0)) {
+        set_error("spacings and distances must be > 0");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    if ((double)d->nx * d->ny * d->nz >= 2147483647.0) {
+        set_error("volume must have fewer than 2^31 voxels");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    if (d->ny > 65535) {
+        set_error("ny must be <= 65535");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    return CBCT_OK;
+}
+
+}  // namespace
+
+// Device energy-trace buffer owned by the geometry (grown on demand).
+static cbct_status get_trace(cbct_geometry *G, size_t n, double **out) {
+    if (G->dtrace_len < n) {
+        cudaFree(G->dtrace);
+        G->dtrace = nullptr;
+        G->dtrace_len = 0;
+        if (cudaMalloc(&G->dtrace, n * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaMalloc of energy trace failed");
+            return CBCT_ERR_OOM;
+        }
+        G->dtrace_len = n;
+    }
+    *out = G->dtrace;
+    return CBCT_OK;
+}
+
+extern "C" {
+
+const char *cbct_last_error(void) { return cbct::last_error(); }
+
+const char *cbct_version(void) { return "cbct-fbs-b300 0.1 (sm_103a)"; }
+
+cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, const double *angles_host, int n_angles,
+                                 cbct_geometry **out) {
+    if (!out) {
+        set_error("out is null");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    ST(check_geometry_desc(desc));
+    if (!angles_host || n_angles < 1 || n_angles > 65535) {
+        set_error("need 1..65535 angles");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    if ((double)n_angles * desc->nu * desc->nv >= 2147483647.0) {
+        set_error("sinogram must have fewer than 2^31 pixels");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    for (int q = 0; q < n_angles; ++q)
+        if (!isfinite(angles_host[q])) {
+            set_error("angle %d is not finite", q);
+            return CBCT_ERR_INVALID_ARG;
+        }
+    cbct_geometry *G = new cbct_geometry();
+    G->desc = *desc;
+    G->angles.assign(angles_host, angles_host + n_angles);
+    if (cudaGetDevice(&G->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete G;
+        set_error("no CUDA device available");
+        return CBCT_ERR_CUDA;
+    }
+    Level *L = nullptr;
+    cbct_status st = ensure_level(G, 0, &L);
+    if (st == CBCT_OK) st = ensure_trace(G, 0);
+    if (st != CBCT_OK) {
+        cbct_geometry_destroy(G);
+        return st;
+    }
+    *out = G;
+    return CBCT_OK;
+}
+
+void cbct_geometry_destroy(cbct_geometry *G) {
+    if (!G) return;
+    for (auto *L : G->levels) free_level(L);
+    cudaFree(G->dscalars);
+    cudaFree(G->dcounter);
+    cudaFree(G->io_vol);
+    cudaFree(G->dtrace);
+    delete G;
+}
+
+cbct_status cbct_level_dims(const cbct_geometry *G, int level, int dims_out[5]) {
+    if (!G || !dims_out || level < 0 || level > 12) {
+        set_error("bad arguments to cbct_level_dims");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    const int s = 1 << level;
+    const cbct_geometry_desc &d = G->desc;
+    dims_out[0] = (d.nx + s - 1) / s;
+    dims_out[1] = (d.ny + s - 1) / s;
+    dims_out[2] = (d.nz + s - 1) / s;
+    dims_out[3] = (d.nu + s - 1) / s;
+    dims_out[4] = (d.nv + s - 1) / s;
+    return CBCT_OK;
+}
+
+cbct_status cbct_project(cbct_geometry *G, const float *f_dev, float *y_dev, cudaStream_t s) {
+    if (!G) {
+        set_error("geometry is null");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    ST(need_ptr(f_dev, "f_dev"));
+    ST(need_ptr(y_dev, "y_dev"));
+    Level *L;
+    ST(ensure_level(G, 0, &L));
+    ST(ensure_workspace(L, false));
+    const GeoDev &g = L->gd;
+    CK(launch_vol_to_internal(f_dev, L->A, g.nx, g.ny, g.nz, s), "volume layout");
+    CK(launch_project(g, L->A, nullptr, nullptr, L->rs, nullptr, PROJ_PLAIN, s, nullptr), "projection");
+    CK(launch_sino_to_api(L->rs, y_dev, g.na, g.nu, g.nv, s), "sinogram layout");
+    return CBCT_OK;
+}
+
+cbct_status cbct_backproject(cbct_geometry *G, const float *y_dev, float *f_dev, cudaStream_t s) {
+    if (!G) {
+        set_error("geometry is null");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    ST(need_ptr(y_dev, "y_dev"));
+    ST(need_ptr(f_dev, "f_dev"));
+    Level *L;
+    ST(ensure_level(G, 0, &L));
+    ST(ensure_workspace(L, false));
+    const GeoDev &g = L->gd;
+    CK(launch_sino_to_internal(y_dev, L->rs, nullptr, g.ray_z, g.na, g.nu, g.nv, s), "sinogram layout");
+    CK(launch_backproject(g, L->rs, nullptr, L->A, 0.f, BP_PLAIN, s), "backprojection");
+    CK(launch_vol_to_api(L->A, f_dev, g.nx, g.ny, g.nz, s), "volume layout");
+    return CBCT_OK;
+}
+
+static cbct_status solve_params(const Level *L, double mu, double beta, double eps, int M, int clamp_mode, bool fp16,
+                                SolveParams *P) {
+    if (!(beta > 0) || !isfinite(beta)) {
+        set_error("beta must be > 0");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    if (!(eps > 0) || !isfinite(eps)) {
+        set_error("eps must be > 0");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    if (M < 1 || M > 10000) {
+        set_error("inner_iters must be in 1..10000");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    if (clamp_mode != 0 && clamp_mode != 1) {
+        set_error("clamp_mode must be 0 or 1");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    const double gam = gamma_of(L, mu);
+    P->c = (float)(gam / beta);
+    P->s = (float)(1.0 / (beta + tv_lipschitz(L, eps)));
+    P->beta = (float)beta;
+    P->eps2 = (float)(eps * eps);
+    P->M = M;
+    P->clamp_mode = clamp_mode;
+    P->fp16 = fp16;
+    P->inv_nv = 1.0 / (double)vol_elems(L->gd);
+    P->mu_over_nr = mu / (double)sino_elems(L->gd);
+    return CBCT_OK;
+}
+
+cbct_status cbct_tv_prox(cbct_geometry *G, const float *g_dev, float *f_inout_dev, double beta, double eps,
+                         int inner_iters, cudaStream_t s) {
+    if (!G) {
+        set_error("geometry is null");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    ST(need_ptr(g_dev, "g_dev"));
+    ST(need_ptr(f_inout_dev, "f_inout_dev"));
+    Level *L;
+    ST(ensure_level(G, 0, &L));
+    ST(ensure_workspace(L, false));
+    SolveParams P;
+    ST(solve_params(L, 1.0, beta, eps, inner_iters, 0, false, &P));
+    const GeoDev &g = L->gd;
+    CK(launch_vol_to_internal(g_dev, L->g, g.nx, g.ny, g.nz, s), "volume layout");
+    CK(launch_vol_to_internal(f_inout_dev, L->f, g.nx, g.ny, g.nz, s), "volume layout");
+    Prof prof;
+    ST(enqueue_prox(L, P, L->f, nullptr, nullptr, prof, s));
+    CK(launch_vol_to_api(L->f, f_inout_dev, g.nx, g.ny, g.nz, s), "volume layout");
+    return CBCT_OK;
+}
+
+cbct_status cbct_fbs(cbct_geometry *G, const float *Y_dev, double mu, double beta, double eps, int inner_iters,
+                     int clamp_mode, int iters, float *f_inout_dev, double *energy_trace, cudaStream_t s) {
+    if (!G) {
+        set_error("geometry is null");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    ST(need_ptr(Y_dev, "Y_dev"));
+    ST(need_ptr(f_inout_dev, "f_inout_dev"));
+    if (iters < 0 || !(mu > 0) || !isfinite(mu)) {
+        set_error("need iters >= 0 and mu > 0");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    Level *L;
+    ST(ensure_level(G, 0, &L));
+    ST(ensure_workspace(L, false));
+    SolveParams P;
+    ST(solve_params(L, mu, beta, eps, inner_iters, clamp_mode, false, &P));
+    double *dtrace;
+    ST(get_trace(G, 3 * (size_t)std::max(iters, 1), &dtrace));
+    const GeoDev &g = L->gd;
+    CK(launch_sino_to_internal(Y_dev, L->Y, nullptr, nullptr, g.na, g.nu, g.nv, s), "sinogram layout");
+    CK(launch_vol_to_internal(f_inout_dev, L->f, g.nx, g.ny, g.nz, s), "volume layout");
+    Prof prof;
+    ST(run_level(G, L, P, iters, dtrace, false, prof, s));
+    CK(launch_vol_to_api(L->f, f_inout_dev, g.nx, g.ny, g.nz, s), "volume layout");
+    if (energy_trace && iters > 0) {
+        CK(cudaMemcpyAsync(energy_trace, dtrace, 3 * sizeof(double) * iters, cudaMemcpyDeviceToHost, s), "trace");
+        CK(cudaStreamSynchronize(s), "fbs");
+    }
+    return CBCT_OK;
+}
+
+cbct_status cbct_power_iteration(cbct_geometry *G, int iters, double *lambda_out, cudaStream_t s) {
+    if (!G || !lambda_out || iters < 1) {
+        set_error("need a geometry, an output pointer and iters >= 1");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    Level *L;
+    ST(ensure_level(G, 0, &L));
+    ST(ensure_workspace(L, false));
+    Prof prof;
+    return power_iteration(G, L, iters, lambda_out, prof, s);
+}
+
+cbct_status cbct_energy(cbct_geometry *G, const float *Y_dev, const float *f_dev, double mu, double eps,
+                        double out_host[3], cudaStream_t s) {
+    if (!G || !out_host) {
+        set_error("null argument");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    ST(need_ptr(Y_dev, "Y_dev"));
+    ST(need_ptr(f_dev, "f_dev"));
+    Level *L;
+    ST(ensure_level(G, 0, &L));
+    ST(ensure_workspace(L, false));
+    SolveParams P;
+    ST(solve_params(L, mu, 1.0, eps, 1, 0, false, &P));
+    double *dtrace;
+    ST(get_trace(G, 3, &dtrace));
+    const GeoDev &g = L->gd;
+    CK(launch_sino_to_internal(Y_dev, L->Y, nullptr, nullptr, g.na, g.nu, g.nv, s), "sinogram layout");
+    CK(launch_vol_to_internal(f_dev, L->A, g.nx, g.ny, g.nz, s), "volume layout");
+    int nb_p = 0, nb_t = 0;
+    double *pp = L->partial, *pt = L->partial + project_partials(g);
+    CK(launch_project(g, L->A, L->Y, nullptr, L->rs, pp, PROJ_RESID32, s, &nb_p), "projection");
+    CK(launch_tv_energy(tv_args(L, P), L->A, pt, s, &nb_t), "tv energy");
+    CK(cudaMemsetAsync(G->dcounter, 0, sizeof(int), s), "counter");
+    CK(launch_energy_finalize(pp, nb_p, pt, nb_t, P.inv_nv, P.mu_over_nr, dtrace, G->dcounter, s), "energy");
+    CK(cudaMemcpyAsync(out_host, dtrace, 3 * sizeof(double), cudaMemcpyDeviceToHost, s), "energy copy");
+    CK(cudaStreamSynchronize(s), "energy");
+    return CBCT_OK;
+}
+
+cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double *angles_host, int n_angles,
+                             double mu, int iters, int levels, const cbct_options *opts, float *f_out_dev,
+                             cudaStream_t s) {
+    if (!G) {
+        set_error("geometry is null");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    ST(need_ptr(Y_dev, "Y_dev"));
+    ST(need_ptr(f_out_dev, "f_out_dev"));
+    if (!angles_host || n_angles != (int)G->angles.size()) {
+        set_error("angles must be the geometry's %d angles", (int)G->angles.size());
+        return CBCT_ERR_INVALID_ARG;
+    }
+    for (int q = 0; q < n_angles; ++q)
+        if (angles_host[q] != G->angles[q]) {
+            set_error("angle %d differs from the geometry's", q);
+            return CBCT_ERR_INVALID_ARG;
+        }
+    if (!(mu > 0) || !isfinite(mu) || iters < 0) {
+        set_error("need mu > 0 and iters >= 0");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    const cbct_geometry_desc &d = G->desc;
+    if (levels < 1 || levels > 8) {
+        set_error("levels must be in 1..8");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    const int need = 1 << (levels - 1);
+    if (d.nx < need || d.ny < need || d.nz < need || d.nu < need || d.nv < need) {
+        set_error("every volume and imager axis needs at least 2^(levels-1) = %d samples", need);
+        return CBCT_ERR_INVALID_ARG;
+    }
+    cbct_options o;
+    memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    const int M = o.inner_iters > 0 ? o.inner_iters : 10;
+    const int K = o.power_iters > 0 ? o.power_iters : 30;
+    const bool fp16 = o.sino_fp16 != 0;
+    int start = levels - 1;
+    if (o.f_init_dev) {
+        if (o.start_level < 0 || o.start_level >= levels) {
+            set_error("start_level must be in 0..levels-1");
+            return CBCT_ERR_INVALID_ARG;
+        }
+        ST(need_ptr(o.f_init_dev, "f_init_dev"));
+        start = o.start_level;
+    }
+
+    std::vector<Level *> Ls(levels);
+    for (int l = 0; l < levels; ++l) {
+        ST(ensure_level(G, l, &Ls[l]));
+        ST(ensure_workspace(Ls[l], fp16));
+    }
+    double *dtrace;
+    ST(get_trace(G, 3 * (size_t)std::max(iters, 1), &dtrace));
+    Prof prof;
+    prof.G = G;
+    prof.s = s;
+    prof.on = o.kernel_ms != nullptr || o.kernel_launches != nullptr;
+    if (prof.on) G->events.release_all();
+
+    // data pyramid: finest level from the caller's stack, coarser by 2x2 binning
+    {
+        Launch l(prof, CBCT_K_TRANSFER);
+        const GeoDev &g0 = Ls[0]->gd;
+        CK(launch_sino_to_internal(Y_dev, Ls[0]->Y, fp16 ? Ls[0]->Yh : nullptr, nullptr, g0.na, g0.nu, g0.nv, s),
+           "sinogram layout");
+    }
+    for (int l = 1; l < levels; ++l) {
+        Launch lz(prof, CBCT_K_TRANSFER);
+        const GeoDev &gp = Ls[l - 1]->gd;
+        CK(launch_restrict(Ls[l - 1]->Y, Ls[l]->Y, gp.na, gp.nu, gp.nv, s), "restriction");
+        if (fp16) CK(launch_to_half(Ls[l]->Y, Ls[l]->Yh, sino_elems(Ls[l]->gd), s), "half copy");
+    }
+
+    for (int l = start; l >= 0; --l) {
+        Level *L = Ls[l];
+        const GeoDev &g = L->gd;
+        if (l == start) {
+            Launch lz(prof, CBCT_K_TRANSFER);
+            if (o.f_init_dev)
+                CK(launch_vol_to_internal(o.f_init_dev, L->f, g.nx, g.ny, g.nz, s), "volume layout");
+            else
+                CK(cudaMemsetAsync(L->f, 0, vol_elems(g) * 4, s), "zero start");
+        } else {
+            Launch lz(prof, CBCT_K_TRANSFER);
+            const GeoDev &gc = Ls[l + 1]->gd;
+            CK(launch_prolong(Ls[l + 1]->f, gc.nx, gc.ny, gc.nz, L->f, g.nx, g.ny, g.nz, s), "prolongation");
+        }
+        double beta;
+        if (o.betas) {
+            beta = o.betas[l];
+        } else if (o.beta > 0) {
+            beta = o.beta;
+        } else {
+            double lam = 0.0;
+            ST(power_iteration(G, L, K, &lam, prof, s));
+            L->lambda = lam;
+            L->lambda_iters = K;
+            beta = std::max(10.0 * mu, 1.05 * gamma_of(L, mu) * lam);
+        }
+        if (o.beta_out) o.beta_out[l] = beta;
+        const double eps = o.eps > 0 ? o.eps : default_eps(L);
+        SolveParams P;
+        ST(solve_params(L, mu, beta, eps, M, o.clamp_mode, fp16, &P));
+        ST(run_level(G, L, P, iters, dtrace, o.use_graphs != 0, prof, s));
+        if (o.energy_trace && iters > 0) {
+            double *dst = o.energy_trace + 3 * (size_t)iters * (levels - 1 - l);
+            CK(cudaMemcpyAsync(dst, dtrace, 3 * sizeof(double) * iters, cudaMemcpyDeviceToHost, s), "trace");
+            CK(cudaStreamSynchronize(s), "trace sync");
+        }
+    }
+    {
+        Launch lz(prof, CBCT_K_TRANSFER);
+        const GeoDev &g0 = Ls[0]->gd;
+        CK(launch_vol_to_api(Ls[0]->f, f_out_dev, g0.nx, g0.ny, g0.nz, s), "volume layout");
+    }
+    return prof.collect(o.kernel_ms, o.kernel_launches);
+}
+
+cbct_status cbct_restrict_sino(int n_angles, int nv, int nu, const float *y_dev, float *y_coarse_dev,
+                               cudaStream_t s) {
+    if (n_angles < 1 || nv < 1 || nu < 1) {
+        set_error("sizes must be >= 1");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    ST(need_ptr(y_dev, "y_dev"));
+    ST(need_ptr(y_coarse_dev, "y_coarse_dev"));
+    CK(launch_restrict(y_dev, y_coarse_dev, n_angles, nv, nu, s), "restriction");
+    return CBCT_OK;
+}
+
+cbct_status cbct_prolong_vol(int nxc, int nyc, int nzc, const float *fc_dev, int nx, int ny, int nz, float *f_dev,
+                             cudaStream_t s) {
+    if (nxc < 1 || nyc < 1 || nzc < 1 || nx < 1 || ny < 1 || nz < 1) {
+        set_error("sizes must be >= 1");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    ST(need_ptr(fc_dev, "fc_dev"));
+    ST(need_ptr(f_dev, "f_dev"));
+    CK(launch_prolong(fc_dev, nzc, nyc, nxc, f_dev, nz, ny, nx, s), "prolongation");
+    return CBCT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,155 @@
+// Internal declarations of the sm_103a CBCT library (not part of the C ABI).
+//
+// Internal layouts (chosen for the kernels, converted at the ABI boundary):
+//   volume    float [nx][ny][nz]      (z fastest: a z-column is contiguous)
+//   sinogram  float [na][nu][nv]      (v fastest: a detector column is contiguous)
+// With these, the 32 lanes of a projector warp (32 consecutive detector rows of one
+// column) read neighbouring voxels of one z-column, and the 32 lanes of an adjoint
+// warp (32 consecutive voxels of one z-column) write contiguous outputs and read
+// contiguous residual rows.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cbct.h"
+
+namespace cbct {
+
+// Ray parameterisation shared by the projector and the adjoint.
+//
+// All rays of detector column a at view ia share one line in the xy-plane.  It is
+// parameterised by t, the horizontal distance (mm) from O, the foot of the
+// perpendicular from the rotation axis: p_xy(t) = O + t e.  The ray through row b
+// has height z(t) = zO + t tan(phi), and 3D length = dt * sec(phi).  Plane
+// crossings are t = (plane - O) / e for x and y planes and t = (plane - zO) cot(phi)
+// for z planes; both kernels evaluate them with the same float32 expression, so the
+// intersection lengths they use are the same numbers.
+struct GeoDev {
+    int nx, ny, nz, nu, nv, na;
+    float hx, hy, hz;
+    float x0, y0, z0;            // lower corner of the volume box
+    float inv_hx, inv_hy, inv_hz;
+    float du, dv, inv_du, inv_dv;
+    float cu, cv;                // (nu-1)/2, (nv-1)/2
+    float dso, dsd;
+    const float4 *ray_xy;        // [na][nu]  O_x, O_y, 1/e_x, 1/e_y   (1/e = 0: parallel)
+    const float2 *ray_e;         // [na][nu]  e_x, e_y
+    const float4 *ray_z;         // [nu][nv]  zO, cot(phi), sec(phi), tan(phi)  (cot = 0: v = 0)
+    const float2 *col;           // [nu]      D = |d_xy|, t_S (source-to-O distance)
+    const float2 *view;          // [na]      cos, sin
+};
+
+__host__ __device__ __forceinline__ size_t vol_elems(const GeoDev &g) { return (size_t)g.nx * g.ny * g.nz; }
+__host__ __device__ __forceinline__ size_t sino_elems(const GeoDev &g) { return (size_t)g.na * g.nu * g.nv; }
+
+#ifdef __CUDACC__
+// Coordinate of grid plane p (exact expression shared by every kernel).
+__device__ __forceinline__ float plane_at(int p, float h, float lo) { return __fmaf_rn((float)p, h, lo); }
+// Crossing parameter of a plane: (plane - origin) * inverse direction, no contraction.
+__device__ __forceinline__ float t_cross(float plane, float origin, float inv) {
+    return __fmul_rn(__fsub_rn(plane, origin), inv);
+}
+#endif
+
+// One multigrid level: host geometry, device tables, workspaces.
+struct Level {
+    // host values (float64 for table construction)
+    int nx, ny, nz, nu, nv, na;
+    double hx, hy, hz, du, dv, dso, dsd;
+    GeoDev gd{};
+    // device allocations owned by the level
+    void *tables = nullptr;
+    float *f = nullptr, *g = nullptr, *A = nullptr, *B = nullptr;  // internal volumes
+    float *rs = nullptr;          // sec(phi) * residual, internal sinogram
+    float *Y = nullptr;           // data, internal sinogram (float32)
+    __half *Yh = nullptr;         // data, internal sinogram (half storage variant)
+    double *partial = nullptr;    // float64 block partials
+    size_t partial_len = 0;
+    double lambda = 0.0;          // cached lambda_max(P^T P) (0 = unknown)
+    int lambda_iters = 0;
+};
+
+struct EventPool {
+    std::vector<cudaEvent_t> free_list, used;
+    std::vector<int> cls;
+    cudaEvent_t get();
+    void release_all();
+    ~EventPool();
+};
+
+}  // namespace cbct
+
+struct cbct_geometry {
+    cbct_geometry_desc desc;
+    std::vector<double> angles;
+    int device = 0;
+    std::vector<cbct::Level *> levels;   // index = level, created on demand
+    double *dscalars = nullptr;          // small device scratch: trace, counters
+    float *io_vol = nullptr;             // API-layout staging (internal <-> API)
+    int *dcounter = nullptr;
+    double *dtrace = nullptr;            // device energy trace
+    size_t dtrace_len = 0;
+    cbct::EventPool events;
+};
+
+namespace cbct {
+
+void set_error(const char *fmt, ...);
+cbct_status cuda_fail(cudaError_t e, const char *what);
+
+// level management (geometry.cu)
+cbct_status ensure_level(cbct_geometry *G, int level, Level **out);
+cbct_status ensure_workspace(Level *L, bool need_half);
+void free_level(Level *L);
+
+// kernel launchers (return cudaError_t of the launch)
+enum ProjMode { PROJ_PLAIN = 0, PROJ_RESID32 = 1, PROJ_RESID16 = 2, PROJ_SCALED = 3 };
+cudaError_t launch_project(const GeoDev &g, const float *vol, const float *y32, const __half *y16,
+                           float *out, double *partial, int mode, cudaStream_t s, int *nblocks_out);
+size_t project_partials(const GeoDev &g);
+
+enum BpMode { BP_PLAIN = 0, BP_STEP = 1 };
+cudaError_t launch_backproject(const GeoDev &g, const float *rs, const float *fin, float *out, float c,
+                               int mode, cudaStream_t s);
+
+struct TvArgs {
+    int nx, ny, nz;          // internal layout [nx][ny][nz]
+    float ihx, ihy, ihz;     // 1/h
+    float s, beta, eps2;
+};
+cudaError_t launch_tv_sweep(const TvArgs &a, const float *fin, const float *g, float *fout, bool clamp,
+                            double *partial_e1, cudaStream_t s, int *nblocks_out);
+size_t tv_partials(int nx, int ny, int nz);
+
+// layout changes
+cudaError_t launch_vol_to_internal(const float *api, float *in, int nx, int ny, int nz, cudaStream_t s);
+cudaError_t launch_vol_to_api(const float *in, float *api, int nx, int ny, int nz, cudaStream_t s);
+// sinogram [na][nv][nu] -> [na][nu][nv]; optional sec(phi) scaling from ray_z, optional half output
+cudaError_t launch_sino_to_internal(const float *api, float *out32, __half *out16, const float4 *ray_z,
+                                    int na, int nu, int nv, cudaStream_t s);
+cudaError_t launch_sino_to_api(const float *in, float *api, int na, int nu, int nv, cudaStream_t s);
+
+// multigrid transfers (layout-agnostic: [n0][n1][n2] volumes, [na][n1][n2] stacks)
+cudaError_t launch_restrict(const float *y, float *yc, int na, int n1, int n2, cudaStream_t s);
+cudaError_t launch_to_half(const float *x, __half *y, size_t n, cudaStream_t s);
+cudaError_t launch_prolong(const float *fc, int c0, int c1, int c2, float *f, int n0, int n1, int n2,
+                           cudaStream_t s);
+
+// reductions and small kernels
+cudaError_t launch_energy_finalize(const double *pe2, int n2, const double *pe1, int n1, double inv_nv,
+                                   double mu_over_nr, double *trace, int *counter, cudaStream_t s);
+cudaError_t launch_dot2(const float *x, const float *y, size_t n, double *partial, cudaStream_t s,
+                        int *nblocks_out);
+cudaError_t launch_power_finalize(const double *partial, int nblk, double *lam, float *scale,
+                                  cudaStream_t s);
+cudaError_t launch_scale(const float *y, const float *scale, float *x, size_t n, cudaStream_t s);
+cudaError_t launch_fill(float *x, float v, size_t n, cudaStream_t s);
+cudaError_t launch_tv_energy(const TvArgs &a, const float *f, double *partial, cudaStream_t s,
+                             int *nblocks_out);
+
+}  // namespace cbct

@@ -1,0 +1,354 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Gates (float32 bulk arithmetic, float64 reductions):
+  projections      relative L2 <= 1e-5 and max |diff| <= 1e-5 max |P f|
+  adjoint          relative L2 <= 1e-5; GPU adjoint identity <= 1e-6
+  volumes after a fixed number of Algorithm A1 iterations: relative L2 <= 1e-4
+  f >= 0 exactly (every stored voxel >= +0.0)
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle.brute_matrix import tiny_geometry
+
+pytestmark = pytest.mark.gpu
+
+P_TOL = 1e-5
+VOL_TOL = 1e-4
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - np.asarray(b, np.float64)) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def lib(cuda):
+    from paper_1002_3675_b300 import cbct
+    return cbct
+
+
+def dev(x):
+    import torch
+    return torch.tensor(np.ascontiguousarray(x, dtype=np.float32), device="cuda")
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def f32(x):
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
+def check_projection(lib, geom, f):
+    G = lib.cbct_geometry_create(geom)
+    y = host(lib.cbct_project(G, dev(f)))
+    ref = oracle.project(geom, f32(f))
+    assert rel(y, ref) <= P_TOL, rel(y, ref)
+    assert np.abs(y - ref).max() <= P_TOL * np.abs(ref).max()
+    return y, ref
+
+
+def ragged_geometry():
+    # sizes off every multiple of 32 and odd imager sizes (rays in voxel planes)
+    return dict(nx=45, ny=38, nz=37, hx=2.0, hy=2.5, hz=3.0, nu=53, nv=41, du=4.0, dv=4.5,
+                dso=400.0, dsd=640.0, angles=2 * math.pi * np.arange(7) / 7 + 0.1)
+
+
+# ---------------------------------------------------------------------------------
+# projector
+# ---------------------------------------------------------------------------------
+
+def test_project_small_random_and_phantom(lib):
+    case = synth.make_case("small", with_truth=True, truth_ss=1)
+    g = case["geom"]
+    rng = np.random.default_rng(20)
+    check_projection(lib, g, rng.uniform(size=(64, 64, 64)) * 0.02)
+    check_projection(lib, g, case["f_true"])
+
+
+def test_project_degenerate_and_ragged(lib):
+    rng = np.random.default_rng(21)
+    g = tiny_geometry(n=8, h=4.0, nu=9, nv=9, du=8.0, dv=8.0, n_angles=4)   # in-plane rays
+    check_projection(lib, g, rng.uniform(size=(8, 8, 8)))
+    g = ragged_geometry()
+    check_projection(lib, g, rng.uniform(size=(37, 38, 45)))
+
+
+def test_project_medium_full_size(lib):
+    g = synth.geometry_for(synth.CONFIGS["medium"])
+    rng = np.random.default_rng(22)
+    f = rng.uniform(size=(64, 256, 256)) * 0.02
+    check_projection(lib, g, f)
+
+
+def test_project_large_sampled_rays(lib):
+    g = synth.geometry_for(synth.CONFIGS["large"])
+    rng = np.random.default_rng(23)
+    f = (rng.uniform(size=(96, 512, 512)) * 0.02).astype(np.float32)
+    G = lib.cbct_geometry_create(g)
+    y = host(lib.cbct_project(G, dev(f)))
+    f64 = f.astype(np.float64)
+    for _ in range(40):
+        ia, b, a = rng.integers(0, 40), rng.integers(0, 384), rng.integers(0, 512)
+        ref = oracle.project_ray(g, f64, int(ia), int(b), int(a))
+        assert abs(y[ia, b, a] - ref) <= P_TOL * max(abs(ref), 1.0), (ia, b, a, y[ia, b, a], ref)
+    # every ray through the central column of the volume is non-zero
+    assert (y[:, 150:234, 200:312] > 0).all()
+
+
+# ---------------------------------------------------------------------------------
+# adjoint
+# ---------------------------------------------------------------------------------
+
+def test_backproject_small_and_ragged(lib):
+    rng = np.random.default_rng(24)
+    for g in (synth.geometry_for(synth.CONFIGS["small"]), ragged_geometry(),
+              tiny_geometry(n=8, h=4.0, nu=9, nv=9, du=8.0, dv=8.0, n_angles=4)):
+        G = lib.cbct_geometry_create(g)
+        y = rng.normal(size=(len(g["angles"]), g["nv"], g["nu"]))
+        bt = host(lib.cbct_backproject(G, dev(y)))
+        ref = oracle.backproject(g, f32(y))
+        assert rel(bt, ref) <= P_TOL, rel(bt, ref)
+
+
+def test_backproject_medium_full_size(lib):
+    g = synth.geometry_for(synth.CONFIGS["medium"])
+    rng = np.random.default_rng(25)
+    y = rng.normal(size=(40, 192, 256))
+    G = lib.cbct_geometry_create(g)
+    bt = host(lib.cbct_backproject(G, dev(y)))
+    ref = oracle.backproject(g, f32(y))
+    assert rel(bt, ref) <= P_TOL, rel(bt, ref)
+
+
+def test_backproject_large_sampled_voxels(lib):
+    g = synth.geometry_for(synth.CONFIGS["large"])
+    rng = np.random.default_rng(26)
+    y = rng.normal(size=(40, 384, 512)).astype(np.float32)
+    G = lib.cbct_geometry_create(g)
+    bt = host(lib.cbct_backproject(G, dev(y)))
+    y64 = y.astype(np.float64)
+    scale = np.abs(bt).max()
+    for _ in range(12):
+        i, j, k = rng.integers(0, 512), rng.integers(0, 512), rng.integers(0, 96)
+        ref = oracle.backproject_voxel(g, y64, int(i), int(j), int(k))
+        assert abs(bt[k, j, i] - ref) <= P_TOL * scale, (i, j, k, bt[k, j, i], ref)
+
+
+def test_gpu_adjoint_identity(lib):
+    for g in (synth.geometry_for(synth.CONFIGS["small"]), ragged_geometry()):
+        G = lib.cbct_geometry_create(g)
+        rng = np.random.default_rng(27)
+        f = rng.uniform(size=(g["nz"], g["ny"], g["nx"]))
+        y = rng.normal(size=(len(g["angles"]), g["nv"], g["nu"]))
+        Pf = host(lib.cbct_project(G, dev(f)))
+        PTy = host(lib.cbct_backproject(G, dev(y)))
+        lhs, rhs = float(np.sum(Pf * f32(y))), float(np.sum(f32(f) * PTy))
+        assert abs(lhs - rhs) <= 1e-6 * np.linalg.norm(Pf) * np.linalg.norm(y)
+
+
+# ---------------------------------------------------------------------------------
+# TV prox, energies, step size
+# ---------------------------------------------------------------------------------
+
+def test_tv_prox_matches_oracle(lib):
+    g = synth.geometry_for(synth.CONFIGS["small"])
+    case = synth.make_case("small", with_truth=True, truth_ss=1)
+    rng = np.random.default_rng(28)
+    f0 = case["f_true"]
+    gv = f0 + rng.normal(scale=0.004, size=f0.shape)
+    eps = oracle.default_eps(g)
+    beta = 2.0e5
+    G = lib.cbct_geometry_create(g)
+    ft = dev(f0)
+    lib.cbct_tv_prox(G, dev(gv), ft, beta, eps, 10)
+    out = host(ft)
+    ref = oracle.prox(f32(gv), f32(f0), (4.0, 4.0, 4.0), beta, eps, 10)
+    assert (out >= 0).all() and not np.signbit(out).any()
+    d_ref = ref - f32(f0)
+    assert np.linalg.norm((out - f32(f0)) - d_ref) <= 1e-4 * np.linalg.norm(d_ref)
+
+
+def test_energy_and_power_iteration(lib):
+    case = synth.make_case("small")
+    g = case["geom"]
+    rng = np.random.default_rng(29)
+    f = rng.uniform(size=(64, 64, 64)) * 0.02
+    eps = oracle.default_eps(g)
+    G = lib.cbct_geometry_create(g)
+    E = lib.cbct_energy(G, dev(case["Y"]), dev(f), case["mu"], eps)
+    ref = oracle.energy(g, f32(case["Y"]), f32(f), case["mu"], eps)
+    assert np.all(np.abs(E - ref) <= 1e-5 * np.abs(ref))
+    lam = lib.cbct_power_iteration(G, 30)
+    lam_ref = oracle.power_iteration(g, 30)
+    assert abs(lam - lam_ref) <= 1e-5 * lam_ref
+
+
+# ---------------------------------------------------------------------------------
+# Algorithm A1 and the multigrid cascade
+# ---------------------------------------------------------------------------------
+
+def test_fbs_small_20_iterations(lib):
+    case = synth.make_case("small")
+    g = case["geom"]
+    mu, eps = case["mu"], oracle.default_eps(g)
+    beta = 1.05 * oracle.gamma(g, mu) * oracle.power_iteration(g, 30)
+    Y = f32(case["Y"])
+    f_ref, tr_ref = oracle.fbs(g, Y, mu, beta, eps, 10, 20)
+    G = lib.cbct_geometry_create(g)
+    ft = dev(np.zeros((64, 64, 64)))
+    ft, tr = lib.cbct_fbs(G, dev(Y), mu, beta, eps, 10, 0, 20, ft, trace=True)
+    f = host(ft)
+    assert rel(f, f_ref) <= VOL_TOL, rel(f, f_ref)
+    assert (f >= 0).all() and not np.signbit(f).any()
+    assert np.all(np.abs(tr - tr_ref) <= 1e-4 * np.abs(tr_ref))
+    assert np.all(np.diff(tr[:, 0]) <= 1e-6 * tr[:-1, 0])
+
+
+def test_fbs_paper_literal_clamp_mode(lib):
+    case = synth.make_case("small")
+    g = case["geom"]
+    mu, eps = case["mu"], oracle.default_eps(g)
+    beta = 1.05 * oracle.gamma(g, mu) * oracle.power_iteration(g, 30)
+    Y = f32(case["Y"])
+    f_ref, tr_ref = oracle.fbs(g, Y, mu, beta, eps, 10, 10, clamp_mode=1)
+    G = lib.cbct_geometry_create(g)
+    ft, tr = lib.cbct_fbs(G, dev(Y), mu, beta, eps, 10, 1, 10, dev(np.zeros((64, 64, 64))), trace=True)
+    f = host(ft)
+    assert rel(f, f_ref) <= VOL_TOL, rel(f, f_ref)
+    assert (f >= 0).all()
+    assert np.all(np.abs(tr - tr_ref) <= 1e-4 * np.abs(tr_ref))
+
+
+def test_reconstruct_two_levels_small(lib):
+    case = synth.make_case("small")
+    g = case["geom"]
+    mu = case["mu"]
+    betas = [1.05 * oracle.gamma(oracle.level_geom(g, l), mu) * oracle.power_iteration(oracle.level_geom(g, l), 30)
+             for l in range(2)]
+    Y = f32(case["Y"])
+    f_ref, tr_ref = oracle.reconstruct(g, Y, mu, 8, 2, betas=betas, M=10)
+    G = lib.cbct_geometry_create(g)
+    ft, info = lib.cbct_reconstruct(G, dev(Y), mu, 8, 2, betas=betas, trace=True)
+    f = host(ft)
+    assert rel(f, f_ref) <= VOL_TOL, rel(f, f_ref)
+    assert (f >= 0).all()
+    assert np.all(np.abs(info["trace"] - tr_ref) <= 1e-4 * np.abs(tr_ref))
+
+
+def test_reconstruct_auto_beta_matches_oracle(lib):
+    case = synth.make_case("small")
+    g = case["geom"]
+    Y = f32(case["Y"])
+    G = lib.cbct_geometry_create(g)
+    ft, info = lib.cbct_reconstruct(G, dev(Y), case["mu"], 4, 2, trace=True)
+    for l in range(2):
+        lg = oracle.level_geom(g, l)
+        ref = max(10 * case["mu"], 1.05 * oracle.gamma(lg, case["mu"]) * oracle.power_iteration(lg, 30))
+        assert abs(info["betas"][l] - ref) <= 1e-5 * ref
+    f_ref, _ = oracle.reconstruct(g, Y, case["mu"], 4, 2, betas=info["betas"])
+    assert rel(host(ft), f_ref) <= VOL_TOL
+
+
+def test_medium_one_iteration_full_size(lib):
+    """One Algorithm A1 iteration at the full 256x256x64 / 40x256x192 size, from an
+    iterate produced by the GPU's own multigrid run (the benchmark configuration)."""
+    case = synth.make_case("medium")
+    g = case["geom"]
+    mu = case["mu"]
+    Y = f32(case["Y"])
+    G = lib.cbct_geometry_create(g)
+    ft, info = lib.cbct_reconstruct(G, dev(Y), mu, 5, 2, trace=True)
+    f_k = host(ft)
+    assert (f_k >= 0).all()
+    for l in range(2):
+        E = info["trace"][l, :, 0]
+        assert np.all(np.diff(E) <= 1e-5 * E[:-1])
+    beta = float(info["betas"][0])
+    eps = oracle.default_eps(g)
+    f1 = host(lib.cbct_fbs(G, dev(Y), mu, beta, eps, 10, 0, 1, dev(f_k)))
+    f1_ref, _ = oracle.fbs(g, Y, mu, beta, eps, 10, 1, f0=f_k)
+    step_ref = f1_ref - f_k
+    assert np.linalg.norm((f1 - f_k) - step_ref) <= 1e-3 * np.linalg.norm(step_ref)
+    assert rel(f1, f1_ref) <= 1e-5
+
+
+def test_multigrid_transfers(lib):
+    rng = np.random.default_rng(30)
+    y = rng.normal(size=(3, 37, 53))
+    yc = host(lib.cbct_restrict_sino(dev(y)))
+    assert np.abs(yc - oracle.restrict_sino(f32(y))).max() <= 1e-6
+    fc = rng.uniform(size=(5, 7, 9))
+    f = host(lib.cbct_prolong_vol(dev(fc), (10, 13, 18)))
+    assert np.abs(f - oracle.prolong_vol(f32(fc), (10, 13, 18))).max() <= 1e-6
+
+
+# ---------------------------------------------------------------------------------
+# variants, determinism, resume, timing
+# ---------------------------------------------------------------------------------
+
+def test_fp16_sinogram_variant_error_reported(lib):
+    case = synth.make_case("small")
+    g = case["geom"]
+    Y = f32(case["Y"])
+    G = lib.cbct_geometry_create(g)
+    betas = [1.4e6]
+    f16 = host(lib.cbct_reconstruct(G, dev(Y), case["mu"], 10, 1, betas=betas, sino_fp16=True))
+    f_ref, _ = oracle.reconstruct(g, Y, case["mu"], 10, 1, betas=betas)
+    err = rel(f16, f_ref)
+    print(f"fp16 sinogram storage: relative L2 error vs FP64 oracle = {err:.3e}")
+    assert err < 1e-2 and (f16 >= 0).all()
+
+
+def test_deterministic_and_graphs_identical(lib, cuda):
+    torch = cuda
+    case = synth.make_case("small")
+    G = lib.cbct_geometry_create(case["geom"])
+    Y = dev(case["Y"])
+    runs = [host(lib.cbct_reconstruct(G, Y, case["mu"], 6, 2)) for _ in range(2)]
+    assert np.array_equal(runs[0], runs[1])
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        fg = lib.cbct_reconstruct(G, Y, case["mu"], 6, 2, use_graphs=True)
+    s.synchronize()
+    assert np.array_equal(host(fg), runs[0])
+
+
+def test_resume_from_checkpoint(lib):
+    case = synth.make_case("small")
+    G = lib.cbct_geometry_create(case["geom"])
+    Y = dev(case["Y"])
+    full = host(lib.cbct_reconstruct(G, Y, case["mu"], 6, 1, beta=1.4e6))
+    half = lib.cbct_reconstruct(G, Y, case["mu"], 3, 1, beta=1.4e6)
+    rest = host(lib.cbct_reconstruct(G, Y, case["mu"], 3, 1, beta=1.4e6, f_init=half, start_level=0))
+    assert np.array_equal(full, rest)
+
+
+def test_kernel_timing_report(lib):
+    case = synth.make_case("small")
+    G = lib.cbct_geometry_create(case["geom"])
+    f, info = lib.cbct_reconstruct(G, dev(case["Y"]), case["mu"], 3, 2, kernel_times=True)
+    ms, n = info["kernel_ms"], info["kernel_launches"]
+    assert n["project"] == 2 * (3 + 30) and n["backproject"] == 2 * (3 + 30)
+    assert n["tv"] == 2 * 3 * 10
+    assert all(ms[k] > 0 for k in ("project", "backproject", "tv"))
+
+
+def test_invalid_arguments_on_device(lib):
+    case = synth.make_case("small")
+    G = lib.cbct_geometry_create(case["geom"])
+    Y = dev(case["Y"])
+    with pytest.raises(lib.CbctError) as e:
+        lib.cbct_reconstruct(G, Y, case["mu"], 2, 8)      # 2^7 > 48 detector rows
+    assert e.value.status == 1
+    with pytest.raises(lib.CbctError):
+        lib.cbct_reconstruct(G, Y, -1.0, 2, 1)
+    with pytest.raises(lib.CbctError):
+        lib.cbct_fbs(G, Y, 1.0, 0.0, 1e-5, 10, 0, 2, dev(np.zeros((64, 64, 64))))

@@ -388,7 +388,7 @@ def test_restriction_is_block_mean():
 def test_single_level_cascade_equals_fbs():
     case = synth.make_case("small")
     g = case["geom"]
-    beta = 7.5e4
+    beta = 1.4e6      # above 1.05 gamma lambda_max for this workload
     eps = oracle.default_eps(g)
     f1, tr1 = oracle.reconstruct(g, case["Y"], case["mu"], 4, 1, betas=[beta], M=5)
     f2, tr2 = oracle.fbs(g, case["Y"], case["mu"], beta, eps, 5, 4)
