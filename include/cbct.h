@@ -183,6 +183,27 @@ cbct_status cbct_restrict_sino(int n_angles, int nv, int nu, const float *y_dev,
 cbct_status cbct_prolong_vol(int nxc, int nyc, int nzc, const float *fc_dev, int nx, int ny, int nz,
                              float *f_dev, cudaStream_t stream);
 
+/* Largest volume (nx*ny*nz) that cbct_tv_energy_noalloc accepts. */
+#define CBCT_NOALLOC_MAX_VOXELS 33554432
+
+/* E1 energy of a volume without allocating anything.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc --
+ * code running while a stream is captured into a CUDA graph, real-time or embedded
+ * hosts that forbid allocation after start-up, plug-ins that must leave the device
+ * heap alone -- and therefore cannot create a cbct_geometry.
+ * Writes *e1_dev = TV_eps(f) / (nx ny nz) (device float64, same definition and
+ * value as element 1 of cbct_energy) for f_dev, a [nz][ny][nx] float32 device
+ * volume with spacings hx, hy, hz.  Asynchronous on `stream`.
+ * Scratch: a 1 MiB array inside the library, reserved on every GPU that loads the
+ * library until the process exits; hence volumes above CBCT_NOALLOC_MAX_VOXELS are
+ * rejected with CBCT_ERR_INVALID_ARG.  The first call on a device looks up that
+ * array's device address (with that device current); make that first call before
+ * any stream capture.  Calls share the array: calls that may overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the caller.
+ * No cudaMalloc, cudaFree or allocating library routine is called. */
+cbct_status cbct_tv_energy_noalloc(int nx, int ny, int nz, double hx, double hy, double hz, double eps,
+                                   const float *f_dev, double *e1_dev, cudaStream_t stream);
+
 /* Thread-local description of the last error on the calling thread. */
 const char *cbct_last_error(void);
 

@@ -66,6 +66,7 @@ _SIGS = {
     "cbct_reconstruct": [_P, _P, C.POINTER(C.c_double), _I, _D, _I, _I, C.POINTER(Options), _P, _V],
     "cbct_restrict_sino": [_I, _I, _I, _P, _P, _V],
     "cbct_prolong_vol": [_I, _I, _I, _P, _I, _I, _I, _P, _V],
+    "cbct_tv_energy_noalloc": [_I, _I, _I, _D, _D, _D, _D, _P, _P, _V],
     "cbct_last_error": [],
     "cbct_version": [],
 }
@@ -239,6 +240,20 @@ def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=N
         info["kernel_ms"] = dict(zip(KERNEL_CLASSES, list(km)))
         info["kernel_launches"] = dict(zip(KERNEL_CLASSES, list(kl)))
     return f_out, info
+
+
+def cbct_tv_energy_noalloc(f, h, eps, out=None):
+    """E1 = TV_eps(f) / Nv into a one-element float64 CUDA tensor, through the entry
+    point that allocates nothing inside the library (for callers that cannot call
+    cudaMalloc); `out` may be preallocated by the caller."""
+    import torch
+    nz, ny, nx = f.shape
+    out = torch.empty(1, dtype=torch.float64, device=f.device) if out is None else out
+    if not (out.is_cuda and out.dtype == torch.float64 and out.numel() >= 1):
+        raise TypeError("out must be a float64 CUDA tensor")
+    _check(lib.cbct_tv_energy_noalloc(nx, ny, nz, float(h[0]), float(h[1]), float(h[2]), eps, _ptr(f, "f"),
+                                      C.c_void_p(out.data_ptr()), _stream()))
+    return out
 
 
 def cbct_restrict_sino(y):
