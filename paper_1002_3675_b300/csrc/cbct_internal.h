@@ -40,6 +40,7 @@ struct GeoDev {
     const float4 *ray_xy;        // [na][nu]  O_x, O_y, 1/e_x, 1/e_y   (1/e = 0: parallel)
     const float2 *ray_e;         // [na][nu]  e_x, e_y
     const float4 *ray_z;         // [nu][nv]  zO, cot(phi), sec(phi), tan(phi)  (cot = 0: v = 0)
+    const float2 *ray_zc;        // [nu][nv]  zO, cot(phi) (same values; the adjoint's table)
     const float2 *col;           // [nu]      D = |d_xy|, t_S (source-to-O distance)
     const float2 *view;          // [na]      cos, sin
 };

@@ -234,12 +234,13 @@ cudaError_t launch_energy_finalize(const double *pe2, int n2, const double *pe1,
     return cudaGetLastError();
 }
 
-// per-block partials of <x, y> and <y, y>
+// per-block partials of <x, y> and <y, y>: float32 within a warp (pairwise tree),
+// float64 across warps and blocks
 __global__ void k_dot2(const float *__restrict__ x, const float *__restrict__ y, size_t n, double *partial) {
-    double sxy = 0.0, syy = 0.0;
+    float sxy = 0.f, syy = 0.f;
     const size_t o = (size_t)blockIdx.x * 256 + threadIdx.x;
     if (o < n) {
-        const double xv = x[o], yv = y[o];
+        const float xv = x[o], yv = y[o];
         sxy = xv * yv;
         syy = yv * yv;
     }
@@ -249,8 +250,8 @@ __global__ void k_dot2(const float *__restrict__ x, const float *__restrict__ y,
     }
     __shared__ double a[8], b[8];
     if ((threadIdx.x & 31) == 0) {
-        a[threadIdx.x >> 5] = sxy;
-        b[threadIdx.x >> 5] = syy;
+        a[threadIdx.x >> 5] = (double)sxy;
+        b[threadIdx.x >> 5] = (double)syy;
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -4,7 +4,7 @@
 // variation with Neumann boundary, sum_j sqrt(|grad f|_j^2 + eps^2).  Its gradient
 // is sum_d D_d^T (D_d f / |grad f|_eps), a 13-point stencil per voxel:
 //   (D_d^T p)_i = (p_{i-1} [i > 0] - p_i [i < n-1]) / h_d.
-// The sweep also emits the float64 partial sums of |grad f|_eps of its input (the
+// The sweep also emits the partial sums of |grad f|_eps of its input (the
 // E1 energy of the entering iterate when the input is f_k).
 //
 // Layout [nx][ny][nz] (z fastest); one thread per voxel, consecutive lanes along z.
@@ -20,7 +20,7 @@ k_tv_sweep(TvArgs A, const float *__restrict__ fin, const float *__restrict__ g,
            double *__restrict__ partial) {
     const size_t n = (size_t)A.nx * A.ny * A.nz;
     const size_t idx = (size_t)blockIdx.x * TV_THREADS + threadIdx.x;
-    double e1 = 0.0;
+    float e1 = 0.f;
     if (idx < n) {
         const int k = (int)(idx % A.nz);
         const size_t t = idx / A.nz;
@@ -36,7 +36,7 @@ k_tv_sweep(TvArgs A, const float *__restrict__ fin, const float *__restrict__ g,
         const float q0 = gx * gx + gy * gy + gz * gz + A.eps2;
         const float n0 = rsqrtf(q0);
         float div = -(gx * A.ihx + gy * A.ihy + gz * A.ihz) * n0;
-        if (E1) e1 = (double)(q0 * n0);
+        if (E1) e1 = q0 * n0;
         // p_x at i-1
         if (i > 0) {
             const float fm = __ldg(fin + idx - sx);
@@ -65,10 +65,11 @@ k_tv_sweep(TvArgs A, const float *__restrict__ fin, const float *__restrict__ g,
         fout[idx] = CLAMP ? fmaxf(x, 0.f) : x;
     }
     if (E1) {
+        // float32 within a warp (pairwise tree), float64 across warps and blocks
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) e1 += __shfl_down_sync(0xffffffffu, e1, off);
         __shared__ double red[TV_THREADS / 32];
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e1;
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)e1;
         __syncthreads();
         if (threadIdx.x == 0) {
             double s = 0.0;

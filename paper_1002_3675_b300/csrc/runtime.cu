@@ -107,6 +107,7 @@ static cbct_status build_level(const cbct_geometry *G, int level, Level *L) {
     std::vector<float4> ray_xy((size_t)na * nu);
     std::vector<float2> ray_e((size_t)na * nu);
     std::vector<float4> ray_z((size_t)nu * nv);
+    std::vector<float2> ray_zc((size_t)nu * nv);
     std::vector<float2> col(nu);
     std::vector<float2> view(na);
     for (int a = 0; a < nu; ++a) {
@@ -121,6 +122,7 @@ static cbct_status build_level(const cbct_geometry *G, int level, Level *L) {
             double cotp = vb != 0.0 ? D / vb : 0.0;
             double secp = sqrt(D * D + vb * vb) / D;
             ray_z[(size_t)a * nv + b] = make_float4((float)zO, (float)cotp, (float)secp, (float)tanp);
+            ray_zc[(size_t)a * nv + b] = make_float2((float)zO, (float)cotp);
         }
     }
     for (int ia = 0; ia < na; ++ia) {
@@ -144,7 +146,8 @@ static cbct_status build_level(const cbct_geometry *G, int level, Level *L) {
     size_t o_xy = 0;
     size_t o_e = align_up(o_xy + ray_xy.size() * sizeof(float4));
     size_t o_z = align_up(o_e + ray_e.size() * sizeof(float2));
-    size_t o_col = align_up(o_z + ray_z.size() * sizeof(float4));
+    size_t o_zc = align_up(o_z + ray_z.size() * sizeof(float4));
+    size_t o_col = align_up(o_zc + ray_zc.size() * sizeof(float2));
     size_t o_view = align_up(o_col + col.size() * sizeof(float2));
     size_t total = align_up(o_view + view.size() * sizeof(float2));
     cbct_status st = dmalloc(&L->tables, total, "ray tables");
@@ -154,6 +157,7 @@ static cbct_status build_level(const cbct_geometry *G, int level, Level *L) {
     if (e == cudaSuccess) e = cudaMemcpy(base + o_xy, ray_xy.data(), ray_xy.size() * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(base + o_e, ray_e.data(), ray_e.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(base + o_z, ray_z.data(), ray_z.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + o_zc, ray_zc.data(), ray_zc.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(base + o_col, col.data(), col.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(base + o_view, view.data(), view.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "uploading ray tables");
@@ -172,6 +176,7 @@ static cbct_status build_level(const cbct_geometry *G, int level, Level *L) {
     g.ray_xy = (const float4 *)(base + o_xy);
     g.ray_e = (const float2 *)(base + o_e);
     g.ray_z = (const float4 *)(base + o_z);
+    g.ray_zc = (const float2 *)(base + o_zc);
     g.col = (const float2 *)(base + o_col);
     g.view = (const float2 *)(base + o_view);
     return CBCT_OK;
