@@ -42,6 +42,7 @@ struct GeoDev {
     const float4 *ray_z;         // [nu][nv]  zO, cot(phi), sec(phi), tan(phi)  (cot = 0: v = 0)
     const float2 *ray_zc;        // [nu][nv]  zO, cot(phi) (same values; the adjoint's table)
     const float2 *col;           // [nu]      D = |d_xy|, t_S (source-to-O distance)
+    const short2 *arange;        // [na][nx][ny] first/last detector column meeting each xy-cell
     const float2 *view;          // [na]      cos, sin
 };
 

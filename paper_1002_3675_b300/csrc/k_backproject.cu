@@ -6,22 +6,44 @@
 // g = f - c P^T r with c = gamma / beta.
 //
 // Work decomposition.  One warp owns 32*VPL voxels of one z-column (i, j); lane l
-// holds voxels k = base + l + 32 v, v < VPL.  For each view, the candidate detector
-// columns are those whose ray plane meets the xy-cell: the interval spanned by the
-// cell's four projected corners, widened by CAND_MARGIN pixel (the computed bounds
-// are accurate to ~1e-4 pixel, and a ray outside the exact interval meets the cell
-// in a zero-length set).  The xy part of the intersection interval is the same for
-// the whole column, so it is computed once per warp.  Each lane then visits, for each
-// of its voxels, the detector rows whose ray meets the voxel (the interval spanned by
-// the four (t, z) corners, same margin) and adds length * (sec(phi) r), the residual
-// having been pre-scaled by sec(phi) in the projector's epilogue.  The sum is taken
-// in a fixed order (view, column, row) with no atomics, so results are deterministic.
+// holds voxels k = base + l + 32 v, v < VPL.  Per view, the detector columns whose ray
+// plane meets the xy-cell come from a precomputed table; for each, the part of the
+// rays' horizontal parameter t inside the cell, [tlo, thi], is the same for the whole
+// z-column.
+//
+// Plane sweep.  In detector-row units, a ray b sits at row b and the plane z at
+// rho_z(t) = z D / ((tS + t) dv) + cv, monotone in t.  Ray b is inside voxel k at t iff
+// rho_{z_k}(t) <= b < rho_{z_k+1}(t), so its length in the voxel is
+// J_{z_k+1}(b) - J_{z_k}(b) with J_z(b) = |{t in [tlo, thi] : b < rho_z(t)}|: thi - tlo for
+// rows below both ends of rho_z, 0 for rows above both, and the exact crossing
+// t* = (z - zO_b) cot_b otherwise (at most one row per plane here).  Hence
+//   sum_b r_b len = (thi - tlo) sum_{b in [N(z_k), N(z_k+1))} r_b + P(z_k+1) - P(z_k),
+// with N(z) the rows below both ends and P(z) the partial rows' sum.  Each lane
+// evaluates the plane below its voxel and takes the plane above from its neighbour.
+// The residual is pre-scaled by sec(phi) (3D length = t-length * sec(phi)).  Sums are
+// taken in a fixed order with no atomics, so results are deterministic.
 #include "cbct_internal.h"
 
 namespace cbct {
 
 static constexpr int BP_THREADS = 128;
-static constexpr float CAND_MARGIN = 0.01f;  // pixels
+
+// N(z) and P(z) of one plane for detector column rzp/rsp over [tlo, thi].
+__device__ __forceinline__ void eval_plane(float z, float q1, float q2, float cv, int nv, float tlo, float thi,
+                                           const float2 *__restrict__ rzp, const float *__restrict__ rsp,
+                                           int &nmin, float &part) {
+    const float r1 = __fmaf_rn(z, q1, cv), r2 = __fmaf_rn(z, q2, cv);
+    const float lo = fminf(r1, r2), hi = fmaxf(r1, r2);
+    nmin = min(max((int)ceilf(lo), 0), nv);
+    const int nmax = min(max((int)ceilf(hi), 0), nv);
+    const bool dec = r1 > r2;  // rho falls with t: the row is below the plane before t*
+    part = 0.f;
+    for (int b = nmin; b < nmax; ++b) {
+        const float2 rz = __ldg(rzp + b);
+        const float ts = fminf(fmaxf(t_cross(z, rz.x, rz.y), tlo), thi);
+        part = __fmaf_rn(__ldg(rsp + b), dec ? ts - tlo : thi - ts, part);
+    }
+}
 
 template <int MODE, int VPL>
 __global__ void __launch_bounds__(BP_THREADS, 8)
@@ -36,41 +58,24 @@ k_backproject(GeoDev G, const float *__restrict__ rs, const float *__restrict__ 
     const long colid = gwarp / nkc;
     const int j = (int)(colid % G.ny);
     const int i = (int)(colid / G.ny);
+    const int base = kc * 32 * VPL;
 
-    float zl[VPL], zh[VPL], acc[VPL];
-    bool valid[VPL];
+    float zb[VPL], acc[VPL];
 #pragma unroll
     for (int v = 0; v < VPL; ++v) {
-        const int k = kc * 32 * VPL + lane + 32 * v;
-        valid[v] = k < G.nz;
-        const int kq = valid[v] ? k : G.nz - 1;
-        zl[v] = plane_at(kq, G.hz, G.z0);
-        zh[v] = plane_at(kq + 1, G.hz, G.z0);
+        zb[v] = plane_at(base + lane + 32 * v, G.hz, G.z0);  // plane below voxel base + lane + 32 v
         acc[v] = 0.f;
     }
+    const float ztop = plane_at(base + 32 * VPL, G.hz, G.z0);  // plane above the warp's last voxel
     const float xl = plane_at(i, G.hx, G.x0), xh = plane_at(i + 1, G.hx, G.x0);
     const float yl = plane_at(j, G.hy, G.y0), yh = plane_at(j + 1, G.hy, G.y0);
-    const float ufac = G.dsd * G.inv_du;
 
 #pragma unroll 1
     for (int ia = 0; ia < G.na; ++ia) {
-        const float2 cs = G.view[ia];
-        // detector-column interval of the xy-cell: u* = dsd (p.u) / (dso - p.s)
-        float amin = INFINITY, amax = -INFINITY;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float px = (q & 1) ? xh : xl, py = (q & 2) ? yh : yl;
-            const float num = py * cs.x - px * cs.y;
-            const float den = G.dso - (px * cs.x + py * cs.y);
-            const float ac = __fdividef(num, den) * ufac + G.cu;
-            amin = fminf(amin, ac);
-            amax = fmaxf(amax, ac);
-        }
-        const int alo = max(0, (int)ceilf(amin - CAND_MARGIN));
-        const int ahi = min(G.nu - 1, (int)floorf(amax + CAND_MARGIN));
+        const short2 ar = G.arange[((size_t)ia * G.nx + i) * G.ny + j];
         const float *rsv = rs + (size_t)ia * G.nu * G.nv;
 #pragma unroll 1
-        for (int a = alo; a <= ahi; ++a) {
+        for (int a = ar.x; a <= ar.y; ++a) {
             const float4 rxy = G.ray_xy[(size_t)ia * G.nu + a];
             float tlo = -INFINITY, thi = INFINITY;
             if (rxy.z != 0.f) {
@@ -88,40 +93,44 @@ k_backproject(GeoDev G, const float *__restrict__ rs, const float *__restrict__ 
                 continue;
             }
             if (!(thi > tlo)) continue;
-            // detector-row interval of a voxel on column a: v* = z D / (tS + t); with
-            // q1 = D/(tS + tlo) > q2 = D/(tS + thi) > 0 the extreme corners follow from
-            // the signs of the voxel's bounding planes
             const float2 Dt = G.col[a];
+            // rows per mm of z at tlo and thi (fast division: a ~1e-4 row error only moves
+            // a row between "full" and "partial" when its crossing lies within ~1e-4 of the
+            // cell's ends, where both give the same length to that precision)
             const float q1 = __fdividef(Dt.x, Dt.y + tlo) * G.inv_dv;
             const float q2 = __fdividef(Dt.x, Dt.y + thi) * G.inv_dv;
+            const float w = thi - tlo;
             const float2 *rzp = G.ray_zc + (size_t)a * G.nv;
             const float *rsp = rsv + (size_t)a * G.nv;
+            int nb[VPL];
+            float pb[VPL];
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) eval_plane(zb[v], q1, q2, G.cv, G.nv, tlo, thi, rzp, rsp, nb[v], pb[v]);
+            int nt;
+            float pt;
+            eval_plane(ztop, q1, q2, G.cv, G.nv, tlo, thi, rzp, rsp, nt, pt);
 #pragma unroll
             for (int v = 0; v < VPL; ++v) {
-                const float bmin = zl[v] * (zl[v] > 0.f ? q2 : q1) + G.cv;
-                const float bmax = zh[v] * (zh[v] > 0.f ? q1 : q2) + G.cv;
-                const int blo = max(0, (int)ceilf(bmin - CAND_MARGIN));
-                int bhi = min(G.nv - 1, (int)floorf(bmax + CAND_MARGIN));
-                if (!valid[v]) bhi = blo - 1;
-                for (int b = blo; b <= bhi; ++b) {
-                    const float2 rz = __ldg(rzp + b);
-                    float lo = tlo, hi = thi;
-                    if (rz.y != 0.f) {
-                        const float z1 = t_cross(zl[v], rz.x, rz.y), z2 = t_cross(zh[v], rz.x, rz.y);
-                        lo = fmaxf(lo, fminf(z1, z2));
-                        hi = fminf(hi, fmaxf(z1, z2));
-                    } else if (!(rz.x >= zl[v] && rz.x < zh[v])) {
-                        continue;
-                    }
-                    if (hi > lo) acc[v] = __fmaf_rn(__fsub_rn(hi, lo), __ldg(rsp + b), acc[v]);
+                // the plane above voxel (lane, v) is the plane below the next voxel
+                int ntop = __shfl_down_sync(0xffffffffu, nb[v], 1);
+                float ptop = __shfl_down_sync(0xffffffffu, pb[v], 1);
+                const int nn = (v + 1 < VPL) ? __shfl_sync(0xffffffffu, nb[(v + 1) % VPL], 0) : nt;
+                const float pn = (v + 1 < VPL) ? __shfl_sync(0xffffffffu, pb[(v + 1) % VPL], 0) : pt;
+                if (lane == 31) {
+                    ntop = nn;
+                    ptop = pn;
                 }
+                float full = 0.f;
+                for (int b = nb[v]; b < ntop; ++b) full += __ldg(rsp + b);
+                acc[v] += __fmaf_rn(w, full, ptop - pb[v]);
             }
         }
     }
 #pragma unroll
     for (int v = 0; v < VPL; ++v) {
-        if (!valid[v]) continue;
-        const size_t o = ((size_t)i * G.ny + j) * G.nz + kc * 32 * VPL + lane + 32 * v;
+        const int k = base + lane + 32 * v;
+        if (k >= G.nz) continue;
+        const size_t o = ((size_t)i * G.ny + j) * G.nz + k;
         out[o] = (MODE == BP_PLAIN) ? acc[v] : __ldg(fin + o) - c * acc[v];
     }
 }

@@ -8,6 +8,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "cbct_internal.h"
 
 namespace cbct {
@@ -96,6 +98,10 @@ static cbct_status build_level(const cbct_geometry *G, int level, Level *L) {
     L->dso = d.dso;
     L->dsd = d.dsd;
     const double half_diag = 0.5 * sqrt((L->nx * L->hx) * (L->nx * L->hx) + (L->ny * L->hy) * (L->ny * L->hy));
+    if (L->nu > 32767) {
+        set_error("level %d: nu = %d above 32767", level, L->nu);
+        return CBCT_ERR_INVALID_ARG;
+    }
     if (!(L->dso > half_diag) || !(L->dsd - L->dso > half_diag)) {
         set_error("level %d: source circle (dso=%g) and imager (dsd-dso=%g) must clear the volume "
                   "half-diagonal %g", level, L->dso, L->dsd - L->dso, half_diag);
@@ -143,13 +149,43 @@ static cbct_status build_level(const cbct_geometry *G, int level, Level *L) {
             ray_e[(size_t)ia * nu + a] = make_float2((float)ex, (float)ey);
         }
     }
+    // Detector columns whose ray plane meets each xy-cell, per view: the interval
+    // spanned by the cell's four projected corners, widened by 0.01 pixel (the rays
+    // outside it meet the cell in a zero-length set); the adjoint's candidates.
+    std::vector<short2> arange((size_t)na * L->nx * L->ny);
+    {
+        const double x0 = -0.5 * L->nx * L->hx, y0 = -0.5 * L->ny * L->hy;
+        for (int ia = 0; ia < na; ++ia) {
+            const double c = cos(G->angles[ia]), sn = sin(G->angles[ia]);
+            for (int i = 0; i < L->nx; ++i)
+                for (int j = 0; j < L->ny; ++j) {
+                    double amin = 1e300, amax = -1e300;
+                    for (int q = 0; q < 4; ++q) {
+                        const double px = x0 + (i + (q & 1)) * L->hx, py = y0 + (j + (q >> 1)) * L->hy;
+                        const double u = L->dsd * (py * c - px * sn) / (L->dso - (px * c + py * sn));
+                        const double av = u / L->du + cu;
+                        amin = std::min(amin, av);
+                        amax = std::max(amax, av);
+                    }
+                    int lo = (int)ceil(amin - 0.01), hi = (int)floor(amax + 0.01);
+                    lo = std::max(lo, 0);
+                    hi = std::min(hi, nu - 1);
+                    if (hi < lo) {  // no column meets the cell: an empty range
+                        lo = 1;
+                        hi = 0;
+                    }
+                    arange[((size_t)ia * L->nx + i) * L->ny + j] = make_short2((short)lo, (short)hi);
+                }
+        }
+    }
     size_t o_xy = 0;
     size_t o_e = align_up(o_xy + ray_xy.size() * sizeof(float4));
     size_t o_z = align_up(o_e + ray_e.size() * sizeof(float2));
     size_t o_zc = align_up(o_z + ray_z.size() * sizeof(float4));
     size_t o_col = align_up(o_zc + ray_zc.size() * sizeof(float2));
     size_t o_view = align_up(o_col + col.size() * sizeof(float2));
-    size_t total = align_up(o_view + view.size() * sizeof(float2));
+    size_t o_ar = align_up(o_view + view.size() * sizeof(float2));
+    size_t total = align_up(o_ar + arange.size() * sizeof(short2));
     cbct_status st = dmalloc(&L->tables, total, "ray tables");
     if (st != CBCT_OK) return st;
     char *base = (char *)L->tables;
@@ -160,6 +196,7 @@ static cbct_status build_level(const cbct_geometry *G, int level, Level *L) {
     if (e == cudaSuccess) e = cudaMemcpy(base + o_zc, ray_zc.data(), ray_zc.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(base + o_col, col.data(), col.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(base + o_view, view.data(), view.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + o_ar, arange.data(), arange.size() * sizeof(short2), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "uploading ray tables");
 
     GeoDev &g = L->gd;
@@ -179,6 +216,7 @@ static cbct_status build_level(const cbct_geometry *G, int level, Level *L) {
     g.ray_zc = (const float2 *)(base + o_zc);
     g.col = (const float2 *)(base + o_col);
     g.view = (const float2 *)(base + o_view);
+    g.arange = (const short2 *)(base + o_ar);
     return CBCT_OK;
 }
 
