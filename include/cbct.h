@@ -50,7 +50,8 @@ typedef enum {
     CBCT_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed    */
     CBCT_ERR_TIMEOUT = 4,      /* a bounded wait expired                         */
     CBCT_ERR_UNSUPPORTED = 5,  /* option combination not implemented            */
-    CBCT_ERR_BUSY = 6          /* admission refused (budget or slots exhausted)  */
+    CBCT_ERR_BUSY = 6,         /* admission refused (budget or slots exhausted)  */
+    CBCT_ERR_CANCELLED = 7     /* request cancelled before it ran                */
 } cbct_status;
 
 /* Scan and grid description (problem statement before Eq. 1: P^theta maps f onto
@@ -96,6 +97,9 @@ typedef struct {
                              device time per kernel class, measured with CUDA events
                              on `stream` (synchronises at the end of the call)    */
     int *kernel_launches; /* optional host out [CBCT_NUM_KERNEL_CLASSES]          */
+    int reuse_lambda;     /* 1: reuse lambda_max(P^T P) of a level computed by an
+                             earlier call on this geometry with the same power_iters
+                             (the estimate is deterministic, so results are unchanged) */
 } cbct_options;
 
 /* Kernel classes reported through cbct_options.kernel_ms. */
@@ -182,6 +186,89 @@ cbct_status cbct_restrict_sino(int n_angles, int nv, int nu, const float *y_dev,
                                cudaStream_t stream);
 cbct_status cbct_prolong_vol(int nxc, int nyc, int nzc, const float *fc_dev, int nx, int ny, int nz,
                              float *f_dev, cudaStream_t stream);
+
+/* Batched reconstruction (many independent reconstructions, as in a serving batch).
+ * Each request is a cbct_reconstruct call; all of them advance together, one
+ * Algorithm A1 iteration (or power-iteration step) per tick, every stage of every
+ * request in one persistent launch per stage.  Each request's volume, energy trace
+ * and betas are bitwise the same as those of its own cbct_reconstruct call.  Every
+ * request needs its own geometry handle.  Synchronous: returns when all volumes are
+ * written.  use_graphs: replay ticks whose stages repeat as captured CUDA graphs
+ * (needs a stream other than 0).  Options honoured per request: as cbct_reconstruct,
+ * except kernel_ms / kernel_launches / use_graphs (ignored). */
+typedef struct {
+    cbct_geometry *geom;
+    const float *Y_dev;       /* finest-level sinogram [n_angles][nv][nu]            */
+    double mu;
+    int iters, levels;
+    const cbct_options *opts; /* nullable                                           */
+    float *f_out_dev;         /* volume [nz][ny][nx], written                        */
+} cbct_request;
+cbct_status cbct_reconstruct_batch(const cbct_request *reqs, int n_reqs, int use_graphs, cudaStream_t stream);
+
+/* Launch shapes of one level (0 = the library's default); they change no result bit. */
+typedef struct {
+    int proj_threads;  /* projector block size: multiple of 32, >= 32 ceil(nv/32), <= 512 */
+    int bp_vpl;        /* adjoint voxels per lane, 1..4                                */
+    int bp_threads;    /* adjoint block size: 64, 128 or 256                           */
+    float proj_ms;     /* autotune: measured time of one projection with the choice    */
+    float bp_ms;       /* autotune: measured time of one adjoint with the choice       */
+} cbct_tuning;
+/* Time the candidate launch shapes of level `level` with CUDA events on `stream`
+ * (synchronises), keep the fastest in the geometry and report it in *out. */
+cbct_status cbct_autotune(cbct_geometry *geom, int level, cbct_tuning *out, cudaStream_t stream);
+/* Apply launch shapes (e.g. from a cache of earlier autotune results). */
+cbct_status cbct_set_tuning(cbct_geometry *geom, int level, const cbct_tuning *tuning);
+
+/* Continuous-batching server.  A worker thread owns a stream and max_slots slots;
+ * a slot keeps one geometry (tables and workspaces) resident and serves one request
+ * at a time, and later requests with the same scan geometry reuse it.  Requests are
+ * admitted in arrival order whenever a slot is free and the device memory of the
+ * geometries in use stays within hbm_budget_bytes (idle geometries are released,
+ * least recently used first).  Admitted requests join the running batch between
+ * iterations, so requests that arrive while others run overlap on the device; each
+ * result is bitwise the one cbct_reconstruct gives for the same request.  The
+ * server uses the device that is current when it is created. */
+typedef struct cbct_server cbct_server;
+typedef struct {
+    cbct_geometry_desc desc;  /* scan and grid                                        */
+    const double *angles_host;/* n_angles radians, copied at submit                    */
+    int n_angles;
+    const float *Y_dev;       /* sinogram [n_angles][nv][nu]; valid until completion    */
+    double mu;
+    int iters, levels;
+    cbct_options opts;        /* as for cbct_reconstruct; betas copied at submit;
+                                 energy_trace, beta_out, kernel_ms ignored             */
+    float *f_out_dev;         /* volume [nz][ny][nx]; written before completion        */
+} cbct_server_request;
+typedef struct {
+    cbct_status status;       /* CBCT_OK, or the error that ended the request          */
+    double latency_s;         /* submit to completion                                  */
+    double queue_s;           /* submit to admission                                   */
+    double betas[8];          /* beta used per level (index 0 = finest)                */
+} cbct_result;
+typedef struct {
+    int queued, running, slots_in_use;
+    uint64_t completed;
+    size_t hbm_in_use;        /* bytes held by resident geometries                     */
+    double busy_s;            /* worker time spent issuing and waiting for device work */
+} cbct_server_stats;
+cbct_status cbct_server_create(size_t hbm_budget_bytes, int max_slots, int use_graphs, cbct_server **out);
+/* Queue a request (returns at once).  Malformed requests: CBCT_ERR_INVALID_ARG;
+ * requests that could never fit the budget: CBCT_ERR_BUSY. */
+cbct_status cbct_server_submit(cbct_server *srv, const cbct_server_request *req, uint64_t *ticket);
+/* Wait up to timeout_ms (< 0: no limit) for a ticket; CBCT_ERR_TIMEOUT if it has not
+ * finished (the ticket stays valid).  Returns the request's status and fills
+ * *result (nullable); a ticket can be collected once. */
+cbct_status cbct_server_wait(cbct_server *srv, uint64_t ticket, int timeout_ms, cbct_result *result);
+/* Cancel a request that is still queued (CBCT_ERR_BUSY if it already runs). */
+cbct_status cbct_server_cancel(cbct_server *srv, uint64_t ticket);
+cbct_status cbct_server_get_stats(cbct_server *srv, cbct_server_stats *out);
+/* Finish running requests, cancel queued ones, release everything. */
+void cbct_server_destroy(cbct_server *srv);
+/* Test hook: the next n geometry set-ups inside the server fail as if out of memory
+ * (no device memory is touched), so failure handling can be exercised safely. */
+void cbct_debug_fail_next_allocations(int n);
 
 /* Largest volume (nx*ny*nz) that cbct_tv_energy_noalloc accepts. */
 #define CBCT_NOALLOC_MAX_VOXELS 33554432

@@ -43,7 +43,33 @@ class Options(C.Structure):
                 ("power_iters", C.c_int), ("start_level", C.c_int), ("f_init_dev", C.c_void_p),
                 ("use_graphs", C.c_int), ("energy_trace", C.POINTER(C.c_double)),
                 ("beta_out", C.POINTER(C.c_double)), ("kernel_ms", C.POINTER(C.c_float)),
-                ("kernel_launches", C.POINTER(C.c_int))]
+                ("kernel_launches", C.POINTER(C.c_int)), ("reuse_lambda", C.c_int)]
+
+
+class Request(C.Structure):
+    _fields_ = [("geom", C.c_void_p), ("Y_dev", C.c_void_p), ("mu", C.c_double), ("iters", C.c_int),
+                ("levels", C.c_int), ("opts", C.POINTER(Options)), ("f_out_dev", C.c_void_p)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("proj_threads", C.c_int), ("bp_vpl", C.c_int), ("bp_threads", C.c_int),
+                ("proj_ms", C.c_float), ("bp_ms", C.c_float)]
+
+
+class ServerRequest(C.Structure):
+    _fields_ = [("desc", GeometryDesc), ("angles_host", C.POINTER(C.c_double)), ("n_angles", C.c_int),
+                ("Y_dev", C.c_void_p), ("mu", C.c_double), ("iters", C.c_int), ("levels", C.c_int),
+                ("opts", Options), ("f_out_dev", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("latency_s", C.c_double), ("queue_s", C.c_double),
+                ("betas", C.c_double * 8)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("queued", C.c_int), ("running", C.c_int), ("slots_in_use", C.c_int),
+                ("completed", C.c_uint64), ("hbm_in_use", C.c_size_t), ("busy_s", C.c_double)]
 
 
 def _load() -> C.CDLL:
@@ -67,6 +93,16 @@ _SIGS = {
     "cbct_restrict_sino": [_I, _I, _I, _P, _P, _V],
     "cbct_prolong_vol": [_I, _I, _I, _P, _I, _I, _I, _P, _V],
     "cbct_tv_energy_noalloc": [_I, _I, _I, _D, _D, _D, _D, _P, _P, _V],
+    "cbct_reconstruct_batch": [C.POINTER(Request), _I, _I, _V],
+    "cbct_autotune": [_P, _I, C.POINTER(Tuning), _V],
+    "cbct_set_tuning": [_P, _I, C.POINTER(Tuning)],
+    "cbct_server_create": [C.c_size_t, _I, _I, C.POINTER(C.c_void_p)],
+    "cbct_server_submit": [_P, C.POINTER(ServerRequest), C.POINTER(C.c_uint64)],
+    "cbct_server_wait": [_P, C.c_uint64, _I, C.POINTER(Result)],
+    "cbct_server_cancel": [_P, C.c_uint64],
+    "cbct_server_get_stats": [_P, C.POINTER(ServerStats)],
+    "cbct_server_destroy": [_P],
+    "cbct_debug_fail_next_allocations": [_I],
     "cbct_last_error": [],
     "cbct_version": [],
 }
@@ -74,7 +110,8 @@ for _name, _args in _SIGS.items():
     _fn = getattr(lib, _name)
     _fn.argtypes = _args
     _fn.restype = C.c_char_p if _name in ("cbct_last_error", "cbct_version") else (
-        None if _name == "cbct_geometry_destroy" else C.c_int)
+        None if _name in ("cbct_geometry_destroy", "cbct_server_destroy", "cbct_debug_fail_next_allocations")
+        else C.c_int)
 
 
 def header_functions(path: str = HEADER):
@@ -200,9 +237,32 @@ def cbct_energy(g: Geometry, Y, f, mu, eps):
     return np.array(out[:])
 
 
+def make_options(levels, *, beta=0.0, betas=None, eps=0.0, inner_iters=0, clamp_mode=0, sino_fp16=False,
+                 power_iters=0, f_init=None, start_level=0, use_graphs=False, reuse_lambda=False, keep=None):
+    """cbct_options from keyword arguments; `keep` (a list) holds arrays the struct points to."""
+    o = Options()
+    o.beta = beta
+    if betas is not None:
+        bet = np.ascontiguousarray(betas, dtype=np.float64)
+        if keep is not None:
+            keep.append(bet)
+        o.betas = bet.ctypes.data_as(C.POINTER(C.c_double))
+    o.eps = eps
+    o.inner_iters = inner_iters
+    o.clamp_mode = clamp_mode
+    o.sino_fp16 = int(bool(sino_fp16))
+    o.power_iters = power_iters
+    o.start_level = start_level
+    o.f_init_dev = _ptr(f_init, "f_init") if f_init is not None else None
+    o.use_graphs = int(bool(use_graphs))
+    o.reuse_lambda = int(bool(reuse_lambda))
+    return o
+
+
 def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=None, *, beta=0.0,
                      betas=None, eps=0.0, inner_iters=0, clamp_mode=0, sino_fp16=False, power_iters=0,
-                     f_init=None, start_level=0, use_graphs=False, trace=False, kernel_times=False):
+                     f_init=None, start_level=0, use_graphs=False, trace=False, kernel_times=False,
+                     reuse_lambda=False):
     """Returns f_out, or (f_out, info) when trace/kernel_times is requested; info holds
     'trace' [levels][iters][3], 'betas' [levels], 'kernel_ms'/'kernel_launches'."""
     f_out = _empty(g.vol_shape) if f_out is None else f_out
@@ -219,6 +279,7 @@ def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=N
     o.start_level = start_level
     o.f_init_dev = _ptr(f_init, "f_init") if f_init is not None else None
     o.use_graphs = int(bool(use_graphs))
+    o.reuse_lambda = int(bool(reuse_lambda))
     tr = np.full((levels, max(iters, 1), 3), np.nan) if trace else None
     if trace:
         o.energy_trace = tr.ctypes.data_as(C.POINTER(C.c_double))
@@ -240,6 +301,106 @@ def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=N
         info["kernel_ms"] = dict(zip(KERNEL_CLASSES, list(km)))
         info["kernel_launches"] = dict(zip(KERNEL_CLASSES, list(kl)))
     return f_out, info
+
+
+def cbct_reconstruct_batch(requests, use_graphs=False):
+    """requests: list of dicts with keys geom (Geometry), Y, mu, iters, levels, f_out
+    (optional) and any cbct_reconstruct keyword (betas, beta, inner_iters, ...),
+    plus trace=True to get the energy trace.  Returns (volumes, infos)."""
+    keep, reqs, outs, infos = [], [], [], []
+    for r in requests:
+        g = r["geom"]
+        levels = r["levels"]
+        kw = {k: v for k, v in r.items() if k in ("beta", "betas", "eps", "inner_iters", "clamp_mode", "sino_fp16",
+                                                  "power_iters", "f_init", "start_level", "reuse_lambda")}
+        o = make_options(levels, keep=keep, **kw)
+        info = {"betas": np.zeros(levels)}
+        o.beta_out = info["betas"].ctypes.data_as(C.POINTER(C.c_double))
+        if r.get("trace"):
+            info["trace"] = np.full((levels, max(r["iters"], 1), 3), np.nan)
+            o.energy_trace = info["trace"].ctypes.data_as(C.POINTER(C.c_double))
+        keep.append(o)
+        f = r.get("f_out")
+        f = _empty(g.vol_shape) if f is None else f
+        outs.append(f)
+        infos.append(info)
+        reqs.append(Request(g.handle, _ptr(r["Y"], "Y"), r["mu"], r["iters"], levels, C.pointer(o), _ptr(f, "f_out")))
+    arr = (Request * len(reqs))(*reqs)
+    _check(lib.cbct_reconstruct_batch(arr, len(reqs), int(bool(use_graphs)), _stream()))
+    for info, r in zip(infos, requests):
+        if "trace" in info:
+            info["trace"] = info["trace"][:, :r["iters"]]
+    return outs, infos
+
+
+def cbct_autotune(g: Geometry, level: int = 0) -> dict:
+    t = Tuning()
+    _check(lib.cbct_autotune(g.handle, level, C.byref(t), _stream()))
+    return dict(proj_threads=t.proj_threads, bp_vpl=t.bp_vpl, bp_threads=t.bp_threads, proj_ms=t.proj_ms,
+                bp_ms=t.bp_ms)
+
+
+def cbct_set_tuning(g: Geometry, level: int, tuning: dict):
+    t = Tuning(int(tuning.get("proj_threads", 0)), int(tuning.get("bp_vpl", 0)), int(tuning.get("bp_threads", 0)),
+               0.0, 0.0)
+    _check(lib.cbct_set_tuning(g.handle, level, C.byref(t)))
+
+
+class Server:
+    """Owning wrapper of cbct_server (continuous-batching reconstruction server)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int, use_graphs: bool = False):
+        h = C.c_void_p()
+        _check(lib.cbct_server_create(int(hbm_budget_bytes), max_slots, int(bool(use_graphs)), C.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, geom: dict, Y, mu, iters, levels, f_out, **kw) -> int:
+        keep = []
+        o = make_options(levels, keep=keep, **kw)
+        ang = np.ascontiguousarray(geom["angles"], dtype=np.float64)
+        keep.append(ang)
+        req = ServerRequest(make_desc(geom), ang.ctypes.data_as(C.POINTER(C.c_double)), len(ang), _ptr(Y, "Y"),
+                            mu, iters, levels, o, _ptr(f_out, "f_out"))
+        t = C.c_uint64()
+        _check(lib.cbct_server_submit(self.handle, C.byref(req), C.byref(t)))
+        self._keep[t.value] = (keep, Y, f_out)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> dict:
+        r = Result()
+        st = lib.cbct_server_wait(self.handle, ticket, timeout_ms, C.byref(r))
+        if st == 4:  # timeout: the ticket stays valid
+            raise CbctError(st, cbct_last_error())
+        self._keep.pop(ticket, None)
+        out = dict(status=r.status, latency_s=r.latency_s, queue_s=r.queue_s, betas=list(r.betas))
+        if st != 0:
+            raise CbctError(st, f"request failed: {out}")
+        return out
+
+    def cancel(self, ticket: int):
+        _check(lib.cbct_server_cancel(self.handle, ticket))
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib.cbct_server_get_stats(self.handle, C.byref(s)))
+        return dict(queued=s.queued, running=s.running, slots_in_use=s.slots_in_use, completed=s.completed,
+                    hbm_in_use=s.hbm_in_use, busy_s=s.busy_s)
+
+    def close(self):
+        if self.handle:
+            lib.cbct_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cbct_debug_fail_next_allocations(n: int):
+    lib.cbct_debug_fail_next_allocations(n)
 
 
 def cbct_tv_energy_noalloc(f, h, eps, out=None):

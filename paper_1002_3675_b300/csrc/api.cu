@@ -12,6 +12,7 @@
 
 #include <algorithm>
 
+#include "batch.h"
 #include "cbct_internal.h"
 
 using namespace cbct;
@@ -19,6 +20,52 @@ using namespace cbct;
 namespace cbct {
 const char *last_error();
 }
+
+namespace cbct {
+
+double default_eps(const Level *L) { return 2e-5 / std::min(L->hx, std::min(L->hy, L->hz)); }
+
+double tv_lipschitz(const Level *L, double eps) {
+    return 4.0 / eps * (1.0 / (L->hx * L->hx) + 1.0 / (L->hy * L->hy) + 1.0 / (L->hz * L->hz));
+}
+
+double gamma_of(const Level *L, double mu) {
+    return 2.0 * mu * (double)vol_elems(L->gd) / (double)sino_elems(L->gd);
+}
+
+cbct_status ensure_trace(cbct_geometry *G, size_t n) {
+    if (!G->dscalars) {
+        // layout: [0..63] scalars (lambda etc.), counter separately
+        if (cudaMalloc(&G->dscalars, sizeof(double) * 64) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaMalloc of scalar scratch failed");
+            return CBCT_ERR_OOM;
+        }
+        if (cudaMalloc(&G->dcounter, sizeof(int) * 4) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaMalloc of counter failed");
+            return CBCT_ERR_OOM;
+        }
+    }
+    (void)n;
+    return CBCT_OK;
+}
+
+TvArgs tv_args(const Level *L, const SolveParams &P) {
+    TvArgs a;
+    a.nx = L->nx;
+    a.ny = L->ny;
+    a.nz = L->nz;
+    a.ihx = (float)(1.0 / L->hx);
+    a.ihy = (float)(1.0 / L->hy);
+    a.ihz = (float)(1.0 / L->hz);
+    a.s = P.s;
+    a.beta = P.beta;
+    a.eps2 = P.eps2;
+    return a;
+}
+
+}  // namespace cbct
 
 namespace {
 
@@ -88,59 +135,6 @@ struct Launch {  // wraps one kernel launch with optional timing
     Launch(Prof &pp, int cc) : p(pp), c(cc) { p.begin(c); }
     ~Launch() { p.end(); }
 };
-
-double default_eps(const Level *L) { return 2e-5 / std::min(L->hx, std::min(L->hy, L->hz)); }
-
-double tv_lipschitz(const Level *L, double eps) {
-    return 4.0 / eps * (1.0 / (L->hx * L->hx) + 1.0 / (L->hy * L->hy) + 1.0 / (L->hz * L->hz));
-}
-
-double gamma_of(const Level *L, double mu) {
-    return 2.0 * mu * (double)vol_elems(L->gd) / (double)sino_elems(L->gd);
-}
-
-cbct_status ensure_trace(cbct_geometry *G, size_t n) {
-    if (!G->dscalars) {
-        // layout: [0..63] scalars (lambda etc.), counter separately
-        if (cudaMalloc(&G->dscalars, sizeof(double) * 64) != cudaSuccess) {
-            cudaGetLastError();
-            set_error("cudaMalloc of scalar scratch failed");
-            return CBCT_ERR_OOM;
-        }
-        if (cudaMalloc(&G->dcounter, sizeof(int) * 4) != cudaSuccess) {
-            cudaGetLastError();
-            set_error("cudaMalloc of counter failed");
-            return CBCT_ERR_OOM;
-        }
-    }
-    (void)n;
-    return CBCT_OK;
-}
-
-struct SolveParams {
-    float c;        // gamma / beta
-    float s;        // inner step 1 / (beta + L_TV)
-    float beta;
-    float eps2;
-    int M;
-    int clamp_mode;
-    bool fp16;
-    double inv_nv, mu_over_nr;
-};
-
-TvArgs tv_args(const Level *L, const SolveParams &P) {
-    TvArgs a;
-    a.nx = L->nx;
-    a.ny = L->ny;
-    a.nz = L->nz;
-    a.ihx = (float)(1.0 / L->hx);
-    a.ihy = (float)(1.0 / L->hy);
-    a.ihz = (float)(1.0 / L->hz);
-    a.s = P.s;
-    a.beta = P.beta;
-    a.eps2 = P.eps2;
-    return a;
-}
 
 // Steps 2 and 3: M sweeps from src0 into L->f (ping-pong through A and B).
 // partial_e1 (optional) receives the E1 partials of the first sweep's input.
@@ -289,7 +283,7 @@ cbct_status check_geometry_desc(const cbct_geometry_desc *d) {
 }  // namespace
 
 // Device energy-trace buffer owned by the geometry (grown on demand).
-static cbct_status get_trace(cbct_geometry *G, size_t n, double **out) {
+cbct_status cbct::get_trace(cbct_geometry *G, size_t n, double **out) {
     if (G->dtrace_len < n) {
         cudaFree(G->dtrace);
         G->dtrace = nullptr;
@@ -302,6 +296,90 @@ static cbct_status get_trace(cbct_geometry *G, size_t n, double **out) {
         G->dtrace_len = n;
     }
     *out = G->dtrace;
+    return CBCT_OK;
+}
+
+cbct_status cbct::solve_params(const Level *L, double mu, double beta, double eps, int M, int clamp_mode, bool fp16,
+                                SolveParams *P) {
+    if (!(beta > 0) || !isfinite(beta)) {
+        set_error("beta must be > 0");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    if (!(eps > 0) || !isfinite(eps)) {
+        set_error("eps must be > 0");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    if (M < 1 || M > 10000) {
+        set_error("inner_iters must be in 1..10000");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    if (clamp_mode != 0 && clamp_mode != 1) {
+        set_error("clamp_mode must be 0 or 1");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    const double gam = gamma_of(L, mu);
+    P->c = (float)(gam / beta);
+    P->s = (float)(1.0 / (beta + tv_lipschitz(L, eps)));
+    P->beta = (float)beta;
+    P->eps2 = (float)(eps * eps);
+    P->M = M;
+    P->clamp_mode = clamp_mode;
+    P->fp16 = fp16;
+    P->inv_nv = 1.0 / (double)vol_elems(L->gd);
+    P->mu_over_nr = mu / (double)sino_elems(L->gd);
+    return CBCT_OK;
+}
+
+cbct_status cbct::validate_request(cbct_geometry *G, const float *Y_dev, double mu, int iters, int levels,
+                                  const cbct_options *o, float *f_out_dev) {
+    if (!G) {
+        set_error("geometry is null");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    if (!aligned16(Y_dev) || !aligned16(f_out_dev)) {
+        set_error("Y_dev and f_out_dev must be non-null 16-byte aligned device pointers");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    if (!(mu > 0) || !isfinite(mu) || iters < 0) {
+        set_error("need mu > 0 and iters >= 0");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    const cbct_geometry_desc &d = G->desc;
+    if (levels < 1 || levels > 8) {
+        set_error("levels must be in 1..8");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    const int need = 1 << (levels - 1);
+    if (d.nx < need || d.ny < need || d.nz < need || d.nu < need || d.nv < need) {
+        set_error("every volume and imager axis needs at least 2^(levels-1) = %d samples", need);
+        return CBCT_ERR_INVALID_ARG;
+    }
+    if (o) {
+        if (o->clamp_mode != 0 && o->clamp_mode != 1) {
+            set_error("clamp_mode must be 0 or 1");
+            return CBCT_ERR_INVALID_ARG;
+        }
+        if (o->inner_iters < 0 || o->inner_iters > 10000 || o->power_iters < 0) {
+            set_error("inner_iters must be in 0..10000 and power_iters >= 0");
+            return CBCT_ERR_INVALID_ARG;
+        }
+        if (o->betas)
+            for (int l = 0; l < levels; ++l)
+                if (!(o->betas[l] > 0) || !isfinite(o->betas[l])) {
+                    set_error("betas[%d] must be > 0", l);
+                    return CBCT_ERR_INVALID_ARG;
+                }
+        if (o->f_init_dev) {
+            if (o->start_level < 0 || o->start_level >= levels) {
+                set_error("start_level must be in 0..levels-1");
+                return CBCT_ERR_INVALID_ARG;
+            }
+            if (!aligned16(o->f_init_dev)) {
+                set_error("f_init_dev must be a 16-byte aligned device pointer");
+                return CBCT_ERR_INVALID_ARG;
+            }
+        }
+    }
     return CBCT_OK;
 }
 
@@ -357,7 +435,6 @@ void cbct_geometry_destroy(cbct_geometry *G) {
     for (auto *L : G->levels) free_level(L);
     cudaFree(G->dscalars);
     cudaFree(G->dcounter);
-    cudaFree(G->io_vol);
     cudaFree(G->dtrace);
     delete G;
 }
@@ -411,36 +488,6 @@ cbct_status cbct_backproject(cbct_geometry *G, const float *y_dev, float *f_dev,
     return CBCT_OK;
 }
 
-static cbct_status solve_params(const Level *L, double mu, double beta, double eps, int M, int clamp_mode, bool fp16,
-                                SolveParams *P) {
-    if (!(beta > 0) || !isfinite(beta)) {
-        set_error("beta must be > 0");
-        return CBCT_ERR_INVALID_ARG;
-    }
-    if (!(eps > 0) || !isfinite(eps)) {
-        set_error("eps must be > 0");
-        return CBCT_ERR_INVALID_ARG;
-    }
-    if (M < 1 || M > 10000) {
-        set_error("inner_iters must be in 1..10000");
-        return CBCT_ERR_INVALID_ARG;
-    }
-    if (clamp_mode != 0 && clamp_mode != 1) {
-        set_error("clamp_mode must be 0 or 1");
-        return CBCT_ERR_INVALID_ARG;
-    }
-    const double gam = gamma_of(L, mu);
-    P->c = (float)(gam / beta);
-    P->s = (float)(1.0 / (beta + tv_lipschitz(L, eps)));
-    P->beta = (float)beta;
-    P->eps2 = (float)(eps * eps);
-    P->M = M;
-    P->clamp_mode = clamp_mode;
-    P->fp16 = fp16;
-    P->inv_nv = 1.0 / (double)vol_elems(L->gd);
-    P->mu_over_nr = mu / (double)sino_elems(L->gd);
-    return CBCT_OK;
-}
 
 cbct_status cbct_tv_prox(cbct_geometry *G, const float *g_dev, float *f_inout_dev, double beta, double eps,
                          int inner_iters, cudaStream_t s) {
@@ -633,9 +680,13 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
             beta = o.beta;
         } else {
             double lam = 0.0;
-            ST(power_iteration(G, L, K, &lam, prof, s));
-            L->lambda = lam;
-            L->lambda_iters = K;
+            if (o.reuse_lambda && L->lambda_iters == K) {
+                lam = L->lambda;
+            } else {
+                ST(power_iteration(G, L, K, &lam, prof, s));
+                L->lambda = lam;
+                L->lambda_iters = K;
+            }
             beta = std::max(10.0 * mu, 1.05 * gamma_of(L, mu) * lam);
         }
         if (o.beta_out) o.beta_out[l] = beta;

@@ -1,0 +1,836 @@
+// Batched reconstruction: many requests advance together, one Algorithm A1
+// iteration (or one power-iteration step) per tick, every stage of every request in
+// one persistent launch per stage.
+//
+// Each launch reads a device table of per-request items (geometry block, buffers,
+// mode) and a prefix table of per-request tile counts; a block (or warp) maps its
+// global tile index to (request, local tile) and runs the same tile body as the
+// single-request kernels.  Every request is computed with exactly the arithmetic of
+// a single-request call, in the same order, so its result is bitwise the same alone
+// and in any mix.  The item tables are rebuilt only when the set of active stages
+// changes; while it does not, a tick's launches can be replayed as a CUDA graph.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "batch.h"
+#include "bp_tile.cuh"
+#include "project_tile.cuh"
+#include "tv_tile.cuh"
+
+namespace cbct {
+
+// ---------------------------------------------------------------------------------
+// batched kernels
+// ---------------------------------------------------------------------------------
+
+struct ProjItem {
+    GeoDev G;
+    const float *vol;
+    const float *y32;
+    const __half *y16;
+    float *out;
+    double *partial;
+    int mode;
+};
+
+struct BpItem {
+    GeoDev G;
+    const float *rs;
+    const float *fin;
+    float *out;
+    float c;
+    int mode;
+};
+
+struct TvItem {
+    TvArgs A;
+    const float *fin;
+    const float *g;
+    float *fout;
+    double *partial;
+    int clamp;
+    int e1;
+};
+
+struct VecItem {  // power-iteration helpers on one volume
+    const float *x;
+    const float *y;
+    float *out;
+    double *partial;
+    double *lam;
+    float *scale;
+    long n;
+    int nblk;
+};
+
+struct EnItem {
+    const double *pe2;
+    const double *pe1;
+    double *trace;
+    int *counter;
+    double inv_nv, mu_over_nr;
+    int n2, n1;
+};
+
+// largest r with start[r] <= t
+__device__ __forceinline__ int find_item(const long *__restrict__ start, int n, long t) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(start + mid) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void copy_words(void *dst, const void *src, int bytes, int lane, int nthreads) {
+    const int *s = (const int *)src;
+    int *d = (int *)dst;
+    for (int q = lane; q < bytes / 4; q += nthreads) d[q] = s[q];
+}
+
+__global__ void __launch_bounds__(PROJ_MAX_THREADS, 2)
+k_project_batch(const ProjItem *__restrict__ items, const long *__restrict__ start, int n, long total) {
+    extern __shared__ float smem[];
+    __shared__ ProjItem it;
+    for (long t = blockIdx.x; t < total; t += gridDim.x) {
+        const int r = find_item(start, n, t);
+        copy_words(&it, items + r, sizeof(ProjItem), threadIdx.x, blockDim.x);
+        __syncthreads();
+        const long local = t - start[r];
+        const int a = (int)(local % it.G.nu);
+        const long rest = local / it.G.nu;
+        const int ia = (int)(rest % it.G.na), zc = (int)(rest / it.G.na);
+        project_tile(it.G, it.mode, it.vol, it.y32, it.y16, it.out, it.partial, a, ia, zc, smem);
+        __syncthreads();
+    }
+}
+
+template <int VPL>
+__global__ void __launch_bounds__(BP_THREADS, 8)
+k_bp_batch(const BpItem *__restrict__ items, const long *__restrict__ start, int n, long total) {
+    __shared__ BpItem it[BP_THREADS / 32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long stride = (long)gridDim.x * (BP_THREADS / 32);
+    for (long t = (long)blockIdx.x * (BP_THREADS / 32) + w; t < total; t += stride) {
+        const int r = find_item(start, n, t);
+        copy_words(&it[w], items + r, sizeof(BpItem), lane, 32);
+        __syncwarp();
+        bp_warp<VPL>(it[w].G, it[w].mode, it[w].rs, it[w].fin, it[w].out, it[w].c, t - start[r]);
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(TV_THREADS)
+k_tv_batch(const TvItem *__restrict__ items, const long *__restrict__ start, int n, long total) {
+    for (long t = blockIdx.x; t < total; t += gridDim.x) {
+        const int r = find_item(start, n, t);
+        const TvItem it = items[r];
+        const long blk = t - start[r];
+        if (it.clamp) {
+            if (it.e1) tv_block<true, true>(it.A, it.fin, it.g, it.fout, it.partial, blk);
+            else tv_block<true, false>(it.A, it.fin, it.g, it.fout, it.partial, blk);
+        } else {
+            if (it.e1) tv_block<false, true>(it.A, it.fin, it.g, it.fout, it.partial, blk);
+            else tv_block<false, false>(it.A, it.fin, it.g, it.fout, it.partial, blk);
+        }
+        __syncthreads();
+    }
+}
+
+// per-block partials of <x, y> and <y, y> (same partition and arithmetic as k_dot2)
+__global__ void k_dot_batch(const VecItem *__restrict__ items, const long *__restrict__ start, int n, long total) {
+    __shared__ float a[8], b[8];
+    for (long t = blockIdx.x; t < total; t += gridDim.x) {
+        const int r = find_item(start, n, t);
+        const VecItem it = items[r];
+        const long blk = t - start[r];
+        float sxy = 0.f, syy = 0.f;
+        const long o = blk * 256 + threadIdx.x;
+        if (o < it.n) {
+            const float xv = it.x[o], yv = it.y[o];
+            sxy = xv * yv;
+            syy = yv * yv;
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            sxy += __shfl_down_sync(0xffffffffu, sxy, off);
+            syy += __shfl_down_sync(0xffffffffu, syy, off);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            a[threadIdx.x >> 5] = sxy;
+            b[threadIdx.x >> 5] = syy;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s1 = 0.0, s2 = 0.0;
+            for (int w = 0; w < 8; ++w) {
+                s1 += (double)a[w];
+                s2 += (double)b[w];
+            }
+            it.partial[2 * blk] = s1;
+            it.partial[2 * blk + 1] = s2;
+        }
+        __syncthreads();
+    }
+}
+
+// lam = <x, y>, scale = 1/|y| per item (one block per item; same tree as k_power_finalize)
+__global__ void k_pfin_batch(const VecItem *__restrict__ items) {
+    const VecItem it = items[blockIdx.x];
+    __shared__ double sh1[256], sh2[256];
+    double s1 = 0.0, s2 = 0.0;
+    for (int q = threadIdx.x; q < it.nblk; q += 256) {
+        s1 += it.partial[2 * q];
+        s2 += it.partial[2 * q + 1];
+    }
+    sh1[threadIdx.x] = s1;
+    sh2[threadIdx.x] = s2;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sh1[threadIdx.x] += sh1[threadIdx.x + w];
+            sh2[threadIdx.x] += sh2[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *it.lam = sh1[0];
+        *it.scale = sh2[0] > 0.0 ? (float)(1.0 / sqrt(sh2[0])) : 0.f;
+    }
+}
+
+__global__ void k_scale_batch(const VecItem *__restrict__ items, const long *__restrict__ start, int n, long total) {
+    for (long t = blockIdx.x; t < total; t += gridDim.x) {
+        const int r = find_item(start, n, t);
+        const VecItem it = items[r];
+        const long o = (t - start[r]) * 256 + threadIdx.x;
+        if (o < it.n) it.out[o] = it.y[o] * *it.scale;
+    }
+}
+
+__device__ double block_sum_fixed_b(const double *p, int n) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int q = threadIdx.x; q < n; q += 256) s += p[q];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_energy_batch(const EnItem *__restrict__ items) {
+    const EnItem it = items[blockIdx.x];
+    const double q = block_sum_fixed_b(it.pe2, it.n2);
+    const double t = block_sum_fixed_b(it.pe1, it.n1);
+    if (threadIdx.x == 0) {
+        const int k = *it.counter;
+        const double e1 = t * it.inv_nv, e2 = q * it.mu_over_nr;
+        it.trace[3 * k + 0] = e1 + e2;
+        it.trace[3 * k + 1] = e1;
+        it.trace[3 * k + 2] = e2;
+        *it.counter = k + 1;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// engine
+// ---------------------------------------------------------------------------------
+
+static int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    }
+    return n;
+}
+
+static long grid_for(long total, int per_sm) {
+    const long cap = (long)sm_count() * per_sm;
+    return std::max(1L, std::min(total, cap));
+}
+
+#define ECK(call, what)                                      \
+    do {                                                     \
+        cudaError_t e__ = (call);                            \
+        if (e__ != cudaSuccess) return cuda_fail(e__, what); \
+    } while (0)
+#define EST(call)                        \
+    do {                                 \
+        cbct_status s__ = (call);        \
+        if (s__ != CBCT_OK) return s__;  \
+    } while (0)
+
+Engine::Engine(cudaStream_t s, bool graphs) : stream(s), use_graphs(graphs && s != 0) {}
+
+Engine::~Engine() {
+    reset_graph();
+    cudaFree(dblob);
+}
+
+void Engine::reset_graph() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+    same_ticks = 0;
+}
+
+cbct_status Engine::add(Job *j) {
+    if (!j || !j->G) {
+        set_error("engine: null job or geometry");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    for (Job *o : jobs)
+        if (o->G == j->G) {
+            set_error("engine: two jobs in flight on the same geometry");
+            return CBCT_ERR_INVALID_ARG;
+        }
+    j->phase = PH_PREPARE;
+    jobs.push_back(j);
+    signature.clear();
+    return CBCT_OK;
+}
+
+void Engine::remove_finished() {
+    const size_t before = jobs.size();
+    jobs.erase(std::remove_if(jobs.begin(), jobs.end(), [](Job *j) { return j->phase == PH_DONE; }), jobs.end());
+    if (jobs.size() != before) signature.clear();
+}
+
+// Per-job work outside the batched stages: data pyramid, level start.
+cbct_status Engine::prepare(Job *j) {
+    cbct_geometry *G = j->G;
+    const cbct_options &o = j->o;
+    j->M = o.inner_iters > 0 ? o.inner_iters : 10;
+    j->K = o.power_iters > 0 ? o.power_iters : 30;
+    j->fp16 = o.sino_fp16 != 0;
+    j->Ls.assign(j->levels, nullptr);
+    for (int l = 0; l < j->levels; ++l) {
+        EST(ensure_level(G, l, &j->Ls[l]));
+        EST(ensure_workspace(j->Ls[l], j->fp16));
+    }
+    EST(ensure_trace(G, 0));
+    double *dtrace;
+    EST(get_trace(G, 3 * (size_t)std::max(j->iters, 1), &dtrace));
+    const GeoDev &g0 = j->Ls[0]->gd;
+    ECK(launch_sino_to_internal(j->Y, j->Ls[0]->Y, j->fp16 ? j->Ls[0]->Yh : nullptr, nullptr, g0.na, g0.nu, g0.nv,
+                                stream),
+        "sinogram layout");
+    for (int l = 1; l < j->levels; ++l) {
+        const GeoDev &gp = j->Ls[l - 1]->gd;
+        ECK(launch_restrict(j->Ls[l - 1]->Y, j->Ls[l]->Y, gp.na, gp.nu, gp.nv, stream), "restriction");
+        if (j->fp16) ECK(launch_to_half(j->Ls[l]->Y, j->Ls[l]->Yh, sino_elems(j->Ls[l]->gd), stream), "half copy");
+    }
+    j->level = o.f_init_dev ? o.start_level : j->levels - 1;
+    j->phase = PH_START_LEVEL;
+    return CBCT_OK;
+}
+
+cbct_status Engine::start_level(Job *j) {
+    Level *L = j->Ls[j->level];
+    const GeoDev &g = L->gd;
+    const bool first = (j->level == (j->o.f_init_dev ? j->o.start_level : j->levels - 1));
+    if (first) {
+        if (j->o.f_init_dev)
+            ECK(launch_vol_to_internal(j->o.f_init_dev, L->f, g.nx, g.ny, g.nz, stream), "volume layout");
+        else
+            ECK(cudaMemsetAsync(L->f, 0, vol_elems(g) * 4, stream), "zero start");
+    } else {
+        const GeoDev &gc = j->Ls[j->level + 1]->gd;
+        ECK(launch_prolong(j->Ls[j->level + 1]->f, gc.nx, gc.ny, gc.nz, L->f, g.nx, g.ny, g.nz, stream),
+            "prolongation");
+    }
+    double beta = 0.0;
+    if (j->o.betas) beta = j->o.betas[j->level];
+    else if (j->o.beta > 0) beta = j->o.beta;
+    if (beta > 0) return begin_fbs(j, beta);
+    if (j->o.reuse_lambda && L->lambda_iters == j->K)
+        return begin_fbs(j, std::max(10.0 * j->mu, 1.05 * gamma_of(L, j->mu) * L->lambda));
+    ECK(launch_fill(L->A, (float)(1.0 / sqrt((double)vol_elems(g))), vol_elems(g), stream), "fill");
+    j->pi_it = 0;
+    j->phase = PH_POWER;
+    return CBCT_OK;
+}
+
+cbct_status Engine::begin_fbs(Job *j, double beta) {
+    Level *L = j->Ls[j->level];
+    j->beta = beta;
+    if (j->o.beta_out) j->o.beta_out[j->level] = beta;
+    const double eps = j->o.eps > 0 ? j->o.eps : default_eps(L);
+    EST(solve_params(L, j->mu, beta, eps, j->M, j->o.clamp_mode, j->fp16, &j->P));
+    ECK(cudaMemsetAsync(j->G->dcounter, 0, sizeof(int), stream), "counter reset");
+    j->it = 0;
+    j->phase = j->iters > 0 ? PH_FBS : PH_LEVEL_DONE;
+    return CBCT_OK;
+}
+
+cbct_status Engine::finish_level(Job *j) {
+    Level *L = j->Ls[j->level];
+    if (j->o.energy_trace && j->iters > 0) {
+        double *dst = j->o.energy_trace + 3 * (size_t)j->iters * (j->levels - 1 - j->level);
+        ECK(cudaMemcpy(dst, j->G->dtrace, 3 * sizeof(double) * j->iters, cudaMemcpyDeviceToHost), "trace");
+    }
+    if (j->level == 0) {
+        const GeoDev &g = L->gd;
+        ECK(launch_vol_to_api(L->f, j->f_out, g.nx, g.ny, g.nz, stream), "volume layout");
+        j->phase = PH_DONE;
+        j->done_event_pending = true;
+        return CBCT_OK;
+    }
+    j->level -= 1;
+    j->phase = PH_START_LEVEL;
+    return CBCT_OK;
+}
+
+// Rebuild the item tables for the current set of (job, phase) pairs.
+cbct_status Engine::build_tables() {
+    const size_t ALIGN = 256;
+    auto align = [&](size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); };
+    hproj.clear();
+    for (auto &v : hbp) v.clear();
+    hdot.clear();
+    htv.clear();
+    hen.clear();
+    std::vector<long> pstart, dstart;
+    std::vector<long> bpstart[4];
+    std::vector<std::vector<long>> tvstart;
+    long ptot = 0, dtot = 0, bptot[4] = {0, 0, 0, 0};
+    proj_threads = 32;
+    max_m = 0;
+    copies.clear();
+    tv_energy_jobs.clear();
+    for (Job *j : jobs) {
+        if (j->phase != PH_POWER && j->phase != PH_FBS) continue;
+        Level *L = j->Ls[j->level];
+        const GeoDev &g = L->gd;
+        const bool power = j->phase == PH_POWER;
+        proj_threads = std::max(proj_threads, project_threads(g));
+        ProjItem pi;
+        pi.G = g;
+        pi.vol = power ? L->A : L->f;
+        pi.y32 = (!power && !j->fp16) ? L->Y : nullptr;
+        pi.y16 = (!power && j->fp16) ? L->Yh : nullptr;
+        pi.out = L->rs;
+        pi.partial = power ? nullptr : L->partial;
+        pi.mode = power ? PROJ_SCALED : (j->fp16 ? PROJ_RESID16 : PROJ_RESID32);
+        hproj.push_back(pi);
+        const int vpl = (g.bp_vpl >= 1 && g.bp_vpl <= 4) ? g.bp_vpl : bp_default_vpl(g);
+        BpItem bi;
+        bi.G = g;
+        bi.rs = L->rs;
+        bi.fin = power ? nullptr : L->f;
+        bi.out = power ? L->B : L->g;
+        bi.c = power ? 0.f : j->P.c;
+        bi.mode = power ? BP_PLAIN : BP_STEP;
+        hbp[vpl - 1].push_back(bi);
+        bpstart[vpl - 1].push_back(bptot[vpl - 1]);
+        long wt = vpl == 1 ? bp_warp_tiles<1>(g) : vpl == 2 ? bp_warp_tiles<2>(g) : vpl == 3 ? bp_warp_tiles<3>(g)
+                                                                                      : bp_warp_tiles<4>(g);
+        bptot[vpl - 1] += wt;
+        if (power) {
+            VecItem vi;
+            vi.x = L->A;
+            vi.y = L->B;
+            vi.out = L->A;
+            vi.partial = L->partial;
+            vi.lam = j->G->dscalars;
+            vi.scale = (float *)(j->G->dscalars + 1);
+            vi.n = (long)vol_elems(g);
+            vi.nblk = (int)((vi.n + 255) / 256);
+            hdot.push_back(vi);
+            dstart.push_back(dtot);
+            dtot += vi.nblk;
+        } else {
+            max_m = std::max(max_m, j->P.M);
+            if (j->P.clamp_mode == 1) tv_energy_jobs.push_back(j);
+            const size_t np = project_partials(g);
+            EnItem ei;
+            ei.pe2 = L->partial;
+            ei.n2 = (int)np;
+            ei.pe1 = L->partial + np;
+            ei.n1 = (int)tv_partials(g.nx, g.ny, g.nz);
+            ei.inv_nv = j->P.inv_nv;
+            ei.mu_over_nr = j->P.mu_over_nr;
+            ei.trace = j->G->dtrace;
+            ei.counter = j->G->dcounter;
+            hen.push_back(ei);
+        }
+        pstart.push_back(ptot);
+        ptot += (long)g.nu * g.na * ((g.nv + project_threads(g) - 1) / project_threads(g));
+    }
+    // TV sweeps: for each m, the jobs with m < M (ping-pong as in the single path)
+    htv.assign(max_m, {});
+    tvstart.assign(max_m, {});
+    tvtot.assign(max_m, 0);
+    for (Job *j : jobs) {
+        if (j->phase != PH_FBS) continue;
+        Level *L = j->Ls[j->level];
+        const TvArgs ta = tv_args(L, j->P);
+        const float *src = j->P.clamp_mode == 0 ? L->f : L->g;
+        const long nb = (long)tv_partials(L->nx, L->ny, L->nz);
+        const size_t np = project_partials(L->gd);
+        for (int m = 0; m < j->P.M; ++m) {
+            const bool last = m == j->P.M - 1;
+            float *dst = last ? L->f : (m % 2 == 0 ? L->A : L->B);
+            if (dst == src) dst = L->A;
+            TvItem ti;
+            ti.A = ta;
+            ti.fin = src;
+            ti.g = L->g;
+            ti.fout = dst;
+            ti.partial = L->partial + np;
+            ti.clamp = (j->P.clamp_mode == 0 || last) ? 1 : 0;
+            ti.e1 = (m == 0 && j->P.clamp_mode == 0) ? 1 : 0;
+            htv[m].push_back(ti);
+            tvstart[m].push_back(tvtot[m]);
+            tvtot[m] += nb;
+            src = dst;
+        }
+        if (src != L->f) copies.push_back({L->f, src, vol_elems(L->gd) * 4});
+    }
+    ptotal = ptot;
+    dtotal = dtot;
+    for (int v = 0; v < 4; ++v) bptotal[v] = bptot[v];
+
+    // one device blob: items and start tables
+    size_t off = 0;
+    auto place = [&](size_t bytes) {
+        size_t o = off;
+        off = align(off + bytes);
+        return o;
+    };
+    const size_t o_proj = place(hproj.size() * sizeof(ProjItem)), o_pst = place(pstart.size() * sizeof(long));
+    size_t o_bp[4], o_bst[4];
+    for (int v = 0; v < 4; ++v) {
+        o_bp[v] = place(hbp[v].size() * sizeof(BpItem));
+        o_bst[v] = place(bpstart[v].size() * sizeof(long));
+    }
+    const size_t o_dot = place(hdot.size() * sizeof(VecItem)), o_dst = place(dstart.size() * sizeof(long));
+    std::vector<size_t> o_tv(max_m), o_tst(max_m);
+    for (int m = 0; m < max_m; ++m) {
+        o_tv[m] = place(htv[m].size() * sizeof(TvItem));
+        o_tst[m] = place(tvstart[m].size() * sizeof(long));
+    }
+    const size_t o_en = place(hen.size() * sizeof(EnItem));
+    std::vector<char> blob(std::max<size_t>(off, 16));
+    auto put = [&](size_t o, const void *src, size_t bytes) {
+        if (bytes) memcpy(blob.data() + o, src, bytes);
+    };
+    put(o_proj, hproj.data(), hproj.size() * sizeof(ProjItem));
+    put(o_pst, pstart.data(), pstart.size() * sizeof(long));
+    for (int v = 0; v < 4; ++v) {
+        put(o_bp[v], hbp[v].data(), hbp[v].size() * sizeof(BpItem));
+        put(o_bst[v], bpstart[v].data(), bpstart[v].size() * sizeof(long));
+    }
+    put(o_dot, hdot.data(), hdot.size() * sizeof(VecItem));
+    put(o_dst, dstart.data(), dstart.size() * sizeof(long));
+    for (int m = 0; m < max_m; ++m) {
+        put(o_tv[m], htv[m].data(), htv[m].size() * sizeof(TvItem));
+        put(o_tst[m], tvstart[m].data(), tvstart[m].size() * sizeof(long));
+    }
+    put(o_en, hen.data(), hen.size() * sizeof(EnItem));
+    if (blob.size() > dblob_len) {
+        ECK(cudaStreamSynchronize(stream), "engine sync");
+        cudaFree(dblob);
+        dblob = nullptr;
+        dblob_len = 0;
+        ECK(cudaMalloc(&dblob, blob.size() * 2), "engine tables");
+        dblob_len = blob.size() * 2;
+    }
+    // the previous tick's launches may still read the old tables
+    ECK(cudaStreamSynchronize(stream), "engine sync");
+    ECK(cudaMemcpy(dblob, blob.data(), blob.size(), cudaMemcpyHostToDevice), "engine tables");
+    char *b = (char *)dblob;
+    d_proj = (ProjItem *)(b + o_proj);
+    d_pstart = (long *)(b + o_pst);
+    for (int v = 0; v < 4; ++v) {
+        d_bp[v] = (BpItem *)(b + o_bp[v]);
+        d_bstart[v] = (long *)(b + o_bst[v]);
+    }
+    d_dot = (VecItem *)(b + o_dot);
+    d_dstart = (long *)(b + o_dst);
+    d_tv.assign(max_m, nullptr);
+    d_tstart.assign(max_m, nullptr);
+    for (int m = 0; m < max_m; ++m) {
+        d_tv[m] = (TvItem *)(b + o_tv[m]);
+        d_tstart[m] = (long *)(b + o_tst[m]);
+    }
+    d_en = (EnItem *)(b + o_en);
+    return CBCT_OK;
+}
+
+static bool attr_done[64] = {};
+
+// The batched stages of one tick (no host synchronisation; capturable).
+cbct_status Engine::launch_stages() {
+    cudaStream_t s = stream;
+    for (Job *j : tv_energy_jobs) {  // literal clamp mode: E1 of f_k needs its own pass
+        Level *L = j->Ls[j->level];
+        int nb = 0;
+        ECK(launch_tv_energy(tv_args(L, j->P), L->f, L->partial + project_partials(L->gd), s, &nb), "tv energy");
+    }
+    if (!hproj.empty()) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+            cudaFuncSetAttribute(k_project_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, PROJ_SMEM);
+            attr_done[dev] = true;
+        }
+        k_project_batch<<<(unsigned)grid_for(ptotal, 2), proj_threads, PROJ_SMEM, s>>>(d_proj, d_pstart,
+                                                                                        (int)hproj.size(), ptotal);
+        ECK(cudaGetLastError(), "batched projection");
+    }
+    for (int v = 0; v < 4; ++v) {
+        if (hbp[v].empty()) continue;
+        const long nblk = grid_for((bptotal[v] + 3) / 4, 8);
+        const int n = (int)hbp[v].size();
+        if (v == 0) k_bp_batch<1><<<(unsigned)nblk, BP_THREADS, 0, s>>>(d_bp[0], d_bstart[0], n, bptotal[0]);
+        if (v == 1) k_bp_batch<2><<<(unsigned)nblk, BP_THREADS, 0, s>>>(d_bp[1], d_bstart[1], n, bptotal[1]);
+        if (v == 2) k_bp_batch<3><<<(unsigned)nblk, BP_THREADS, 0, s>>>(d_bp[2], d_bstart[2], n, bptotal[2]);
+        if (v == 3) k_bp_batch<4><<<(unsigned)nblk, BP_THREADS, 0, s>>>(d_bp[3], d_bstart[3], n, bptotal[3]);
+        ECK(cudaGetLastError(), "batched backprojection");
+    }
+    if (!hdot.empty()) {
+        const int n = (int)hdot.size();
+        k_dot_batch<<<(unsigned)grid_for(dtotal, 8), 256, 0, s>>>(d_dot, d_dstart, n, dtotal);
+        k_pfin_batch<<<(unsigned)n, 256, 0, s>>>(d_dot);
+        k_scale_batch<<<(unsigned)grid_for(dtotal, 8), 256, 0, s>>>(d_dot, d_dstart, n, dtotal);
+        ECK(cudaGetLastError(), "batched power iteration");
+    }
+    for (int m = 0; m < max_m; ++m) {
+        k_tv_batch<<<(unsigned)grid_for(tvtot[m], 8), TV_THREADS, 0, s>>>(d_tv[m], d_tstart[m], (int)htv[m].size(),
+                                                                       tvtot[m]);
+        ECK(cudaGetLastError(), "batched tv sweep");
+    }
+    for (const auto &c : copies) ECK(cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToDevice, s), "copy");
+    if (!hen.empty()) {
+        k_energy_batch<<<(unsigned)hen.size(), 256, 0, s>>>(d_en);
+        ECK(cudaGetLastError(), "batched energy");
+    }
+    return CBCT_OK;
+}
+
+cbct_status Engine::tick() {
+    // per-job transitions that are not batched
+    for (Job *j : jobs) {
+        if (j->phase == PH_PREPARE) EST(prepare(j));
+        if (j->phase == PH_START_LEVEL) EST(start_level(j));
+    }
+    std::vector<long> sig;
+    for (Job *j : jobs) {
+        if (j->phase != PH_POWER && j->phase != PH_FBS) continue;
+        sig.push_back((long)(uintptr_t)j);
+        sig.push_back(j->phase * 16 + j->level);
+    }
+    if (sig != signature) {
+        reset_graph();
+        EST(build_tables());
+        signature = sig;
+    } else {
+        ++same_ticks;
+    }
+    if (!sig.empty()) {
+        if (use_graphs && same_ticks >= 1 && !gexec) {
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                cbct_status st = launch_stages();
+                cudaError_t e = cudaStreamEndCapture(stream, &graph);
+                if (st != CBCT_OK) {
+                    if (graph) cudaGraphDestroy(graph);
+                    return st;
+                }
+                if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+                e = cudaGraphInstantiate(&gexec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (e != cudaSuccess) {
+                    gexec = nullptr;
+                    return cuda_fail(e, "graph instantiate");
+                }
+            } else {
+                cudaGetLastError();
+                use_graphs = false;
+            }
+        }
+        if (gexec) ECK(cudaGraphLaunch(gexec, stream), "graph launch");
+        else EST(launch_stages());
+    }
+    // advance, then one synchronisation for every job that needs host values
+    bool need_sync = false;
+    for (Job *j : jobs) {
+        if (j->phase == PH_POWER && ++j->pi_it == j->K) {
+            j->phase = PH_POWER_DONE;
+            need_sync = true;
+        } else if (j->phase == PH_FBS && ++j->it == j->iters) {
+            j->phase = PH_LEVEL_DONE;
+            need_sync = true;
+        } else if (j->phase == PH_LEVEL_DONE) {
+            need_sync = true;
+        }
+    }
+    if (need_sync) {
+        ECK(cudaStreamSynchronize(stream), "engine sync");
+        for (Job *j : jobs) {
+            if (j->phase == PH_POWER_DONE) {
+                double lam = 0.0;
+                ECK(cudaMemcpy(&lam, j->G->dscalars, sizeof(double), cudaMemcpyDeviceToHost), "lambda");
+                Level *L = j->Ls[j->level];
+                L->lambda = lam;
+                L->lambda_iters = j->K;
+                EST(begin_fbs(j, std::max(10.0 * j->mu, 1.05 * gamma_of(L, j->mu) * lam)));
+            }
+            if (j->phase == PH_LEVEL_DONE) EST(finish_level(j));
+        }
+    }
+    return CBCT_OK;
+}
+
+bool Engine::busy() const {
+    for (Job *j : jobs)
+        if (j->phase != PH_DONE) return true;
+    return false;
+}
+
+cbct_status Engine::run_all() {
+    while (busy()) EST(tick());
+    return CBCT_OK;
+}
+
+}  // namespace cbct
+
+using namespace cbct;
+
+extern "C" cbct_status cbct_reconstruct_batch(const cbct_request *reqs, int n, int use_graphs, cudaStream_t stream) {
+    if (!reqs || n < 1) {
+        set_error("need at least one request");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    std::vector<Job> jobs(n);
+    Engine E(stream, use_graphs != 0);
+    for (int q = 0; q < n; ++q) {
+        const cbct_request &r = reqs[q];
+        cbct_status st = validate_request(r.geom, r.Y_dev, r.mu, r.iters, r.levels, r.opts, r.f_out_dev);
+        if (st != CBCT_OK) {
+            set_error("request %d: %s", q, cbct_last_error());
+            return st;
+        }
+        Job &j = jobs[q];
+        j.G = r.geom;
+        j.Y = r.Y_dev;
+        j.mu = r.mu;
+        j.iters = r.iters;
+        j.levels = r.levels;
+        if (r.opts) j.o = *r.opts;
+        j.f_out = r.f_out_dev;
+        st = E.add(&j);
+        if (st != CBCT_OK) {
+            set_error("request %d: %s", q, cbct_last_error());
+            return st;
+        }
+    }
+    return E.run_all();
+}
+
+// ---------------------------------------------------------------------------------
+// autotuner: launch shapes per level (results are bitwise independent of them)
+// ---------------------------------------------------------------------------------
+
+static float time_ms(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+    float ms = 0.f;
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+}
+
+extern "C" cbct_status cbct_autotune(cbct_geometry *G, int level, cbct_tuning *out, cudaStream_t s) {
+    if (!G || !out) {
+        set_error("null argument");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    Level *L;
+    EST(ensure_level(G, level, &L));
+    EST(ensure_workspace(L, false));
+    GeoDev g = L->gd;
+    const size_t nv = vol_elems(g);
+    ECK(launch_fill(L->A, 1e-3f, nv, s), "fill");
+    cudaEvent_t e0, e1;
+    ECK(cudaEventCreate(&e0), "event");
+    ECK(cudaEventCreate(&e1), "event");
+    const int reps = 3;
+    // projector block size
+    const int need = std::min(PROJ_MAX_THREADS, 32 * ((g.nv + 31) / 32));
+    int best_t = 0;
+    float best_p = 1e30f;
+    for (int T : {need, 256, 320, 384, 448, 512}) {
+        if (T < need || T > PROJ_MAX_THREADS) continue;
+        g.proj_threads = T;
+        launch_project(g, L->A, nullptr, nullptr, L->rs, nullptr, PROJ_SCALED, s, nullptr);
+        cudaEventRecord(e0, s);
+        for (int q = 0; q < reps; ++q) launch_project(g, L->A, nullptr, nullptr, L->rs, nullptr, PROJ_SCALED, s, nullptr);
+        cudaEventRecord(e1, s);
+        const float ms = time_ms(s, e0, e1) / reps;
+        if (ms < best_p) {
+            best_p = ms;
+            best_t = T;
+        }
+    }
+    g.proj_threads = best_t;
+    // adjoint voxels per lane and block size
+    int best_v = 0, best_b = 0;
+    float best_q = 1e30f;
+    const int vmax = std::min(4, (g.nz + 31) / 32);
+    for (int v = 1; v <= vmax; ++v)
+        for (int T : {64, 128, 256}) {
+            g.bp_vpl = v;
+            g.bp_threads = T;
+            launch_backproject(g, L->rs, nullptr, L->B, 0.f, BP_PLAIN, s);
+            cudaEventRecord(e0, s);
+            for (int q = 0; q < reps; ++q) launch_backproject(g, L->rs, nullptr, L->B, 0.f, BP_PLAIN, s);
+            cudaEventRecord(e1, s);
+            const float ms = time_ms(s, e0, e1) / reps;
+            if (ms < best_q) {
+                best_q = ms;
+                best_v = v;
+                best_b = T;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ECK(cudaGetLastError(), "autotune");
+    L->gd.proj_threads = best_t;
+    L->gd.bp_vpl = best_v;
+    L->gd.bp_threads = best_b;
+    out->proj_threads = best_t;
+    out->bp_vpl = best_v;
+    out->bp_threads = best_b;
+    out->proj_ms = best_p;
+    out->bp_ms = best_q;
+    return CBCT_OK;
+}
+
+extern "C" cbct_status cbct_set_tuning(cbct_geometry *G, int level, const cbct_tuning *t) {
+    if (!G || !t) {
+        set_error("null argument");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    Level *L;
+    EST(ensure_level(G, level, &L));
+    const int need = std::min(PROJ_MAX_THREADS, 32 * ((L->gd.nv + 31) / 32));
+    if ((t->proj_threads && (t->proj_threads < need || t->proj_threads > PROJ_MAX_THREADS || t->proj_threads % 32)) ||
+        t->bp_vpl < 0 || t->bp_vpl > 4 ||
+        (t->bp_threads && t->bp_threads != 64 && t->bp_threads != 128 && t->bp_threads != 256)) {
+        set_error("tuning values out of range");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    L->gd.proj_threads = t->proj_threads;
+    L->gd.bp_vpl = t->bp_vpl;
+    L->gd.bp_threads = t->bp_threads;
+    return CBCT_OK;
+}

@@ -1,0 +1,97 @@
+// Batched execution engine (shared by cbct_reconstruct_batch and the server).
+#pragma once
+
+#include <vector>
+
+#include "cbct_internal.h"
+
+namespace cbct {
+
+struct ProjItem;
+struct BpItem;
+struct TvItem;
+struct VecItem;
+struct EnItem;
+
+enum JobPhase { PH_PREPARE = 0, PH_START_LEVEL, PH_POWER, PH_POWER_DONE, PH_FBS, PH_LEVEL_DONE, PH_DONE };
+
+// One reconstruction in flight: the arguments of cbct_reconstruct and its progress.
+struct Job {
+    cbct_geometry *G = nullptr;
+    const float *Y = nullptr;
+    double mu = 0.0;
+    int iters = 0, levels = 1;
+    cbct_options o{};
+    float *f_out = nullptr;
+    // progress
+    int level = 0, it = 0, pi_it = 0, M = 10, K = 30;
+    int phase = PH_PREPARE;
+    bool fp16 = false;
+    double beta = 0.0;
+    SolveParams P{};
+    std::vector<Level *> Ls;
+    bool done_event_pending = false;
+};
+
+struct CopyOp {
+    float *dst;
+    const float *src;
+    size_t bytes;
+};
+
+// Advances every job by one power-iteration step or one Algorithm A1 iteration per
+// tick, all stages of all jobs in one batched launch per stage.
+class Engine {
+  public:
+    Engine(cudaStream_t s, bool graphs);
+    ~Engine();
+    cbct_status add(Job *j);
+    cbct_status tick();
+    cbct_status run_all();
+    bool busy() const;
+    void remove_finished();
+    std::vector<Job *> jobs;
+    cudaStream_t stream;
+
+  private:
+    cbct_status prepare(Job *j);
+    cbct_status start_level(Job *j);
+    cbct_status begin_fbs(Job *j, double beta);
+    cbct_status finish_level(Job *j);
+    cbct_status build_tables();
+    cbct_status launch_stages();
+    void reset_graph();
+
+    bool use_graphs;
+    std::vector<long> signature;
+    int same_ticks = 0;
+    cudaGraphExec_t gexec = nullptr;
+    // host copies of the item tables and their device blob
+    std::vector<ProjItem> hproj;
+    std::vector<BpItem> hbp[4];
+    std::vector<VecItem> hdot;
+    std::vector<std::vector<TvItem>> htv;
+    std::vector<EnItem> hen;
+    std::vector<long> tvtot;
+    std::vector<CopyOp> copies;
+    std::vector<Job *> tv_energy_jobs;
+    long ptotal = 0, dtotal = 0, bptotal[4] = {0, 0, 0, 0};
+    int proj_threads = 32, max_m = 0;
+    void *dblob = nullptr;
+    size_t dblob_len = 0;
+    ProjItem *d_proj = nullptr;
+    long *d_pstart = nullptr;
+    BpItem *d_bp[4] = {nullptr, nullptr, nullptr, nullptr};
+    long *d_bstart[4] = {nullptr, nullptr, nullptr, nullptr};
+    VecItem *d_dot = nullptr;
+    long *d_dstart = nullptr;
+    std::vector<TvItem *> d_tv;
+    std::vector<long *> d_tstart;
+    EnItem *d_en = nullptr;
+};
+
+// Argument checks shared by cbct_reconstruct, the batch and the server.
+cbct_status validate_request(cbct_geometry *G, const float *Y, double mu, int iters, int levels,
+                             const cbct_options *o, float *f_out);
+
+}  // namespace cbct

@@ -1,0 +1,150 @@
+// Device-side warp tile of the adjoint gather (shared by the single-request and
+// batched kernels).
+#pragma once
+
+// Adjoint of the projector, evaluated voxel by voxel (the structure of Eq. 2 of Jia
+// et al. 2010: every voxel's variation of E2 is computed independently from the
+// residual images), with the exact intersection lengths of P instead of Eq. 2's
+// interpolated weights, so that the result is the matrix transpose P^T of the
+// paragraph before Eq. 2.  Fused epilogue: step 1 of Algorithm A1,
+// g = f - c P^T r with c = gamma / beta.
+//
+// Work decomposition.  One warp owns 32*VPL voxels of one z-column (i, j); lane l
+// holds voxels k = base + l + 32 v, v < VPL.  Per view, the detector columns whose ray
+// plane meets the xy-cell come from a precomputed table; for each, the part of the
+// rays' horizontal parameter t inside the cell, [tlo, thi], is the same for the whole
+// z-column.
+//
+// Plane sweep.  In detector-row units, a ray b sits at row b and the plane z at
+// rho_z(t) = z D / ((tS + t) dv) + cv, monotone in t.  Ray b is inside voxel k at t iff
+// rho_{z_k}(t) <= b < rho_{z_k+1}(t), so its length in the voxel is
+// J_{z_k+1}(b) - J_{z_k}(b) with J_z(b) = |{t in [tlo, thi] : b < rho_z(t)}|: thi - tlo for
+// rows below both ends of rho_z, 0 for rows above both, and the exact crossing
+// t* = (z - zO_b) cot_b otherwise (at most one row per plane here).  Hence
+//   sum_b r_b len = (thi - tlo) sum_{b in [N(z_k), N(z_k+1))} r_b + P(z_k+1) - P(z_k),
+// with N(z) the rows below both ends and P(z) the partial rows' sum.  Each lane
+// evaluates the plane below its voxel and takes the plane above from its neighbour.
+// The residual is pre-scaled by sec(phi) (3D length = t-length * sec(phi)).  Sums are
+// taken in a fixed order with no atomics, so results are deterministic.
+#include "cbct_internal.h"
+
+namespace cbct {
+
+constexpr int BP_THREADS = 128;
+
+// N(z) and P(z) of one plane for detector column rzp/rsp over [tlo, thi].
+__device__ __forceinline__ void eval_plane(float z, float q1, float q2, float cv, int nv, float tlo, float thi,
+                                           const float2 *__restrict__ rzp, const float *__restrict__ rsp,
+                                           int &nmin, float &part) {
+    const float r1 = __fmaf_rn(z, q1, cv), r2 = __fmaf_rn(z, q2, cv);
+    const float lo = fminf(r1, r2), hi = fmaxf(r1, r2);
+    nmin = min(max((int)ceilf(lo), 0), nv);
+    const int nmax = min(max((int)ceilf(hi), 0), nv);
+    const bool dec = r1 > r2;  // rho falls with t: the row is below the plane before t*
+    part = 0.f;
+    for (int b = nmin; b < nmax; ++b) {
+        const float2 rz = __ldg(rzp + b);
+        const float ts = fminf(fmaxf(t_cross(z, rz.x, rz.y), tlo), thi);
+        part = __fmaf_rn(__ldg(rsp + b), dec ? ts - tlo : thi - ts, part);
+    }
+}
+
+// Number of warp tiles of a level: z-chunks of 32*VPL voxels times xy-cells.
+template <int VPL>
+__host__ __device__ __forceinline__ long bp_warp_tiles(const GeoDev &G) {
+    return (long)G.nx * G.ny * ((G.nz + 32 * VPL - 1) / (32 * VPL));
+}
+
+// One warp tile (warp-uniform): z-chunk kc of xy-cell colid.  mode: BP_PLAIN writes
+// P^T rs, BP_STEP writes fin - c P^T rs.  Shared by the single-request and batched
+// kernels, so a request's result does not depend on what else is in the launch.
+template <int VPL>
+__device__ __forceinline__ void bp_warp(const GeoDev &G, const int mode, const float *__restrict__ rs,
+                                        const float *__restrict__ fin, float *__restrict__ out, const float c,
+                                        const long wtile) {
+    const int lane = threadIdx.x & 31;
+    const int nkc = (G.nz + 32 * VPL - 1) / (32 * VPL);
+    const long gwarp = wtile;
+    const int kc = (int)(gwarp % nkc);
+    const long colid = gwarp / nkc;
+    const int j = (int)(colid % G.ny);
+    const int i = (int)(colid / G.ny);
+    const int base = kc * 32 * VPL;
+
+    float zb[VPL], acc[VPL];
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+        zb[v] = plane_at(base + lane + 32 * v, G.hz, G.z0);  // plane below voxel base + lane + 32 v
+        acc[v] = 0.f;
+    }
+    const float ztop = plane_at(base + 32 * VPL, G.hz, G.z0);  // plane above the warp's last voxel
+    const float xl = plane_at(i, G.hx, G.x0), xh = plane_at(i + 1, G.hx, G.x0);
+    const float yl = plane_at(j, G.hy, G.y0), yh = plane_at(j + 1, G.hy, G.y0);
+
+#pragma unroll 1
+    for (int ia = 0; ia < G.na; ++ia) {
+        const short2 ar = G.arange[((size_t)ia * G.nx + i) * G.ny + j];
+        const float *rsv = rs + (size_t)ia * G.nu * G.nv;
+#pragma unroll 1
+        for (int a = ar.x; a <= ar.y; ++a) {
+            const float4 rxy = G.ray_xy[(size_t)ia * G.nu + a];
+            float tlo = -INFINITY, thi = INFINITY;
+            if (rxy.z != 0.f) {
+                const float t1 = t_cross(xl, rxy.x, rxy.z), t2 = t_cross(xh, rxy.x, rxy.z);
+                tlo = fminf(t1, t2);
+                thi = fmaxf(t1, t2);
+            } else if (!(rxy.x >= xl && rxy.x < xh)) {
+                continue;
+            }
+            if (rxy.w != 0.f) {
+                const float t1 = t_cross(yl, rxy.y, rxy.w), t2 = t_cross(yh, rxy.y, rxy.w);
+                tlo = fmaxf(tlo, fminf(t1, t2));
+                thi = fminf(thi, fmaxf(t1, t2));
+            } else if (!(rxy.y >= yl && rxy.y < yh)) {
+                continue;
+            }
+            if (!(thi > tlo)) continue;
+            const float2 Dt = G.col[a];
+            // rows per mm of z at tlo and thi (fast division: a ~1e-4 row error only moves
+            // a row between "full" and "partial" when its crossing lies within ~1e-4 of the
+            // cell's ends, where both give the same length to that precision)
+            const float q1 = __fdividef(Dt.x, Dt.y + tlo) * G.inv_dv;
+            const float q2 = __fdividef(Dt.x, Dt.y + thi) * G.inv_dv;
+            const float w = thi - tlo;
+            const float2 *rzp = G.ray_zc + (size_t)a * G.nv;
+            const float *rsp = rsv + (size_t)a * G.nv;
+            int nb[VPL];
+            float pb[VPL];
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) eval_plane(zb[v], q1, q2, G.cv, G.nv, tlo, thi, rzp, rsp, nb[v], pb[v]);
+            int nt;
+            float pt;
+            eval_plane(ztop, q1, q2, G.cv, G.nv, tlo, thi, rzp, rsp, nt, pt);
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) {
+                // the plane above voxel (lane, v) is the plane below the next voxel
+                int ntop = __shfl_down_sync(0xffffffffu, nb[v], 1);
+                float ptop = __shfl_down_sync(0xffffffffu, pb[v], 1);
+                const int nn = (v + 1 < VPL) ? __shfl_sync(0xffffffffu, nb[(v + 1) % VPL], 0) : nt;
+                const float pn = (v + 1 < VPL) ? __shfl_sync(0xffffffffu, pb[(v + 1) % VPL], 0) : pt;
+                if (lane == 31) {
+                    ntop = nn;
+                    ptop = pn;
+                }
+                float full = 0.f;
+                for (int b = nb[v]; b < ntop; ++b) full += __ldg(rsp + b);
+                acc[v] += __fmaf_rn(w, full, ptop - pb[v]);
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+        const int k = base + lane + 32 * v;
+        if (k >= G.nz) continue;
+        const size_t o = ((size_t)i * G.ny + j) * G.nz + k;
+        out[o] = (mode == BP_PLAIN) ? acc[v] : __fmaf_rn(-c, acc[v], __ldg(fin + o));
+    }
+}
+
+
+}  // namespace cbct

@@ -44,6 +44,10 @@ struct GeoDev {
     const float2 *col;           // [nu]      D = |d_xy|, t_S (source-to-O distance)
     const short2 *arange;        // [na][nx][ny] first/last detector column meeting each xy-cell
     const float2 *view;          // [na]      cos, sin
+    // launch shapes (0 = default); none of them changes any result bit
+    int proj_threads;            // projector block size (>= 32 ceil(nv/32) up to 512, multiple of 32)
+    int bp_vpl;                  // adjoint voxels per lane (1..4)
+    int bp_threads;              // adjoint block size (64, 128 or 256)
 };
 
 __host__ __device__ __forceinline__ size_t vol_elems(const GeoDev &g) { return (size_t)g.nx * g.ny * g.nz; }
@@ -92,7 +96,6 @@ struct cbct_geometry {
     int device = 0;
     std::vector<cbct::Level *> levels;   // index = level, created on demand
     double *dscalars = nullptr;          // small device scratch: trace, counters
-    float *io_vol = nullptr;             // API-layout staging (internal <-> API)
     int *dcounter = nullptr;
     double *dtrace = nullptr;            // device energy trace
     size_t dtrace_len = 0;
@@ -118,6 +121,8 @@ size_t project_partials(const GeoDev &g);
 enum BpMode { BP_PLAIN = 0, BP_STEP = 1 };
 cudaError_t launch_backproject(const GeoDev &g, const float *rs, const float *fin, float *out, float c,
                                int mode, cudaStream_t s);
+int project_threads(const GeoDev &g);
+int bp_default_vpl(const GeoDev &g);
 
 struct TvArgs {
     int nx, ny, nz;          // internal layout [nx][ny][nz]
@@ -153,5 +158,26 @@ cudaError_t launch_scale(const float *y, const float *scale, float *x, size_t n,
 cudaError_t launch_fill(float *x, float v, size_t n, cudaStream_t s);
 cudaError_t launch_tv_energy(const TvArgs &a, const float *f, double *partial, cudaStream_t s,
                              int *nblocks_out);
+
+
+// Solver constants of one level (Algorithm A1, discrete scaling of Eq. 1).
+struct SolveParams {
+    float c;        // gamma / beta
+    float s;        // inner step 1 / (beta + L_TV)
+    float beta;
+    float eps2;
+    int M;
+    int clamp_mode;
+    bool fp16;
+    double inv_nv, mu_over_nr;
+};
+double default_eps(const Level *L);
+double tv_lipschitz(const Level *L, double eps);
+double gamma_of(const Level *L, double mu);
+cbct_status ensure_trace(cbct_geometry *G, size_t n);
+TvArgs tv_args(const Level *L, const SolveParams &P);
+cbct_status solve_params(const Level *L, double mu, double beta, double eps, int M, int clamp_mode, bool fp16,
+                         SolveParams *P);
+cbct_status get_trace(cbct_geometry *G, size_t n, double **out);
 
 }  // namespace cbct
