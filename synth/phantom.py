@@ -28,6 +28,9 @@ import numpy as np
 
 __all__ = [
     "CONFIGS",
+    "BATCH_SIZES",
+    "make_request",
+    "make_request_set",
     "Ellipsoid",
     "geometry_for",
     "pixel_rays",
@@ -192,26 +195,43 @@ def voxelize(ells, geom: dict, ss: int = 4) -> np.ndarray:
 
 
 def analytic_sinogram(ells, geom: dict) -> np.ndarray:
-    """Exact line integrals sum_k density_k * chord_k for every pixel ray, [na][nv][nu]."""
+    """Exact line integrals sum_k density_k * chord_k for every pixel ray, [na][nv][nu].
+
+    Along the unit ray S + s d, ellipsoid (p - c)^T M (p - c) <= 1 gives the quadratic
+    A s^2 + 2 B s + C = 0 with A = d^T M d, B = d^T M q, C = q^T M q - 1, q = S - c, and
+    the chord is 2 sqrt(B^2 - A C) / A (the whole ellipsoid lies between source and
+    imager)."""
     out = np.zeros((len(geom["angles"]), geom["nv"], geom["nu"]))
+    quads = [(e, e.quadric()) for e in ells]
     for ia, th in enumerate(geom["angles"]):
         S, P = pixel_rays(geom, float(th))
-        d = P - S
-        d /= np.linalg.norm(d, axis=-1, keepdims=True)
-        for e in ells:
-            M = e.quadric()
+        d = (P - S).reshape(-1, 3)
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        dx, dy, dz = d[:, 0].copy(), d[:, 1].copy(), d[:, 2].copy()
+        xx, yy, zz, xy, xz, yz = dx * dx, dy * dy, dz * dz, dx * dy, dx * dz, dy * dz
+        acc = np.zeros(d.shape[0])
+        for e, M in quads:
             q = S - e.centre
-            A = np.einsum("...i,ij,...j->...", d, M, d)
-            B = np.einsum("...i,ij,j->...", d, M, q)
-            Cq = float(q @ M @ q) - 1.0
-            disc = B * B - A * Cq
-            out[ia] += e.density * np.where(disc > 0, 2.0 * np.sqrt(np.maximum(disc, 0.0)) / A, 0.0)
+            mq = M @ q
+            A = M[0, 0] * xx + M[1, 1] * yy + M[2, 2] * zz + 2.0 * (M[0, 1] * xy + M[0, 2] * xz + M[1, 2] * yz)
+            B = mq[0] * dx + mq[1] * dy + mq[2] * dz
+            disc = B * B - A * (float(q @ mq) - 1.0)
+            pos = disc > 0
+            acc[pos] += e.density * 2.0 * np.sqrt(disc[pos]) / A[pos]
+        out[ia] = acc.reshape(geom["nv"], geom["nu"])
     return out
 
 
 def poisson_log(Y: np.ndarray, I0: float, rng) -> np.ndarray:
-    """Poisson counts N ~ Poisson(I0 exp(-Y)); returns -ln(max(N, 0.5) / I0)."""
-    N = rng.poisson(I0 * np.exp(-Y)).astype(np.float64)
+    """Poisson counts N ~ Poisson(I0 exp(-Y)); returns -ln(max(N, 0.5) / I0).
+
+    The counts are drawn by torch's CPU Poisson sampler (fast for every mean) from a
+    generator seeded by the case's PCG64 stream, so the data stay seeded."""
+    import torch
+
+    gen = torch.Generator().manual_seed(int(rng.integers(0, 2 ** 62)))
+    lam = torch.from_numpy(np.ascontiguousarray(I0 * np.exp(-Y), dtype=np.float64))
+    N = torch.poisson(lam, generator=gen).numpy()
     return -np.log(np.maximum(N, 0.5) / I0)
 
 
@@ -229,3 +249,34 @@ def make_case(name: str, *, with_truth: bool = False, truth_ss: int = 2, theta0:
     if with_truth:
         case["f_true"] = voxelize(ells, geom, truth_ss)
     return case
+
+
+# Heterogeneous requests of a batch (volume 128^3 to 384x384x64, 20-60 views with a
+# random start offset, 128x96 to 384x288 imagers, Poisson I0 log-uniform in
+# 1e4..1e5).  The transverse extent is 256 mm and the axial one 160 mm; the imager
+# pitch makes the imager cover the volume's field of view x 1.1 at dsd/dso = 1.5.
+BATCH_SIZES = [((128, 128, 128), (128, 96)), ((192, 192, 96), (192, 144)), ((256, 256, 64), (256, 192)),
+               ((256, 256, 96), (256, 192)), ((320, 320, 64), (320, 240)), ((384, 384, 64), (384, 288))]
+
+
+def make_request(rng, size_index=None, levels=2, iters=30):
+    """One seeded request of the heterogeneous batch workload."""
+    if size_index is None:
+        size_index = int(rng.integers(0, len(BATCH_SIZES)))
+    (nx, ny, nz), (nu, nv) = BATCH_SIZES[size_index]
+    hx = 256.0 / nx
+    hz = 160.0 / nz
+    na = int(rng.integers(20, 61))
+    du = 1.1 * 256.0 * 1.5 / nu
+    dv = 1.1 * 160.0 * 1.5 / nv
+    cfg = dict(vol=(nx, ny, nz), h=(hx, hx, hz), det=(nu, nv), pitch=(du, dv), n_angles=na, dso=1000.0, dsd=1500.0)
+    geom = geometry_for(cfg, theta0=float(rng.uniform(0.0, 2.0 * math.pi / na)))
+    ells = make_ellipsoids(geom, rng, 10, 0)
+    I0 = float(10 ** rng.uniform(4.0, 5.0))
+    Y = poisson_log(analytic_sinogram(ells, geom), I0, rng)
+    return dict(geom=geom, Y=Y, mu=5.0, levels=levels, iters=iters, I0=I0, size_index=size_index)
+
+
+def make_request_set(seed, n, levels=2, iters=30):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [make_request(rng, q % len(BATCH_SIZES), levels, iters) for q in range(n)]
