@@ -13,6 +13,16 @@ reconstructions (no data-path collective; weak scaling).
 
 Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead, on
 the host cores, one Algorithm A1 iteration of the finest level per step.
+
+Two serving modes print their own line (reconstructions/s):
+
+* ``--mode batch``: 16 heterogeneous requests (six volume sizes from 128^3 to
+  384x384x64, 20-60 views, random start angles, 2 levels x 30 iterations), run one at
+  a time through ``cbct_reconstruct`` and together through ``cbct_reconstruct_batch``.
+* ``--mode serve``: the same requests arrive as a Poisson stream at a fixed fraction of
+  the one-at-a-time capacity and go through the continuous-batching server; latency
+  percentiles are compared with a one-at-a-time FIFO queue fed the same arrival times
+  and the measured per-request service times.
 """
 from __future__ import annotations
 
@@ -22,6 +32,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -42,7 +53,7 @@ CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.ac
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 # Lane-operations per nonzero that no implementation of the exact-length operators can
-# avoid ("Roofline"): adjoint 8 (two z-crossings: 2 sub + 2 mul, clip:
+# avoid: adjoint 8 (two z-crossings: 2 sub + 2 mul, clip:
 # 1 max + 1 min, length: 1 sub, accumulate: 1 fma); projector 4 (pick next crossing:
 # 1 min, length: 1 sub, accumulate: 1 fma, advance the crossing: 1 fma).
 OPS_PER_NNZ = {"backproject": 8.0, "project": 4.0}
@@ -66,7 +77,8 @@ class ClockSampler:
 
     def __init__(self, gpu_index):
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(os.environ.get("CBCT_CLOCK_LOG_DIR", tempfile.gettempdir()),
+                                 f"clocks_{os.getpid()}.csv")
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
@@ -305,6 +317,159 @@ def run_gpu(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def _upload_requests(reqs, dev):
+    import torch
+    out = []
+    for r in reqs:
+        g = r["geom"]
+        out.append(dict(r, Y_dev=torch.tensor(np.asarray(r["Y"], dtype=np.float32), device=dev),
+                        f_dev=torch.zeros((g["nz"], g["ny"], g["nx"]), dtype=torch.float32, device=dev)))
+    return out
+
+
+def _request_text(reqs):
+    sizes = sorted({(r["geom"]["nx"], r["geom"]["ny"], r["geom"]["nz"]) for r in reqs})
+    views = [len(r["geom"]["angles"]) for r in reqs]
+    return (f"{len(reqs)} requests, volumes {', '.join('x'.join(map(str, s)) for s in sizes)}, "
+            f"{min(views)}-{max(views)} views, {reqs[0]['levels']} levels x {reqs[0]['iters']} FBS iterations, "
+            f"Poisson I0 1e4-1e5")
+
+
+def _sequential(cbct, reqs, stream):
+    """Per-request service times (s) of one-at-a-time cbct_reconstruct calls."""
+    import torch
+    times = []
+    for r in reqs:
+        G = r["G"]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cbct.cbct_reconstruct(G, r["Y_dev"], r["mu"], r["iters"], r["levels"], f_out=r["f_dev"])
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    return times
+
+
+def run_batch(args, world, rank, local):
+    import torch
+
+    from paper_1002_3675_b300 import cbct
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    reqs = _upload_requests(synth.make_request_set(1003 + rank, args.requests), dev)
+    for r in reqs:
+        r["G"] = cbct.cbct_geometry_create(r["geom"])
+    stream = torch.cuda.current_stream()
+    batch = [dict(geom=r["G"], Y=r["Y_dev"], mu=r["mu"], iters=r["iters"], levels=r["levels"], f_out=r["f_dev"])
+             for r in reqs]
+    for _ in range(max(1, args.warmup // 3)):
+        _sequential(cbct, reqs, stream)
+        cbct.cbct_reconstruct_batch(batch, use_graphs=True)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local) if rank == 0 else None
+    barrier(world)
+    seq_s, bat_s = [], []
+    for _ in range(args.steps):
+        seq_s.append(sum(_sequential(cbct, reqs, stream)))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cbct.cbct_reconstruct_batch(batch, use_graphs=True)
+        e1.record(stream)
+        e1.synchronize()
+        bat_s.append(e0.elapsed_time(e1) / 1e3)
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    seq_t = max_over_ranks(sum(seq_s), world)
+    bat_t = max_over_ranks(sum(bat_s), world)
+    n = world * args.steps * len(reqs)
+    if rank == 0:
+        line = {"mode": "batch", "metric": "reconstructions/s", "value": n / bat_t, "unit": "recon/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * bat_t / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded ellipsoid phantoms, analytic line integrals, Poisson/log noise)",
+                "config": {"workload": _request_text(reqs), "step": "all requests once", "graphs": True,
+                           "parallelism": f"replicas x{world}"},
+                "one_at_a_time": {"value": n / seq_t, "unit": "recon/s", "ms_per_step": 1e3 * seq_t / args.steps},
+                "batch_speedup": seq_t / bat_t, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+
+
+def _fifo_latencies(arrivals, service):
+    """Latencies of a one-at-a-time FIFO queue with the given arrival and service times."""
+    free, out = 0.0, []
+    for a, s in zip(arrivals, service):
+        start = max(a, free)
+        free = start + s
+        out.append(free - a)
+    return out
+
+
+def run_serve(args, world, rank, local):
+    import torch
+
+    from paper_1002_3675_b300 import cbct
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    base = _upload_requests(synth.make_request_set(1003 + rank, args.requests), dev)
+    for r in base:
+        r["G"] = cbct.cbct_geometry_create(r["geom"])
+    stream = torch.cuda.current_stream()
+    _sequential(cbct, base, stream)
+    service = dict(enumerate(_sequential(cbct, base, stream)))
+    mean_s = statistics.mean(service.values())
+    rate = args.load / mean_s                     # arrivals/s at the chosen fraction of one-at-a-time capacity
+    n = args.requests * args.steps
+    rng = np.random.default_rng(2000 + rank)
+    gaps = rng.exponential(1.0 / rate, size=n)
+    order = [q % len(base) for q in range(n)]
+    srv = cbct.Server(args.budget_gb << 30, args.slots, use_graphs=True)
+    # warm-up: every geometry once, so resident tables and graphs exist
+    for r in base:
+        srv.wait(srv.submit(r["geom"], r["Y_dev"], r["mu"], r["iters"], r["levels"], r["f_dev"]), 600000)
+    outs = [torch.empty_like(base[q]["f_dev"]) for q in order]
+    sampler = ClockSampler(local) if rank == 0 else None
+    barrier(world)
+    t0 = time.perf_counter()
+    tickets, arrivals = [], []
+    next_t = t0
+    for q, gap, f in zip(order, gaps, outs):
+        next_t += gap
+        while True:
+            d = next_t - time.perf_counter()
+            if d <= 0:
+                break
+            time.sleep(min(d, 0.002))
+        r = base[q]
+        arrivals.append(time.perf_counter() - t0)
+        tickets.append(srv.submit(r["geom"], r["Y_dev"], r["mu"], r["iters"], r["levels"], f))
+    res = [srv.wait(t, 600000) for t in tickets]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    stats = srv.stats()
+    srv.close()
+    lat = [r["latency_s"] for r in res]
+    fifo = _fifo_latencies(arrivals, [service[q] for q in order])
+    wall = max_over_ranks(wall, world)
+    if rank == 0:
+        pct = lambda xs, p: float(np.percentile(np.asarray(xs), p))  # noqa: E731
+        line = {"mode": "serve", "metric": "reconstructions/s", "value": world * n / wall, "unit": "recon/s",
+                "n_gpus": world, "steps": args.steps, "warmup": 1, "ms_per_step": 1e3 * wall / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded ellipsoid phantoms, analytic line integrals, Poisson/log noise)",
+                "config": {"workload": _request_text(base), "arrivals": f"Poisson, {rate:.2f}/s "
+                           f"({args.load:.2f} x one-at-a-time capacity)", "slots": args.slots,
+                           "hbm_budget_gb": args.budget_gb, "graphs": True, "parallelism": f"replicas x{world}"},
+                "latency_s": {"p50": pct(lat, 50), "p90": pct(lat, 90), "p99": pct(lat, 99), "max": max(lat)},
+                "fifo_one_at_a_time_latency_s": {"p50": pct(fifo, 50), "p90": pct(fifo, 90), "p99": pct(fifo, 99),
+                                                 "max": max(fifo)},
+                "mean_service_s": mean_s, "server_busy_s": stats["busy_s"], "clocks": clocks}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -313,10 +478,19 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="medium", choices=sorted(WORKLOAD_TEXT))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve"])
+    ap.add_argument("--requests", type=int, default=16)
+    ap.add_argument("--load", type=float, default=1.5, help="serve: arrival rate / one-at-a-time capacity")
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--budget-gb", type=int, default=64)
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.mode == "batch":
+        run_batch(args, world, rank, local)
+    elif args.mode == "serve":
+        run_serve(args, world, rank, local)
     else:
         run_gpu(args, world, rank, local)
     if world > 1:
