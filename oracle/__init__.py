@@ -35,12 +35,12 @@ class _Geom(C.Structure):
                 ("hx", C.c_double), ("hy", C.c_double), ("hz", C.c_double),
                 ("nu", C.c_int), ("nv", C.c_int), ("du", C.c_double), ("dv", C.c_double),
                 ("dso", C.c_double), ("dsd", C.c_double),
-                ("na", C.c_int), ("angles", C.POINTER(C.c_double))]
+                ("na", C.c_int), ("angles", C.POINTER(C.c_double)), ("tv_mode", C.c_int)]
 
 
 class _Vol(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
-                ("hx", C.c_double), ("hy", C.c_double), ("hz", C.c_double)]
+                ("hx", C.c_double), ("hy", C.c_double), ("hz", C.c_double), ("tv_mode", C.c_int)]
 
 
 _lib = None
@@ -97,20 +97,20 @@ def _f64(a):
 class _GeomHolder:
     """Keeps the angle array alive while the C struct points into it."""
 
-    def __init__(self, geom: dict):
+    def __init__(self, geom: dict, tv_mode: int = 0):
         self.angles = _f64(geom["angles"])
         self.s = _Geom(geom["nx"], geom["ny"], geom["nz"], geom["hx"], geom["hy"], geom["hz"],
                        geom["nu"], geom["nv"], geom["du"], geom["dv"], geom["dso"], geom["dsd"],
-                       len(self.angles), _ptr(self.angles))
+                       len(self.angles), _ptr(self.angles), int(tv_mode))
 
 
-def _g(geom):
-    return _GeomHolder(geom)
+def _g(geom, tv_mode=0):
+    return _GeomHolder(geom, tv_mode)
 
 
-def _vol(shape, h):
+def _vol(shape, h, tv_mode=0):
     nz, ny, nx = shape
-    return _Vol(nx, ny, nz, float(h[0]), float(h[1]), float(h[2]))
+    return _Vol(nx, ny, nz, float(h[0]), float(h[1]), float(h[2]), int(tv_mode))
 
 
 def vol_shape(geom):
@@ -179,17 +179,19 @@ def count_nnz(geom) -> int:
 
 
 # --- TV (E1) and the step-2 prox ------------------------------------------------------
+# tv_mode 0: isotropic sum_j sqrt(|grad f|^2 + eps^2); 1: anisotropic
+# sum_j sum_d sqrt((D_d f)^2 + eps^2).
 
-def tv(f, h, eps):
+def tv(f, h, eps, tv_mode=0):
     f = _f64(f)
-    v = _vol(f.shape, h)
+    v = _vol(f.shape, h, tv_mode)
     return _load().or_tv(C.byref(v), _ptr(f), eps)
 
 
-def tv_grad(f, h, eps):
+def tv_grad(f, h, eps, tv_mode=0):
     f = _f64(f)
     out = np.empty_like(f)
-    v = _vol(f.shape, h)
+    v = _vol(f.shape, h, tv_mode)
     _load().or_tv_grad(C.byref(v), _ptr(f), eps, _ptr(out))
     return out
 
@@ -199,11 +201,11 @@ def tv_lipschitz(h, eps):
     return _load().or_tv_lipschitz(C.byref(v), eps)
 
 
-def prox(g, f0, h, beta, eps, M, clamp_mode=0, tv_weight=1.0, return_phi=False):
+def prox(g, f0, h, beta, eps, M, clamp_mode=0, tv_weight=1.0, return_phi=False, tv_mode=0):
     g = _f64(g)
     f = _f64(f0).copy() if f0 is not None else np.zeros_like(g)
     phi = np.empty(M + 1) if return_phi else None
-    v = _vol(g.shape, h)
+    v = _vol(g.shape, h, tv_mode)
     _load().or_prox(C.byref(v), _ptr(g), _ptr(f), beta, eps, M, clamp_mode, tv_weight, _ptr(phi))
     return (f, phi) if return_phi else f
 
@@ -220,11 +222,11 @@ def default_eps(geom):
     return _load().or_default_eps(C.byref(h.s))
 
 
-def energy(geom, Y, f, mu, eps, return_residual=False):
+def energy(geom, Y, f, mu, eps, return_residual=False, tv_mode=0):
     Y, f = _f64(Y), _f64(f)
     out = np.empty(3)
     r = np.empty(sino_shape(geom)) if return_residual else None
-    h = _g(geom)
+    h = _g(geom, tv_mode)
     _load().or_energy(C.byref(h.s), _ptr(Y), _ptr(f), mu, eps, _ptr(out), _ptr(r))
     return (out, r) if return_residual else out
 
@@ -239,11 +241,11 @@ def auto_beta(geom, mu, K=30):
     return _load().or_auto_beta(C.byref(h.s), mu, K)
 
 
-def fbs(geom, Y, mu, beta, eps, M, iters, f0=None, clamp_mode=0, tv_weight=1.0):
+def fbs(geom, Y, mu, beta, eps, M, iters, f0=None, clamp_mode=0, tv_weight=1.0, tv_mode=0):
     Y = _f64(Y)
     f = _f64(f0).copy() if f0 is not None else np.zeros(vol_shape(geom))
     trace = np.empty((iters, 3))
-    h = _g(geom)
+    h = _g(geom, tv_mode)
     _load().or_fbs(C.byref(h.s), _ptr(Y), mu, beta, eps, M, clamp_mode, tv_weight, iters, _ptr(f), _ptr(trace))
     return f, trace
 
@@ -275,12 +277,12 @@ def level_geom(geom, level):
     return g2
 
 
-def reconstruct(geom, Y, mu, iters, levels, betas=None, eps=0.0, M=10, clamp_mode=0, K_pi=30):
+def reconstruct(geom, Y, mu, iters, levels, betas=None, eps=0.0, M=10, clamp_mode=0, K_pi=30, tv_mode=0):
     Y = _f64(Y)
     f = np.empty(vol_shape(geom))
     trace = np.empty((levels, iters, 3))
     b = _f64(betas) if betas is not None else None
-    h = _g(geom)
+    h = _g(geom, tv_mode)
     _load().or_reconstruct(C.byref(h.s), _ptr(Y), mu, iters, levels, _ptr(b), eps, M, clamp_mode,
                            K_pi, _ptr(f), _ptr(trace))
     return f, trace

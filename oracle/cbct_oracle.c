@@ -19,7 +19,8 @@
  *   - the adjoint used in step 1 of Algorithm A1 is the exact matrix transpose named
  *     in the paragraph before Eq. 2; here it is a scatter over the same crossings.
  *   - E1 (Eq. 1) is the isotropic TV with forward differences, Neumann boundary,
- *     smoothed as sqrt(|grad f|^2 + eps^2).
+ *     smoothed as sqrt(|grad f|^2 + eps^2) (tv_mode 0).  tv_mode 1 is the anisotropic
+ *     reading of the l1 norm of the gradient, sum_d sqrt((D_d f)^2 + eps^2).
  *   - step 2 of Algorithm A1 ("simple gradient descent") is projected gradient on
  *     TV_eps(f) + beta/2 |f - g|^2 over f >= 0 from f0 = f_k, step 1/(beta + L_TV),
  *     L_TV = (4/eps) sum_d h_d^-2; clamp_mode 1 instead descends from g without the
@@ -44,6 +45,7 @@ typedef struct {
     double dso, dsd;
     int na;
     const double *angles;
+    int tv_mode; /* 0: isotropic E1, 1: anisotropic E1 */
 } or_geom;
 
 /* ------------------------------------------------------------------------------ */
@@ -331,6 +333,7 @@ double or_ray_voxel_length(const or_geom *g, int ia, int b, int a, int i, int j,
 typedef struct {
     int nx, ny, nz;
     double hx, hy, hz;
+    int tv_mode; /* 0: isotropic, 1: anisotropic */
 } or_vol;
 
 #define VIDX(v, i, j, k) ((((long)(k)) * (v)->ny + (j)) * (long)(v)->nx + (i))
@@ -344,7 +347,19 @@ static void grad_at(const or_vol *v, const double *f, int i, int j, int k, doubl
     out[2] = k < v->nz - 1 ? (f[VIDX(v, i, j, k + 1)] - c) / v->hz : 0.0;
 }
 
-/* TV_eps(f) = sum_j sqrt(|grad f|_j^2 + eps^2), summed slice by slice in a fixed order. */
+/* Smoothed magnitude of one voxel's gradient: the term of TV_eps at that voxel. */
+static double tv_term(const or_vol *v, const double gr[3], double eps)
+{
+    if (v->tv_mode == 1)
+        return sqrt(gr[0] * gr[0] + eps * eps) + sqrt(gr[1] * gr[1] + eps * eps) + sqrt(gr[2] * gr[2] + eps * eps);
+    return sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2] + eps * eps);
+}
+
+/*
+ * TV_eps(f) = sum_j sqrt(|grad f|_j^2 + eps^2) (isotropic) or
+ * sum_j sum_d sqrt((D_d f)_j^2 + eps^2) (anisotropic), summed slice by slice in a
+ * fixed order.
+ */
 double or_tv(const or_vol *v, const double *f, double eps)
 {
     double *slice = (double *)calloc(v->nz, sizeof(double));
@@ -355,7 +370,7 @@ double or_tv(const or_vol *v, const double *f, double eps)
             for (int i = 0; i < v->nx; ++i) {
                 double gr[3];
                 grad_at(v, f, i, j, k, gr);
-                s += sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2] + eps * eps);
+                s += tv_term(v, gr, eps);
             }
         slice[k] = s;
     }
@@ -366,7 +381,8 @@ double or_tv(const or_vol *v, const double *f, double eps)
 }
 
 /*
- * Gradient of TV_eps: sum_d D_d^T (D_d f / |grad f|_eps), with
+ * Gradient of TV_eps: sum_d D_d^T p_d with p_d = D_d f / |grad f|_eps (isotropic) or
+ * p_d = D_d f / sqrt((D_d f)^2 + eps^2) (anisotropic), and
  * (D_d^T p)_i = (p_{i-1} [i > 0] - p_i [i < n-1]) / h_d.
  */
 void or_tv_grad(const or_vol *v, const double *f, double eps, double *out)
@@ -379,11 +395,12 @@ void or_tv_grad(const or_vol *v, const double *f, double eps, double *out)
             for (int i = 0; i < v->nx; ++i) {
                 double gr[3];
                 grad_at(v, f, i, j, k, gr);
-                double nrm = sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2] + eps * eps);
                 long q = VIDX(v, i, j, k);
-                p[3 * q + 0] = gr[0] / nrm;
-                p[3 * q + 1] = gr[1] / nrm;
-                p[3 * q + 2] = gr[2] / nrm;
+                for (int d = 0; d < 3; ++d) {
+                    double nrm = v->tv_mode == 1 ? sqrt(gr[d] * gr[d] + eps * eps)
+                                                 : sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2] + eps * eps);
+                    p[3 * q + d] = gr[d] / nrm;
+                }
             }
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < v->nz; ++k)
@@ -399,7 +416,10 @@ void or_tv_grad(const or_vol *v, const double *f, double eps, double *out)
     free(p);
 }
 
-/* Lipschitz bound of grad TV_eps: (4/eps) sum_d h_d^-2. */
+/*
+ * Lipschitz bound of grad TV_eps: (4/eps) sum_d h_d^-2 in both modes (each smoothed
+ * magnitude has curvature at most 1/eps, and |D_d|^2 <= 4/h_d^2).
+ */
 double or_tv_lipschitz(const or_vol *v, double eps)
 {
     return 4.0 / eps * (1.0 / (v->hx * v->hx) + 1.0 / (v->hy * v->hy) + 1.0 / (v->hz * v->hz));
@@ -447,7 +467,7 @@ void or_prox(const or_vol *v, const double *g, double *f, double beta, double ep
 
 static or_vol vol_of(const or_geom *g)
 {
-    or_vol v = {g->nx, g->ny, g->nz, g->hx, g->hy, g->hz};
+    or_vol v = {g->nx, g->ny, g->nz, g->hx, g->hy, g->hz, g->tv_mode};
     return v;
 }
 

@@ -248,6 +248,51 @@ def test_tv_matches_autograd_definition():
     assert np.abs(t.grad.numpy() - oracle.tv_grad(f, H, eps)).max() <= 1e-10
 
 
+def test_anisotropic_tv_gradient_and_closed_forms():
+    """tv_mode 1 (sum_d sqrt((D_d f)^2 + eps^2)): central finite differences of the
+    value, the constant volume (3 Nv eps, zero gradient) and a ramp in x and y whose
+    isotropic and anisotropic totals have different closed forms."""
+    rng = np.random.default_rng(17)
+    f = rng.uniform(size=(5, 6, 7))
+    eps = 0.05
+    gr = oracle.tv_grad(f, H, eps, tv_mode=1)
+    step = 1e-6
+    for _ in range(20):
+        k, j, i = rng.integers(0, 5), rng.integers(0, 6), rng.integers(0, 7)
+        fp, fm = f.copy(), f.copy()
+        fp[k, j, i] += step
+        fm[k, j, i] -= step
+        fd = (oracle.tv(fp, H, eps, tv_mode=1) - oracle.tv(fm, H, eps, tv_mode=1)) / (2 * step)
+        assert abs(fd - gr[k, j, i]) <= 1e-7 * max(1.0, abs(fd))
+    c = np.full((4, 5, 6), 3.0)
+    assert abs(oracle.tv(c, H, 0.01, tv_mode=1) - 3 * c.size * 0.01) <= 1e-12 * c.size
+    assert np.abs(oracle.tv_grad(c, H, 0.01, tv_mode=1)).max() == 0.0
+    nz, ny, nx = 4, 5, 6
+    a, b = 0.3, -0.8
+    ramp = a * np.arange(nx)[None, None, :] + b * np.arange(ny)[None, :, None] + np.zeros((nz, ny, nx))
+    A, B = abs(a) / H[0], abs(b) / H[1]
+    aniso = nz * ny * (nx - 1) * A + nz * nx * (ny - 1) * B
+    iso = nz * ((nx - 1) * (ny - 1) * np.hypot(A, B) + (nx - 1) * A + (ny - 1) * B)
+    assert abs(oracle.tv(ramp, H, 0.0, tv_mode=1) - aniso) <= 1e-12 * aniso
+    assert abs(oracle.tv(ramp, H, 0.0) - iso) <= 1e-12 * iso
+    assert aniso > iso
+
+
+def test_anisotropic_tv_matches_autograd_definition():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(18)
+    f = rng.uniform(size=(6, 5, 7))
+    eps = 0.02
+    t = torch.tensor(f, requires_grad=True, dtype=torch.float64)
+    dz = torch.nn.functional.pad(torch.diff(t, dim=0), (0, 0, 0, 0, 0, 1)) / H[2]
+    dy = torch.nn.functional.pad(torch.diff(t, dim=1), (0, 0, 0, 1)) / H[1]
+    dx = torch.nn.functional.pad(torch.diff(t, dim=2), (0, 1)) / H[0]
+    val = sum(torch.sqrt(d * d + eps * eps).sum() for d in (dx, dy, dz))
+    val.backward()
+    assert abs(val.item() - oracle.tv(f, H, eps, tv_mode=1)) <= 1e-12 * val.item()
+    assert np.abs(t.grad.numpy() - oracle.tv_grad(f, H, eps, tv_mode=1)).max() <= 1e-10
+
+
 def test_prox_limits_and_monotonicity():
     rng = np.random.default_rng(9)
     g = rng.normal(size=(6, 7, 8))
@@ -263,23 +308,47 @@ def test_prox_limits_and_monotonicity():
     # paper-literal clamp (descend from g, clamp once): still non-negative
     f1 = oracle.prox(g, None, H, 3.0, eps, 25, clamp_mode=1)
     assert (f1 >= 0).all() and np.any(f1 == 0)
+    # the anisotropic E1 keeps both properties (same Lipschitz bound)
+    f2, phi2 = oracle.prox(g, f0, H, 3.0, eps, 25, return_phi=True, tv_mode=1)
+    assert np.all(np.diff(phi2) <= 1e-12 * np.abs(phi2[:-1])) and (f2 >= 0).all()
+    assert np.abs(oracle.prox(g, f0, H, 1e9, eps, 60, tv_mode=1) - np.maximum(g, 0)).max() < 1e-6
 
 
 # ---------------------------------------------------------------------------------
 # Algorithm A1 (FBS) and the energy of Eq. 1
 # ---------------------------------------------------------------------------------
 
-def test_fbs_energy_monotone_small_workload():
+@pytest.mark.parametrize("tv_mode", [0, 1])
+def test_fbs_energy_monotone_small_workload(tv_mode):
     case = synth.make_case("small")
     g = case["geom"]
     beta = oracle.auto_beta(g, case["mu"])
     eps = oracle.default_eps(g)
-    f, tr = oracle.fbs(g, case["Y"], case["mu"], beta, eps, 10, 20)
-    E = list(tr[:, 0]) + [oracle.energy(g, case["Y"], f, case["mu"], eps)[0]]
+    f, tr = oracle.fbs(g, case["Y"], case["mu"], beta, eps, 10, 20, tv_mode=tv_mode)
+    E = list(tr[:, 0]) + [oracle.energy(g, case["Y"], f, case["mu"], eps, tv_mode=tv_mode)[0]]
     for a, b in zip(E[:-1], E[1:]):
         assert b <= a * (1 + 1e-12)
     assert E[-1] < 0.2 * E[0]
     assert (f >= 0).all()
+
+
+def test_beta_ten_mu_regime_on_a_scaled_geometry():
+    """Scaling every length by s scales P by s and lambda_max(P^T P) by s^2; at
+    s = 1e-3 the bound 1.05 gamma lambda falls below 10 mu, so the automatic beta is
+    the paper's 10 mu, and Algorithm A1 still decreases the energy there."""
+    case = synth.make_case("small")
+    g = case["geom"]
+    s = 1e-3
+    gs = dict(g, **{k: g[k] * s for k in ("hx", "hy", "hz", "du", "dv", "dso", "dsd")})
+    lam, lam_s = oracle.power_iteration(g, 30), oracle.power_iteration(gs, 30)
+    assert abs(lam_s - s * s * lam) <= 1e-9 * s * s * lam
+    mu = case["mu"]
+    assert oracle.auto_beta(gs, mu) == 10.0 * mu
+    Ys = case["Y"] * s          # line integrals of the same densities over shorter chords
+    eps = oracle.default_eps(gs)
+    f, tr = oracle.fbs(gs, Ys, mu, 10.0 * mu, eps, 10, 10)
+    E = list(tr[:, 0]) + [oracle.energy(gs, Ys, f, mu, eps)[0]]
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(E[:-1], E[1:]))
 
 
 def test_fbs_fixed_point():
