@@ -100,6 +100,9 @@ typedef struct {
     int reuse_lambda;     /* 1: reuse lambda_max(P^T P) of a level computed by an
                              earlier call on this geometry with the same power_iters
                              (the estimate is deterministic, so results are unchanged) */
+    int tv_mode;          /* E1 of Eq. 1: 0 isotropic sum_j sqrt(|grad f|_j^2 + eps^2)
+                             [default]; 1 anisotropic sum_j sum_d sqrt((D_d f)_j^2 + eps^2)
+                             (the l1 norm of the gradient taken per axis)        */
 } cbct_options;
 
 /* Kernel classes reported through cbct_options.kernel_ms. */
@@ -140,20 +143,21 @@ cbct_status cbct_backproject(cbct_geometry *geom, const float *y_dev, float *f_d
 /* Steps 2 and 3 of Algorithm A1 on the geometry's grid: inner_iters projected
  * gradient steps on TV_eps(f) + beta/2 |f - g|^2 over f >= 0, starting from the
  * volume in f_inout_dev, step 1/(beta + (4/eps) sum_d h_d^-2).  TV_eps is the
- * isotropic forward-difference TV with Neumann boundary, sqrt(|grad f|^2 + eps^2)
- * per voxel (E1 of Eq. 1).  Every output voxel is >= +0.0.  g_dev: volume. */
+ * forward-difference TV with Neumann boundary (E1 of Eq. 1): tv_mode 0 isotropic,
+ * sqrt(|grad f|^2 + eps^2) per voxel; tv_mode 1 anisotropic, sum over the axes of
+ * sqrt((D_d f)^2 + eps^2).  Every output voxel is >= +0.0.  g_dev: volume. */
 cbct_status cbct_tv_prox(cbct_geometry *geom, const float *g_dev, float *f_inout_dev, double beta,
-                         double eps, int inner_iters, cudaStream_t stream);
+                         double eps, int inner_iters, int tv_mode, cudaStream_t stream);
 
 /* Algorithm A1 on a single grid (the geometry's own), `iters` iterations from the
  * volume in f_inout_dev:
  *   g = f - (gamma/beta) P^T (P f - Y),  gamma = 2 mu Nv / (n_angles nu nv)
- *   f = step 2 and 3 as in cbct_tv_prox (clamp_mode as in cbct_options)
+ *   f = step 2 and 3 as in cbct_tv_prox (clamp_mode, tv_mode as in cbct_options)
  * beta must be > 0 (no automatic choice here).  Y_dev: measured sinogram.
  * energy_trace: optional host [iters][3] (E, E1, mu*E2 of each entering iterate;
  * synchronises the stream once at the end). */
 cbct_status cbct_fbs(cbct_geometry *geom, const float *Y_dev, double mu, double beta, double eps,
-                     int inner_iters, int clamp_mode, int iters, float *f_inout_dev,
+                     int inner_iters, int clamp_mode, int tv_mode, int iters, float *f_inout_dev,
                      double *energy_trace, cudaStream_t stream);
 
 /* Largest eigenvalue of P^T P by `iters` power iterations from the all-ones volume;
@@ -162,9 +166,10 @@ cbct_status cbct_fbs(cbct_geometry *geom, const float *Y_dev, double mu, double 
 cbct_status cbct_power_iteration(cbct_geometry *geom, int iters, double *lambda_out, cudaStream_t stream);
 
 /* Energy of Eq. 1 on the grid, float64: out_host = {E, E1, mu*E2} with
- * E1 = TV_eps(f) / Nv and E2 = |P f - Y|^2 / (n_angles nu nv).  Synchronises. */
+ * E1 = TV_eps(f) / Nv (tv_mode as in cbct_options) and
+ * E2 = |P f - Y|^2 / (n_angles nu nv).  Synchronises. */
 cbct_status cbct_energy(cbct_geometry *geom, const float *Y_dev, const float *f_dev, double mu,
-                        double eps, double out_host[3], cudaStream_t stream);
+                        double eps, int tv_mode, double out_host[3], cudaStream_t stream);
 
 /* Full reconstruction (Eq. 1 by Algorithm A1 with multigrid): for level
  * l = levels-1 .. 0 (coarsest first) the data are the 2x2-binned sinogram of the
@@ -278,8 +283,8 @@ void cbct_debug_fail_next_allocations(int n);
  * code running while a stream is captured into a CUDA graph, real-time or embedded
  * hosts that forbid allocation after start-up, plug-ins that must leave the device
  * heap alone -- and therefore cannot create a cbct_geometry.
- * Writes *e1_dev = TV_eps(f) / (nx ny nz) (device float64, same definition and
- * value as element 1 of cbct_energy) for f_dev, a [nz][ny][nx] float32 device
+ * Writes *e1_dev = TV_eps(f) / (nx ny nz) (device float64, isotropic; same
+ * definition and value as element 1 of cbct_energy with tv_mode 0) for f_dev, a [nz][ny][nx] float32 device
  * volume with spacings hx, hy, hz.  Asynchronous on `stream`.
  * Scratch: a 1 MiB array inside the library, reserved on every GPU that loads the
  * library until the process exits; hence volumes above CBCT_NOALLOC_MAX_VOXELS are

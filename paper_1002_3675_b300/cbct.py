@@ -43,7 +43,7 @@ class Options(C.Structure):
                 ("power_iters", C.c_int), ("start_level", C.c_int), ("f_init_dev", C.c_void_p),
                 ("use_graphs", C.c_int), ("energy_trace", C.POINTER(C.c_double)),
                 ("beta_out", C.POINTER(C.c_double)), ("kernel_ms", C.POINTER(C.c_float)),
-                ("kernel_launches", C.POINTER(C.c_int)), ("reuse_lambda", C.c_int)]
+                ("kernel_launches", C.POINTER(C.c_int)), ("reuse_lambda", C.c_int), ("tv_mode", C.c_int)]
 
 
 class Request(C.Structure):
@@ -85,10 +85,10 @@ _SIGS = {
     "cbct_level_dims": [_P, _I, C.POINTER(C.c_int)],
     "cbct_project": [_P, _P, _P, _V],
     "cbct_backproject": [_P, _P, _P, _V],
-    "cbct_tv_prox": [_P, _P, _P, _D, _D, _I, _V],
-    "cbct_fbs": [_P, _P, _D, _D, _D, _I, _I, _I, _P, C.POINTER(C.c_double), _V],
+    "cbct_tv_prox": [_P, _P, _P, _D, _D, _I, _I, _V],
+    "cbct_fbs": [_P, _P, _D, _D, _D, _I, _I, _I, _I, _P, C.POINTER(C.c_double), _V],
     "cbct_power_iteration": [_P, _I, C.POINTER(C.c_double), _V],
-    "cbct_energy": [_P, _P, _P, _D, _D, C.POINTER(C.c_double), _V],
+    "cbct_energy": [_P, _P, _P, _D, _D, _I, C.POINTER(C.c_double), _V],
     "cbct_reconstruct": [_P, _P, C.POINTER(C.c_double), _I, _D, _I, _I, C.POINTER(Options), _P, _V],
     "cbct_restrict_sino": [_I, _I, _I, _P, _P, _V],
     "cbct_prolong_vol": [_I, _I, _I, _P, _I, _I, _I, _P, _V],
@@ -213,15 +213,15 @@ def cbct_backproject(g: Geometry, y, f=None):
     return f
 
 
-def cbct_tv_prox(g: Geometry, gvol, f, beta: float, eps: float, inner_iters: int):
-    _check(lib.cbct_tv_prox(g.handle, _ptr(gvol, "g"), _ptr(f, "f"), beta, eps, inner_iters, _stream()))
+def cbct_tv_prox(g: Geometry, gvol, f, beta: float, eps: float, inner_iters: int, tv_mode: int = 0):
+    _check(lib.cbct_tv_prox(g.handle, _ptr(gvol, "g"), _ptr(f, "f"), beta, eps, inner_iters, tv_mode, _stream()))
     return f
 
 
-def cbct_fbs(g: Geometry, Y, mu, beta, eps, inner_iters, clamp_mode, iters, f, trace=False):
+def cbct_fbs(g: Geometry, Y, mu, beta, eps, inner_iters, clamp_mode, iters, f, trace=False, tv_mode=0):
     tr = np.zeros((max(iters, 1), 3)) if trace else None
-    _check(lib.cbct_fbs(g.handle, _ptr(Y, "Y"), mu, beta, eps, inner_iters, clamp_mode, iters, _ptr(f, "f"),
-                        tr.ctypes.data_as(C.POINTER(C.c_double)) if trace else None, _stream()))
+    _check(lib.cbct_fbs(g.handle, _ptr(Y, "Y"), mu, beta, eps, inner_iters, clamp_mode, tv_mode, iters,
+                        _ptr(f, "f"), tr.ctypes.data_as(C.POINTER(C.c_double)) if trace else None, _stream()))
     return (f, tr[:iters]) if trace else f
 
 
@@ -231,14 +231,15 @@ def cbct_power_iteration(g: Geometry, iters: int = 30) -> float:
     return lam.value
 
 
-def cbct_energy(g: Geometry, Y, f, mu, eps):
+def cbct_energy(g: Geometry, Y, f, mu, eps, tv_mode=0):
     out = (C.c_double * 3)()
-    _check(lib.cbct_energy(g.handle, _ptr(Y, "Y"), _ptr(f, "f"), mu, eps, out, _stream()))
+    _check(lib.cbct_energy(g.handle, _ptr(Y, "Y"), _ptr(f, "f"), mu, eps, tv_mode, out, _stream()))
     return np.array(out[:])
 
 
 def make_options(levels, *, beta=0.0, betas=None, eps=0.0, inner_iters=0, clamp_mode=0, sino_fp16=False,
-                 power_iters=0, f_init=None, start_level=0, use_graphs=False, reuse_lambda=False, keep=None):
+                 power_iters=0, f_init=None, start_level=0, use_graphs=False, reuse_lambda=False, tv_mode=0,
+                 keep=None):
     """cbct_options from keyword arguments; `keep` (a list) holds arrays the struct points to."""
     o = Options()
     o.beta = beta
@@ -256,13 +257,14 @@ def make_options(levels, *, beta=0.0, betas=None, eps=0.0, inner_iters=0, clamp_
     o.f_init_dev = _ptr(f_init, "f_init") if f_init is not None else None
     o.use_graphs = int(bool(use_graphs))
     o.reuse_lambda = int(bool(reuse_lambda))
+    o.tv_mode = int(tv_mode)
     return o
 
 
 def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=None, *, beta=0.0,
                      betas=None, eps=0.0, inner_iters=0, clamp_mode=0, sino_fp16=False, power_iters=0,
                      f_init=None, start_level=0, use_graphs=False, trace=False, kernel_times=False,
-                     reuse_lambda=False):
+                     reuse_lambda=False, tv_mode=0):
     """Returns f_out, or (f_out, info) when trace/kernel_times is requested; info holds
     'trace' [levels][iters][3], 'betas' [levels], 'kernel_ms'/'kernel_launches'."""
     f_out = _empty(g.vol_shape) if f_out is None else f_out
@@ -280,6 +282,7 @@ def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=N
     o.f_init_dev = _ptr(f_init, "f_init") if f_init is not None else None
     o.use_graphs = int(bool(use_graphs))
     o.reuse_lambda = int(bool(reuse_lambda))
+    o.tv_mode = int(tv_mode)
     tr = np.full((levels, max(iters, 1), 3), np.nan) if trace else None
     if trace:
         o.energy_trace = tr.ctypes.data_as(C.POINTER(C.c_double))
@@ -312,7 +315,7 @@ def cbct_reconstruct_batch(requests, use_graphs=False):
         g = r["geom"]
         levels = r["levels"]
         kw = {k: v for k, v in r.items() if k in ("beta", "betas", "eps", "inner_iters", "clamp_mode", "sino_fp16",
-                                                  "power_iters", "f_init", "start_level", "reuse_lambda")}
+                                                  "power_iters", "f_init", "start_level", "reuse_lambda", "tv_mode")}
         o = make_options(levels, keep=keep, **kw)
         info = {"betas": np.zeros(levels)}
         o.beta_out = info["betas"].ctypes.data_as(C.POINTER(C.c_double))

@@ -62,6 +62,7 @@ TvArgs tv_args(const Level *L, const SolveParams &P) {
     a.s = P.s;
     a.beta = P.beta;
     a.eps2 = P.eps2;
+    a.aniso = P.tv_mode;
     return a;
 }
 
@@ -300,7 +301,7 @@ cbct_status cbct::get_trace(cbct_geometry *G, size_t n, double **out) {
 }
 
 cbct_status cbct::solve_params(const Level *L, double mu, double beta, double eps, int M, int clamp_mode, bool fp16,
-                                SolveParams *P) {
+                                SolveParams *P, int tv_mode) {
     if (!(beta > 0) || !isfinite(beta)) {
         set_error("beta must be > 0");
         return CBCT_ERR_INVALID_ARG;
@@ -317,6 +318,10 @@ cbct_status cbct::solve_params(const Level *L, double mu, double beta, double ep
         set_error("clamp_mode must be 0 or 1");
         return CBCT_ERR_INVALID_ARG;
     }
+    if (tv_mode != 0 && tv_mode != 1) {
+        set_error("tv_mode must be 0 or 1");
+        return CBCT_ERR_INVALID_ARG;
+    }
     const double gam = gamma_of(L, mu);
     P->c = (float)(gam / beta);
     P->s = (float)(1.0 / (beta + tv_lipschitz(L, eps)));
@@ -324,6 +329,7 @@ cbct_status cbct::solve_params(const Level *L, double mu, double beta, double ep
     P->eps2 = (float)(eps * eps);
     P->M = M;
     P->clamp_mode = clamp_mode;
+    P->tv_mode = tv_mode;
     P->fp16 = fp16;
     P->inv_nv = 1.0 / (double)vol_elems(L->gd);
     P->mu_over_nr = mu / (double)sino_elems(L->gd);
@@ -357,6 +363,10 @@ cbct_status cbct::validate_request(cbct_geometry *G, const float *Y_dev, double 
     if (o) {
         if (o->clamp_mode != 0 && o->clamp_mode != 1) {
             set_error("clamp_mode must be 0 or 1");
+            return CBCT_ERR_INVALID_ARG;
+        }
+        if (o->tv_mode != 0 && o->tv_mode != 1) {
+            set_error("tv_mode must be 0 or 1");
             return CBCT_ERR_INVALID_ARG;
         }
         if (o->inner_iters < 0 || o->inner_iters > 10000 || o->power_iters < 0) {
@@ -490,7 +500,7 @@ cbct_status cbct_backproject(cbct_geometry *G, const float *y_dev, float *f_dev,
 
 
 cbct_status cbct_tv_prox(cbct_geometry *G, const float *g_dev, float *f_inout_dev, double beta, double eps,
-                         int inner_iters, cudaStream_t s) {
+                         int inner_iters, int tv_mode, cudaStream_t s) {
     if (!G) {
         set_error("geometry is null");
         return CBCT_ERR_INVALID_ARG;
@@ -501,7 +511,7 @@ cbct_status cbct_tv_prox(cbct_geometry *G, const float *g_dev, float *f_inout_de
     ST(ensure_level(G, 0, &L));
     ST(ensure_workspace(L, false));
     SolveParams P;
-    ST(solve_params(L, 1.0, beta, eps, inner_iters, 0, false, &P));
+    ST(solve_params(L, 1.0, beta, eps, inner_iters, 0, false, &P, tv_mode));
     const GeoDev &g = L->gd;
     CK(launch_vol_to_internal(g_dev, L->g, g.nx, g.ny, g.nz, s), "volume layout");
     CK(launch_vol_to_internal(f_inout_dev, L->f, g.nx, g.ny, g.nz, s), "volume layout");
@@ -512,7 +522,8 @@ cbct_status cbct_tv_prox(cbct_geometry *G, const float *g_dev, float *f_inout_de
 }
 
 cbct_status cbct_fbs(cbct_geometry *G, const float *Y_dev, double mu, double beta, double eps, int inner_iters,
-                     int clamp_mode, int iters, float *f_inout_dev, double *energy_trace, cudaStream_t s) {
+                     int clamp_mode, int tv_mode, int iters, float *f_inout_dev, double *energy_trace,
+                     cudaStream_t s) {
     if (!G) {
         set_error("geometry is null");
         return CBCT_ERR_INVALID_ARG;
@@ -527,7 +538,7 @@ cbct_status cbct_fbs(cbct_geometry *G, const float *Y_dev, double mu, double bet
     ST(ensure_level(G, 0, &L));
     ST(ensure_workspace(L, false));
     SolveParams P;
-    ST(solve_params(L, mu, beta, eps, inner_iters, clamp_mode, false, &P));
+    ST(solve_params(L, mu, beta, eps, inner_iters, clamp_mode, false, &P, tv_mode));
     double *dtrace;
     ST(get_trace(G, 3 * (size_t)std::max(iters, 1), &dtrace));
     const GeoDev &g = L->gd;
@@ -556,7 +567,7 @@ cbct_status cbct_power_iteration(cbct_geometry *G, int iters, double *lambda_out
 }
 
 cbct_status cbct_energy(cbct_geometry *G, const float *Y_dev, const float *f_dev, double mu, double eps,
-                        double out_host[3], cudaStream_t s) {
+                        int tv_mode, double out_host[3], cudaStream_t s) {
     if (!G || !out_host) {
         set_error("null argument");
         return CBCT_ERR_INVALID_ARG;
@@ -567,7 +578,7 @@ cbct_status cbct_energy(cbct_geometry *G, const float *Y_dev, const float *f_dev
     ST(ensure_level(G, 0, &L));
     ST(ensure_workspace(L, false));
     SolveParams P;
-    ST(solve_params(L, mu, 1.0, eps, 1, 0, false, &P));
+    ST(solve_params(L, mu, 1.0, eps, 1, 0, false, &P, tv_mode));
     double *dtrace;
     ST(get_trace(G, 3, &dtrace));
     const GeoDev &g = L->gd;
@@ -692,7 +703,7 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
         if (o.beta_out) o.beta_out[l] = beta;
         const double eps = o.eps > 0 ? o.eps : default_eps(L);
         SolveParams P;
-        ST(solve_params(L, mu, beta, eps, M, o.clamp_mode, fp16, &P));
+        ST(solve_params(L, mu, beta, eps, M, o.clamp_mode, fp16, &P, o.tv_mode));
         ST(run_level(G, L, P, iters, dtrace, o.use_graphs != 0, prof, s));
         if (o.energy_trace && iters > 0) {
             double *dst = o.energy_trace + 3 * (size_t)iters * (levels - 1 - l);

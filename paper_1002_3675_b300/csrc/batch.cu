@@ -365,7 +365,7 @@ cbct_status Engine::begin_fbs(Job *j, double beta) {
     j->beta = beta;
     if (j->o.beta_out) j->o.beta_out[j->level] = beta;
     const double eps = j->o.eps > 0 ? j->o.eps : default_eps(L);
-    EST(solve_params(L, j->mu, beta, eps, j->M, j->o.clamp_mode, j->fp16, &j->P));
+    EST(solve_params(L, j->mu, beta, eps, j->M, j->o.clamp_mode, j->fp16, &j->P, j->o.tv_mode));
     ECK(cudaMemsetAsync(j->G->dcounter, 0, sizeof(int), stream), "counter reset");
     j->it = 0;
     j->phase = j->iters > 0 ? PH_FBS : PH_LEVEL_DONE;

@@ -128,6 +128,7 @@ struct TvArgs {
     int nx, ny, nz;          // internal layout [nx][ny][nz]
     float ihx, ihy, ihz;     // 1/h
     float s, beta, eps2;
+    int aniso;               // 0: isotropic E1, 1: anisotropic E1
 };
 cudaError_t launch_tv_sweep(const TvArgs &a, const float *fin, const float *g, float *fout, bool clamp,
                             double *partial_e1, cudaStream_t s, int *nblocks_out);
@@ -168,6 +169,7 @@ struct SolveParams {
     float eps2;
     int M;
     int clamp_mode;
+    int tv_mode;
     bool fp16;
     double inv_nv, mu_over_nr;
 };
@@ -177,7 +179,7 @@ double gamma_of(const Level *L, double mu);
 cbct_status ensure_trace(cbct_geometry *G, size_t n);
 TvArgs tv_args(const Level *L, const SolveParams &P);
 cbct_status solve_params(const Level *L, double mu, double beta, double eps, int M, int clamp_mode, bool fp16,
-                         SolveParams *P);
+                         SolveParams *P, int tv_mode = 0);
 cbct_status get_trace(cbct_geometry *G, size_t n, double **out);
 
 }  // namespace cbct

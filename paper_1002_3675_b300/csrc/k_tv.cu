@@ -26,7 +26,11 @@ k_tv_energy(TvArgs A, const float *__restrict__ fin, double *__restrict__ partia
         const float gx = ((i < A.nx - 1 ? fin[idx + sx] : f0) - f0) * A.ihx;
         const float gy = ((j < A.ny - 1 ? fin[idx + sy] : f0) - f0) * A.ihy;
         const float gz = ((k < A.nz - 1 ? fin[idx + 1] : f0) - f0) * A.ihz;
-        e1 = sqrt((double)gx * gx + (double)gy * gy + (double)gz * gz + (double)A.eps2);
+        if (A.aniso)
+            e1 = sqrt((double)gx * gx + (double)A.eps2) + sqrt((double)gy * gy + (double)A.eps2) +
+                 sqrt((double)gz * gz + (double)A.eps2);
+        else
+            e1 = sqrt((double)gx * gx + (double)gy * gy + (double)gz * gz + (double)A.eps2);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) e1 += __shfl_down_sync(0xffffffffu, e1, off);
