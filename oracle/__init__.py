@@ -35,7 +35,8 @@ class _Geom(C.Structure):
                 ("hx", C.c_double), ("hy", C.c_double), ("hz", C.c_double),
                 ("nu", C.c_int), ("nv", C.c_int), ("du", C.c_double), ("dv", C.c_double),
                 ("dso", C.c_double), ("dsd", C.c_double),
-                ("na", C.c_int), ("angles", C.POINTER(C.c_double)), ("tv_mode", C.c_int)]
+                ("na", C.c_int), ("angles", C.POINTER(C.c_double)), ("tv_mode", C.c_int),
+                ("adjoint_mode", C.c_int)]
 
 
 class _Vol(C.Structure):
@@ -56,6 +57,7 @@ def _load():
             "or_project": (None, [G, _D, _D]),
             "or_backproject": (None, [G, _D, _D]),
             "or_backproject_voxel": (C.c_double, [G, _D, C.c_int, C.c_int, C.c_int]),
+            "or_backproject_eq2": (None, [G, _D, _D]),
             "or_project_ray": (C.c_double, [G, _D, C.c_int, C.c_int, C.c_int]),
             "or_ray_segments": (C.c_int, [G, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_long), _D, C.c_int]),
             "or_ray_voxel_length": (C.c_double, [G] + [C.c_int] * 6),
@@ -97,15 +99,15 @@ def _f64(a):
 class _GeomHolder:
     """Keeps the angle array alive while the C struct points into it."""
 
-    def __init__(self, geom: dict, tv_mode: int = 0):
+    def __init__(self, geom: dict, tv_mode: int = 0, adjoint_mode: int = 0):
         self.angles = _f64(geom["angles"])
         self.s = _Geom(geom["nx"], geom["ny"], geom["nz"], geom["hx"], geom["hy"], geom["hz"],
                        geom["nu"], geom["nv"], geom["du"], geom["dv"], geom["dso"], geom["dsd"],
-                       len(self.angles), _ptr(self.angles), int(tv_mode))
+                       len(self.angles), _ptr(self.angles), int(tv_mode), int(adjoint_mode))
 
 
-def _g(geom, tv_mode=0):
-    return _GeomHolder(geom, tv_mode)
+def _g(geom, tv_mode=0, adjoint_mode=0):
+    return _GeomHolder(geom, tv_mode, adjoint_mode)
 
 
 def _vol(shape, h, tv_mode=0):
@@ -144,6 +146,16 @@ def backproject(geom, y):
     f = np.empty(vol_shape(geom))
     h = _g(geom)
     _load().or_backproject(C.byref(h.s), _ptr(y), _ptr(f))
+    return f
+
+
+def backproject_eq2(geom, y):
+    """B y of Eq. 2: per voxel centre and view, y bilinearly interpolated at (u*, v*)
+    times L^3/(L0 l^2), summed over views and scaled by dV/(du dv)."""
+    y = _f64(y)
+    f = np.empty(vol_shape(geom))
+    h = _g(geom)
+    _load().or_backproject_eq2(C.byref(h.s), _ptr(y), _ptr(f))
     return f
 
 
@@ -241,11 +253,11 @@ def auto_beta(geom, mu, K=30):
     return _load().or_auto_beta(C.byref(h.s), mu, K)
 
 
-def fbs(geom, Y, mu, beta, eps, M, iters, f0=None, clamp_mode=0, tv_weight=1.0, tv_mode=0):
+def fbs(geom, Y, mu, beta, eps, M, iters, f0=None, clamp_mode=0, tv_weight=1.0, tv_mode=0, adjoint_mode=0):
     Y = _f64(Y)
     f = _f64(f0).copy() if f0 is not None else np.zeros(vol_shape(geom))
     trace = np.empty((iters, 3))
-    h = _g(geom, tv_mode)
+    h = _g(geom, tv_mode, adjoint_mode)
     _load().or_fbs(C.byref(h.s), _ptr(Y), mu, beta, eps, M, clamp_mode, tv_weight, iters, _ptr(f), _ptr(trace))
     return f, trace
 
@@ -277,12 +289,13 @@ def level_geom(geom, level):
     return g2
 
 
-def reconstruct(geom, Y, mu, iters, levels, betas=None, eps=0.0, M=10, clamp_mode=0, K_pi=30, tv_mode=0):
+def reconstruct(geom, Y, mu, iters, levels, betas=None, eps=0.0, M=10, clamp_mode=0, K_pi=30, tv_mode=0,
+                adjoint_mode=0):
     Y = _f64(Y)
     f = np.empty(vol_shape(geom))
     trace = np.empty((levels, iters, 3))
     b = _f64(betas) if betas is not None else None
-    h = _g(geom, tv_mode)
+    h = _g(geom, tv_mode, adjoint_mode)
     _load().or_reconstruct(C.byref(h.s), _ptr(Y), mu, iters, levels, _ptr(b), eps, M, clamp_mode,
                            K_pi, _ptr(f), _ptr(trace))
     return f, trace

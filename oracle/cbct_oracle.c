@@ -17,7 +17,10 @@
  *     projector: (Pf)_ray = sum_j |ray ∩ box_j| f_j, computed by merging the ray's
  *     plane crossings (Siddon's parametric method).
  *   - the adjoint used in step 1 of Algorithm A1 is the exact matrix transpose named
- *     in the paragraph before Eq. 2; here it is a scatter over the same crossings.
+ *     in the paragraph before Eq. 2; here it is a scatter over the same crossings
+ *     (adjoint_mode 0).  adjoint_mode 1 takes Eq. 2 itself instead: per voxel centre
+ *     and view, the residual bilinearly interpolated at the imager point (u*, v*)
+ *     weighted by L^3/(L0 l^2), times dV/(du dv) so that it approximates P^T.
  *   - E1 (Eq. 1) is the isotropic TV with forward differences, Neumann boundary,
  *     smoothed as sqrt(|grad f|^2 + eps^2) (tv_mode 0).  tv_mode 1 is the anisotropic
  *     reading of the l1 norm of the gradient, sum_d sqrt((D_d f)^2 + eps^2).
@@ -45,7 +48,8 @@ typedef struct {
     double dso, dsd;
     int na;
     const double *angles;
-    int tv_mode; /* 0: isotropic E1, 1: anisotropic E1 */
+    int tv_mode;      /* 0: isotropic E1, 1: anisotropic E1 */
+    int adjoint_mode; /* step 1 adjoint: 0 exact transpose, 1 Eq. 2 interpolation */
 } or_geom;
 
 /* ------------------------------------------------------------------------------ */
@@ -268,6 +272,57 @@ void or_backproject(const or_geom *g, const double *y, double *f)
         f[j] = s;
     }
     free(acc);
+}
+
+/*
+ * Eq. 2 read as an operator B on projection stacks (the paper's voxel-driven
+ * evaluation of the variation of E2).  With r(u*, v*) the bilinear interpolation of
+ * y between pixel centres (samples outside the pixel grid count as 0),
+ *   (B y)_j = dV / (du dv) * sum_theta L^3(u*, v*) / (L0 l^2(x_j)) * r_theta(u*, v*),
+ * where x_j is the voxel centre, (u*, v*) the imager point on the line from the
+ * source through x_j, l = |x_j - S|, L = |(u*, v*) - S| and L0 = dsd.  Multiplying
+ * Eq. 2 by Nv and writing A = Np du dv shows that B takes the place of P^T in
+ * step 1 (the matched transpose of the problem statement).
+ */
+void or_backproject_eq2(const or_geom *g, const double *y, double *f)
+{
+    const double dV = g->hx * g->hy * g->hz;
+    const double scale = dV / (g->du * g->dv);
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < g->nz; ++k)
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i) {
+                double x = (i - 0.5 * (g->nx - 1)) * g->hx;
+                double yy = (j - 0.5 * (g->ny - 1)) * g->hy;
+                double z = (k - 0.5 * (g->nz - 1)) * g->hz;
+                double acc = 0.0;
+                for (int ia = 0; ia < g->na; ++ia) {
+                    double c = cos(g->angles[ia]), s = sin(g->angles[ia]);
+                    /* source frame: depth along the central ray, offsets along u and v */
+                    double depth = g->dso - (x * c + yy * s);
+                    double us = g->dsd * (-x * s + yy * c) / depth;
+                    double vs = g->dsd * z / depth;
+                    double dx = x - g->dso * c, dy = yy - g->dso * s;
+                    double l2 = dx * dx + dy * dy + z * z;
+                    double L = sqrt(g->dsd * g->dsd + us * us + vs * vs);
+                    double w = L * L * L / (g->dsd * l2);
+                    /* bilinear interpolation between pixel centres */
+                    double fa = us / g->du + 0.5 * (g->nu - 1);
+                    double fb = vs / g->dv + 0.5 * (g->nv - 1);
+                    int a0 = (int)floor(fa), b0 = (int)floor(fb);
+                    double ta = fa - a0, tb = fb - b0;
+                    double r = 0.0;
+                    for (int db = 0; db <= 1; ++db)
+                        for (int da = 0; da <= 1; ++da) {
+                            int a = a0 + da, b = b0 + db;
+                            if (a < 0 || a >= g->nu || b < 0 || b >= g->nv) continue;
+                            double wt = (da ? ta : 1.0 - ta) * (db ? tb : 1.0 - tb);
+                            r += wt * y[((long)ia * g->nv + b) * g->nu + a];
+                        }
+                    acc += w * r;
+                }
+                f[((long)k * g->ny + j) * g->nx + i] = scale * acc;
+            }
 }
 
 /*
@@ -554,6 +609,7 @@ double or_auto_beta(const or_geom *g, double mu, int K)
 /*
  * Algorithm A1 for `iters` iterations from the volume in f (updated in place).
  * trace (optional, 3 * iters): {E, E1, E2-term} of the iterate entering each iteration.
+ * Step 1 uses the exact transpose, or B of Eq. 2 when g->adjoint_mode is 1.
  */
 void or_fbs(const or_geom *g, const double *Y, double mu, double beta, double eps, int M,
             int clamp_mode, double tv_weight, int iters, double *f, double *trace)
@@ -580,7 +636,10 @@ void or_fbs(const or_geom *g, const double *Y, double mu, double beta, double ep
             trace[3 * it + 1] = e1;
             trace[3 * it + 2] = e2;
         }
-        or_backproject(g, r, bp);
+        if (g->adjoint_mode == 1)
+            or_backproject_eq2(g, r, bp);
+        else
+            or_backproject(g, r, bp);
         double c = gamma / beta;
         for (long j = 0; j < nvox; ++j) gv[j] = f[j] - c * bp[j];
         /* steps 2 and 3 */

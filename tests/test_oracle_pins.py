@@ -199,6 +199,95 @@ def test_adjoint_matches_eq2_jacobian():
     assert np.abs(ratios - 1.0).max() < 0.05
 
 
+def _imager_point(g, th, x):
+    """(a*, b*, L, l) for voxel centre x: the line from the source through x meets the
+    imager plane; solved as a 3x3 linear system (independent of the oracle's closed
+    form)."""
+    S = np.array([g["dso"] * math.cos(th), g["dso"] * math.sin(th), 0.0])
+    C = S + g["dsd"] * np.array([-math.cos(th), -math.sin(th), 0.0])
+    eu = np.array([-math.sin(th), math.cos(th), 0.0])
+    ev = np.array([0.0, 0.0, 1.0])
+    # S + t (x - S) = C + u eu + v ev
+    t, u, v = np.linalg.solve(np.column_stack([x - S, -eu, -ev]), C - S)
+    P = S + t * (x - S)
+    a = u / g["du"] + (g["nu"] - 1) / 2
+    b = v / g["dv"] + (g["nv"] - 1) / 2
+    return a, b, float(np.linalg.norm(P - S)), float(np.linalg.norm(x - S))
+
+
+def _eq2_geom():
+    return dict(nx=10, ny=9, nz=8, hx=4.0, hy=4.5, hz=5.0, nu=36, nv=30, du=3.0, dv=3.5,
+                dso=300.0, dsd=450.0, angles=2 * math.pi * np.arange(5) / 5 + 0.13)
+
+
+def _centre(g, i, j, k):
+    return np.array([(i - (g["nx"] - 1) / 2) * g["hx"], (j - (g["ny"] - 1) / 2) * g["hy"],
+                     (k - (g["nz"] - 1) / 2) * g["hz"]])
+
+
+def test_eq2_adjoint_single_pixel_impulse():
+    """B of Eq. 2 applied to one pixel of one view: every voxel whose imager point lies
+    within one pixel of it (in both directions) gets dV/(du dv) L^3/(L0 l^2) times the
+    bilinear hat weight, every other voxel exactly 0."""
+    g = _eq2_geom()
+    ia, bp, ap = 2, 17, 14
+    y = np.zeros((5, 30, 36))
+    y[ia, bp, ap] = 1.0
+    B = oracle.backproject_eq2(g, y)
+    scale = g["hx"] * g["hy"] * g["hz"] / (g["du"] * g["dv"])
+    hit = 0
+    for k in range(g["nz"]):
+        for j in range(g["ny"]):
+            for i in range(g["nx"]):
+                a, b, L, l = _imager_point(g, g["angles"][ia], _centre(g, i, j, k))
+                wa, wb = 1 - abs(a - ap), 1 - abs(b - bp)
+                ref = scale * L ** 3 / (g["dsd"] * l * l) * wa * wb if (wa > 0 and wb > 0) else 0.0
+                hit += ref > 0
+                assert abs(B[k, j, i] - ref) <= 1e-12 * max(1.0, abs(ref))
+    assert hit >= 2
+
+
+def test_eq2_adjoint_reproduces_linear_residuals():
+    """Bilinear interpolation is exact for residuals linear in the pixel indices, so
+    B y is a closed form in (a*, b*) for voxels that project inside the pixel grid."""
+    g = _eq2_geom()
+    ia_, b_, a_ = np.meshgrid(np.arange(5), np.arange(30), np.arange(36), indexing="ij")
+    y = 0.7 + 0.013 * a_ - 0.021 * b_ + 0.05 * ia_
+    B = oracle.backproject_eq2(g, y)
+    scale = g["hx"] * g["hy"] * g["hz"] / (g["du"] * g["dv"])
+    for (i, j, k) in [(0, 0, 0), (9, 8, 7), (4, 4, 4), (2, 7, 5), (8, 1, 3)]:
+        ref = 0.0
+        for t, th in enumerate(g["angles"]):
+            a, b, L, l = _imager_point(g, th, _centre(g, i, j, k))
+            assert 0 <= a <= 35 and 0 <= b <= 29
+            ref += scale * L ** 3 / (g["dsd"] * l * l) * (0.7 + 0.013 * a - 0.021 * b + 0.05 * t)
+        assert abs(B[k, j, i] - ref) <= 1e-12 * abs(ref)
+
+
+def test_eq2_adjoint_approaches_the_transpose():
+    """With an imager that samples every voxel finely, B 1 and P^T 1 agree on interior
+    voxels (Eq. 2 is the continuum form of the transpose)."""
+    n, h = 12, 4.0
+    g = dict(nx=n, ny=n, nz=n, hx=h, hy=h, hz=h, nu=200, nv=200, du=0.6, dv=0.6,
+             dso=300.0, dsd=450.0, angles=2 * math.pi * np.arange(8) / 8 + 0.05)
+    ones = np.ones((8, 200, 200))
+    ratio = oracle.backproject_eq2(g, ones)[3:9, 3:9, 3:9] / oracle.backproject(g, ones)[3:9, 3:9, 3:9]
+    assert abs(ratio.mean() - 1.0) < 0.01
+    assert np.abs(ratio - 1.0).max() < 0.05
+
+
+def test_fbs_with_eq2_adjoint_reduces_the_energy():
+    case = synth.make_case("small")
+    g = case["geom"]
+    mu, eps = case["mu"], oracle.default_eps(g)
+    beta = oracle.auto_beta(g, mu)
+    f, tr = oracle.fbs(g, case["Y"], mu, beta, eps, 10, 20, adjoint_mode=1)
+    E_end = oracle.energy(g, case["Y"], f, mu, eps)[0]
+    assert E_end < 0.3 * tr[0, 0] and (f >= 0).all()
+    f0, _ = oracle.fbs(g, case["Y"], mu, beta, eps, 10, 20)
+    assert np.linalg.norm(f - f0) > 1e-3 * np.linalg.norm(f0)   # a different operator
+
+
 # ---------------------------------------------------------------------------------
 # E1 and the step-2 prox (Algorithm A1 steps 2 and 3)
 # ---------------------------------------------------------------------------------
