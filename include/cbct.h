@@ -103,6 +103,10 @@ typedef struct {
     int tv_mode;          /* E1 of Eq. 1: 0 isotropic sum_j sqrt(|grad f|_j^2 + eps^2)
                              [default]; 1 anisotropic sum_j sum_d sqrt((D_d f)_j^2 + eps^2)
                              (the l1 norm of the gradient taken per axis)        */
+    int adjoint_mode;     /* the adjoint in step 1 of Algorithm A1: 0 the exact transpose
+                             P^T [default]; 1 the voxel-driven interpolation of Eq. 2
+                             (see cbct_backproject_eq2).  The automatic beta always
+                             comes from lambda_max(P^T P).                        */
 } cbct_options;
 
 /* Kernel classes reported through cbct_options.kernel_ms. */
@@ -139,6 +143,16 @@ cbct_status cbct_project(cbct_geometry *geom, const float *f_dev, float *y_dev, 
  * the same intersection lengths, in a fixed order and without atomics.
  * y_dev: sinogram; f_dev: volume (written). */
 cbct_status cbct_backproject(cbct_geometry *geom, const float *y_dev, float *f_dev, cudaStream_t stream);
+
+/* The variation of E2 as Eq. 2 evaluates it, as an operator on projection stacks:
+ *   f_j = dV / (du dv) * sum_theta L^3 / (L0 l^2) * y_theta(u*, v*)
+ * for every voxel centre x_j, where (u*, v*) is the imager point on the line from the
+ * source through x_j, l = |x_j - source|, L = |(u*, v*) - source|, L0 = dsd, and
+ * y_theta(u*, v*) interpolates y bilinearly between pixel centres (zero outside the
+ * pixel grid).  The factor dV / (du dv) makes it an approximation of P^T y (Eq. 2
+ * times Nv with A = nu nv du dv); it is not its exact transpose.
+ * y_dev: sinogram; f_dev: volume (written). */
+cbct_status cbct_backproject_eq2(cbct_geometry *geom, const float *y_dev, float *f_dev, cudaStream_t stream);
 
 /* Steps 2 and 3 of Algorithm A1 on the geometry's grid: inner_iters projected
  * gradient steps on TV_eps(f) + beta/2 |f - g|^2 over f >= 0, starting from the

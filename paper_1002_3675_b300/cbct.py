@@ -43,7 +43,8 @@ class Options(C.Structure):
                 ("power_iters", C.c_int), ("start_level", C.c_int), ("f_init_dev", C.c_void_p),
                 ("use_graphs", C.c_int), ("energy_trace", C.POINTER(C.c_double)),
                 ("beta_out", C.POINTER(C.c_double)), ("kernel_ms", C.POINTER(C.c_float)),
-                ("kernel_launches", C.POINTER(C.c_int)), ("reuse_lambda", C.c_int), ("tv_mode", C.c_int)]
+                ("kernel_launches", C.POINTER(C.c_int)), ("reuse_lambda", C.c_int), ("tv_mode", C.c_int),
+                ("adjoint_mode", C.c_int)]
 
 
 class Request(C.Structure):
@@ -85,6 +86,7 @@ _SIGS = {
     "cbct_level_dims": [_P, _I, C.POINTER(C.c_int)],
     "cbct_project": [_P, _P, _P, _V],
     "cbct_backproject": [_P, _P, _P, _V],
+    "cbct_backproject_eq2": [_P, _P, _P, _V],
     "cbct_tv_prox": [_P, _P, _P, _D, _D, _I, _I, _V],
     "cbct_fbs": [_P, _P, _D, _D, _D, _I, _I, _I, _I, _P, C.POINTER(C.c_double), _V],
     "cbct_power_iteration": [_P, _I, C.POINTER(C.c_double), _V],
@@ -213,6 +215,12 @@ def cbct_backproject(g: Geometry, y, f=None):
     return f
 
 
+def cbct_backproject_eq2(g: Geometry, y, f=None):
+    f = _empty(g.vol_shape) if f is None else f
+    _check(lib.cbct_backproject_eq2(g.handle, _ptr(y, "y"), _ptr(f, "f"), _stream()))
+    return f
+
+
 def cbct_tv_prox(g: Geometry, gvol, f, beta: float, eps: float, inner_iters: int, tv_mode: int = 0):
     _check(lib.cbct_tv_prox(g.handle, _ptr(gvol, "g"), _ptr(f, "f"), beta, eps, inner_iters, tv_mode, _stream()))
     return f
@@ -239,7 +247,7 @@ def cbct_energy(g: Geometry, Y, f, mu, eps, tv_mode=0):
 
 def make_options(levels, *, beta=0.0, betas=None, eps=0.0, inner_iters=0, clamp_mode=0, sino_fp16=False,
                  power_iters=0, f_init=None, start_level=0, use_graphs=False, reuse_lambda=False, tv_mode=0,
-                 keep=None):
+                 adjoint_mode=0, keep=None):
     """cbct_options from keyword arguments; `keep` (a list) holds arrays the struct points to."""
     o = Options()
     o.beta = beta
@@ -258,13 +266,14 @@ def make_options(levels, *, beta=0.0, betas=None, eps=0.0, inner_iters=0, clamp_
     o.use_graphs = int(bool(use_graphs))
     o.reuse_lambda = int(bool(reuse_lambda))
     o.tv_mode = int(tv_mode)
+    o.adjoint_mode = int(adjoint_mode)
     return o
 
 
 def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=None, *, beta=0.0,
                      betas=None, eps=0.0, inner_iters=0, clamp_mode=0, sino_fp16=False, power_iters=0,
                      f_init=None, start_level=0, use_graphs=False, trace=False, kernel_times=False,
-                     reuse_lambda=False, tv_mode=0):
+                     reuse_lambda=False, tv_mode=0, adjoint_mode=0):
     """Returns f_out, or (f_out, info) when trace/kernel_times is requested; info holds
     'trace' [levels][iters][3], 'betas' [levels], 'kernel_ms'/'kernel_launches'."""
     f_out = _empty(g.vol_shape) if f_out is None else f_out
@@ -283,6 +292,7 @@ def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=N
     o.use_graphs = int(bool(use_graphs))
     o.reuse_lambda = int(bool(reuse_lambda))
     o.tv_mode = int(tv_mode)
+    o.adjoint_mode = int(adjoint_mode)
     tr = np.full((levels, max(iters, 1), 3), np.nan) if trace else None
     if trace:
         o.energy_trace = tr.ctypes.data_as(C.POINTER(C.c_double))
@@ -315,7 +325,7 @@ def cbct_reconstruct_batch(requests, use_graphs=False):
         g = r["geom"]
         levels = r["levels"]
         kw = {k: v for k, v in r.items() if k in ("beta", "betas", "eps", "inner_iters", "clamp_mode", "sino_fp16",
-                                                  "power_iters", "f_init", "start_level", "reuse_lambda", "tv_mode")}
+                                                  "power_iters", "f_init", "start_level", "reuse_lambda", "tv_mode", "adjoint_mode")}
         o = make_options(levels, keep=keep, **kw)
         info = {"betas": np.zeros(levels)}
         o.beta_out = info["betas"].ctypes.data_as(C.POINTER(C.c_double))

@@ -23,6 +23,8 @@ const char *last_error();
 
 namespace cbct {
 
+double eq2_scale(const Level *L) { return L->hx * L->hy * L->hz / (L->du * L->dv); }
+
 double default_eps(const Level *L) { return 2e-5 / std::min(L->hx, std::min(L->hy, L->hz)); }
 
 double tv_lipschitz(const Level *L, double eps) {
@@ -172,15 +174,19 @@ cbct_status enqueue_iteration(cbct_geometry *G, Level *L, const SolveParams &P, 
         Launch l(prof, CBCT_K_REDUCE);
         CK(launch_tv_energy(tv_args(L, P), L->f, pt, s, &nb_t), "tv energy");
     }
+    const bool eq2 = P.adjoint_mode == 1;
     {
         Launch l(prof, CBCT_K_PROJECT);
-        CK(launch_project(gd, L->f, P.fp16 ? nullptr : L->Y, P.fp16 ? L->Yh : nullptr, L->rs, pp,
-                          P.fp16 ? PROJ_RESID16 : PROJ_RESID32, s, &nb_p),
+        const int mode = P.fp16 ? (eq2 ? PROJ_RAW16 : PROJ_RESID16) : (eq2 ? PROJ_RAW32 : PROJ_RESID32);
+        CK(launch_project(gd, L->f, P.fp16 ? nullptr : L->Y, P.fp16 ? L->Yh : nullptr, L->rs, pp, mode, s, &nb_p),
            "projection");
     }
     {
         Launch l(prof, CBCT_K_BACKPROJECT);
-        CK(launch_backproject(gd, L->rs, L->f, L->g, P.c, BP_STEP, s), "backprojection");
+        if (eq2)
+            CK(launch_backproject_eq2(gd, L->rs, L->f, L->g, P.c_eq2, BP_STEP, s), "eq2 backprojection");
+        else
+            CK(launch_backproject(gd, L->rs, L->f, L->g, P.c, BP_STEP, s), "backprojection");
     }
     ST(enqueue_prox(L, P, P.clamp_mode == 0 ? L->f : L->g, P.clamp_mode == 0 ? pt : nullptr,
                     P.clamp_mode == 0 ? &nb_t : nullptr, prof, s));
@@ -301,7 +307,7 @@ cbct_status cbct::get_trace(cbct_geometry *G, size_t n, double **out) {
 }
 
 cbct_status cbct::solve_params(const Level *L, double mu, double beta, double eps, int M, int clamp_mode, bool fp16,
-                                SolveParams *P, int tv_mode) {
+                                SolveParams *P, int tv_mode, int adjoint_mode) {
     if (!(beta > 0) || !isfinite(beta)) {
         set_error("beta must be > 0");
         return CBCT_ERR_INVALID_ARG;
@@ -322,6 +328,10 @@ cbct_status cbct::solve_params(const Level *L, double mu, double beta, double ep
         set_error("tv_mode must be 0 or 1");
         return CBCT_ERR_INVALID_ARG;
     }
+    if (adjoint_mode != 0 && adjoint_mode != 1) {
+        set_error("adjoint_mode must be 0 or 1");
+        return CBCT_ERR_INVALID_ARG;
+    }
     const double gam = gamma_of(L, mu);
     P->c = (float)(gam / beta);
     P->s = (float)(1.0 / (beta + tv_lipschitz(L, eps)));
@@ -330,6 +340,8 @@ cbct_status cbct::solve_params(const Level *L, double mu, double beta, double ep
     P->M = M;
     P->clamp_mode = clamp_mode;
     P->tv_mode = tv_mode;
+    P->adjoint_mode = adjoint_mode;
+    P->c_eq2 = (float)(gam / beta * eq2_scale(L));
     P->fp16 = fp16;
     P->inv_nv = 1.0 / (double)vol_elems(L->gd);
     P->mu_over_nr = mu / (double)sino_elems(L->gd);
@@ -367,6 +379,10 @@ cbct_status cbct::validate_request(cbct_geometry *G, const float *Y_dev, double 
         }
         if (o->tv_mode != 0 && o->tv_mode != 1) {
             set_error("tv_mode must be 0 or 1");
+            return CBCT_ERR_INVALID_ARG;
+        }
+        if (o->adjoint_mode != 0 && o->adjoint_mode != 1) {
+            set_error("adjoint_mode must be 0 or 1");
             return CBCT_ERR_INVALID_ARG;
         }
         if (o->inner_iters < 0 || o->inner_iters > 10000 || o->power_iters < 0) {
@@ -494,6 +510,23 @@ cbct_status cbct_backproject(cbct_geometry *G, const float *y_dev, float *f_dev,
     const GeoDev &g = L->gd;
     CK(launch_sino_to_internal(y_dev, L->rs, nullptr, g.ray_z, g.na, g.nu, g.nv, s), "sinogram layout");
     CK(launch_backproject(g, L->rs, nullptr, L->A, 0.f, BP_PLAIN, s), "backprojection");
+    CK(launch_vol_to_api(L->A, f_dev, g.nx, g.ny, g.nz, s), "volume layout");
+    return CBCT_OK;
+}
+
+cbct_status cbct_backproject_eq2(cbct_geometry *G, const float *y_dev, float *f_dev, cudaStream_t s) {
+    if (!G) {
+        set_error("geometry is null");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    ST(need_ptr(y_dev, "y_dev"));
+    ST(need_ptr(f_dev, "f_dev"));
+    Level *L;
+    ST(ensure_level(G, 0, &L));
+    ST(ensure_workspace(L, false));
+    const GeoDev &g = L->gd;
+    CK(launch_sino_to_internal(y_dev, L->rs, nullptr, nullptr, g.na, g.nu, g.nv, s), "sinogram layout");
+    CK(launch_backproject_eq2(g, L->rs, nullptr, L->A, (float)eq2_scale(L), BP_PLAIN, s), "eq2 backprojection");
     CK(launch_vol_to_api(L->A, f_dev, g.nx, g.ny, g.nz, s), "volume layout");
     return CBCT_OK;
 }
@@ -703,7 +736,7 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
         if (o.beta_out) o.beta_out[l] = beta;
         const double eps = o.eps > 0 ? o.eps : default_eps(L);
         SolveParams P;
-        ST(solve_params(L, mu, beta, eps, M, o.clamp_mode, fp16, &P, o.tv_mode));
+        ST(solve_params(L, mu, beta, eps, M, o.clamp_mode, fp16, &P, o.tv_mode, o.adjoint_mode));
         ST(run_level(G, L, P, iters, dtrace, o.use_graphs != 0, prof, s));
         if (o.energy_trace && iters > 0) {
             double *dst = o.energy_trace + 3 * (size_t)iters * (levels - 1 - l);

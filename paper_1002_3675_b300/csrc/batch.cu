@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "batch.h"
+#include "bp_eq2_tile.cuh"
 #include "bp_tile.cuh"
 #include "project_tile.cuh"
 #include "tv_tile.cuh"
@@ -42,6 +43,15 @@ struct BpItem {
     const float *fin;
     float *out;
     float c;
+    int mode;
+};
+
+struct Eq2Item {  // Eq. 2 adjoint + gradient step of one request
+    GeoDev G;
+    const float *r;
+    const float *fin;
+    float *out;
+    float cscale;
     int mode;
 };
 
@@ -121,6 +131,18 @@ k_bp_batch(const BpItem *__restrict__ items, const long *__restrict__ start, int
         __syncwarp();
         bp_warp<VPL>(it[w].G, it[w].mode, it[w].rs, it[w].fin, it[w].out, it[w].c, t - start[r]);
         __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(EQ2_THREADS)
+k_eq2_batch(const Eq2Item *__restrict__ items, const long *__restrict__ start, int n, long total) {
+    __shared__ Eq2Item it;
+    for (long t = blockIdx.x; t < total; t += gridDim.x) {
+        const int r = find_item(start, n, t);
+        copy_words(&it, items + r, sizeof(Eq2Item), threadIdx.x, blockDim.x);
+        __syncthreads();
+        eq2_block(it.G, it.r, it.fin, it.out, it.cscale, it.mode, t - start[r]);
+        __syncthreads();
     }
 }
 
@@ -365,7 +387,7 @@ cbct_status Engine::begin_fbs(Job *j, double beta) {
     j->beta = beta;
     if (j->o.beta_out) j->o.beta_out[j->level] = beta;
     const double eps = j->o.eps > 0 ? j->o.eps : default_eps(L);
-    EST(solve_params(L, j->mu, beta, eps, j->M, j->o.clamp_mode, j->fp16, &j->P, j->o.tv_mode));
+    EST(solve_params(L, j->mu, beta, eps, j->M, j->o.clamp_mode, j->fp16, &j->P, j->o.tv_mode, j->o.adjoint_mode));
     ECK(cudaMemsetAsync(j->G->dcounter, 0, sizeof(int), stream), "counter reset");
     j->it = 0;
     j->phase = j->iters > 0 ? PH_FBS : PH_LEVEL_DONE;
@@ -400,7 +422,9 @@ cbct_status Engine::build_tables() {
     htv.clear();
     hen.clear();
     std::vector<long> pstart, dstart;
-    std::vector<long> bpstart[4];
+    std::vector<long> bpstart[4], eqstart;
+    heq.clear();
+    long eqtot = 0;
     std::vector<std::vector<long>> tvstart;
     long ptot = 0, dtot = 0, bptot[4] = {0, 0, 0, 0};
     proj_threads = 32;
@@ -420,21 +444,37 @@ cbct_status Engine::build_tables() {
         pi.y16 = (!power && j->fp16) ? L->Yh : nullptr;
         pi.out = L->rs;
         pi.partial = power ? nullptr : L->partial;
-        pi.mode = power ? PROJ_SCALED : (j->fp16 ? PROJ_RESID16 : PROJ_RESID32);
+        const bool eq2 = !power && j->P.adjoint_mode == 1;
+        pi.mode = power ? PROJ_SCALED
+                        : (j->fp16 ? (eq2 ? PROJ_RAW16 : PROJ_RESID16) : (eq2 ? PROJ_RAW32 : PROJ_RESID32));
         hproj.push_back(pi);
+        if (eq2) {
+            Eq2Item ei;
+            ei.G = g;
+            ei.r = L->rs;
+            ei.fin = L->f;
+            ei.out = L->g;
+            ei.cscale = j->P.c_eq2;
+            ei.mode = BP_STEP;
+            heq.push_back(ei);
+            eqstart.push_back(eqtot);
+            eqtot += (long)((vol_elems(g) + EQ2_THREADS - 1) / EQ2_THREADS);
+        }
         const int vpl = (g.bp_vpl >= 1 && g.bp_vpl <= 4) ? g.bp_vpl : bp_default_vpl(g);
-        BpItem bi;
-        bi.G = g;
-        bi.rs = L->rs;
-        bi.fin = power ? nullptr : L->f;
-        bi.out = power ? L->B : L->g;
-        bi.c = power ? 0.f : j->P.c;
-        bi.mode = power ? BP_PLAIN : BP_STEP;
-        hbp[vpl - 1].push_back(bi);
-        bpstart[vpl - 1].push_back(bptot[vpl - 1]);
-        long wt = vpl == 1 ? bp_warp_tiles<1>(g) : vpl == 2 ? bp_warp_tiles<2>(g) : vpl == 3 ? bp_warp_tiles<3>(g)
-                                                                                      : bp_warp_tiles<4>(g);
-        bptot[vpl - 1] += wt;
+        if (!eq2) {
+            BpItem bi;
+            bi.G = g;
+            bi.rs = L->rs;
+            bi.fin = power ? nullptr : L->f;
+            bi.out = power ? L->B : L->g;
+            bi.c = power ? 0.f : j->P.c;
+            bi.mode = power ? BP_PLAIN : BP_STEP;
+            hbp[vpl - 1].push_back(bi);
+            bpstart[vpl - 1].push_back(bptot[vpl - 1]);
+            long wt = vpl == 1 ? bp_warp_tiles<1>(g) : vpl == 2 ? bp_warp_tiles<2>(g) : vpl == 3 ? bp_warp_tiles<3>(g)
+                                                                                          : bp_warp_tiles<4>(g);
+            bptot[vpl - 1] += wt;
+        }
         if (power) {
             VecItem vi;
             vi.x = L->A;
@@ -499,6 +539,7 @@ cbct_status Engine::build_tables() {
     ptotal = ptot;
     dtotal = dtot;
     for (int v = 0; v < 4; ++v) bptotal[v] = bptot[v];
+    eqtotal = eqtot;
 
     // one device blob: items and start tables
     size_t off = 0;
@@ -513,6 +554,7 @@ cbct_status Engine::build_tables() {
         o_bp[v] = place(hbp[v].size() * sizeof(BpItem));
         o_bst[v] = place(bpstart[v].size() * sizeof(long));
     }
+    const size_t o_eq = place(heq.size() * sizeof(Eq2Item)), o_est = place(eqstart.size() * sizeof(long));
     const size_t o_dot = place(hdot.size() * sizeof(VecItem)), o_dst = place(dstart.size() * sizeof(long));
     std::vector<size_t> o_tv(max_m), o_tst(max_m);
     for (int m = 0; m < max_m; ++m) {
@@ -530,6 +572,8 @@ cbct_status Engine::build_tables() {
         put(o_bp[v], hbp[v].data(), hbp[v].size() * sizeof(BpItem));
         put(o_bst[v], bpstart[v].data(), bpstart[v].size() * sizeof(long));
     }
+    put(o_eq, heq.data(), heq.size() * sizeof(Eq2Item));
+    put(o_est, eqstart.data(), eqstart.size() * sizeof(long));
     put(o_dot, hdot.data(), hdot.size() * sizeof(VecItem));
     put(o_dst, dstart.data(), dstart.size() * sizeof(long));
     for (int m = 0; m < max_m; ++m) {
@@ -555,6 +599,8 @@ cbct_status Engine::build_tables() {
         d_bp[v] = (BpItem *)(b + o_bp[v]);
         d_bstart[v] = (long *)(b + o_bst[v]);
     }
+    d_eq = (Eq2Item *)(b + o_eq);
+    d_eqstart = (long *)(b + o_est);
     d_dot = (VecItem *)(b + o_dot);
     d_dstart = (long *)(b + o_dst);
     d_tv.assign(max_m, nullptr);
@@ -597,6 +643,10 @@ cbct_status Engine::launch_stages() {
         if (v == 2) k_bp_batch<3><<<(unsigned)nblk, BP_THREADS, 0, s>>>(d_bp[2], d_bstart[2], n, bptotal[2]);
         if (v == 3) k_bp_batch<4><<<(unsigned)nblk, BP_THREADS, 0, s>>>(d_bp[3], d_bstart[3], n, bptotal[3]);
         ECK(cudaGetLastError(), "batched backprojection");
+    }
+    if (!heq.empty()) {
+        k_eq2_batch<<<(unsigned)grid_for(eqtotal, 8), EQ2_THREADS, 0, s>>>(d_eq, d_eqstart, (int)heq.size(), eqtotal);
+        ECK(cudaGetLastError(), "batched eq2 backprojection");
     }
     if (!hdot.empty()) {
         const int n = (int)hdot.size();

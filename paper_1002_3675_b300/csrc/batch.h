@@ -9,6 +9,7 @@ namespace cbct {
 
 struct ProjItem;
 struct BpItem;
+struct Eq2Item;
 struct TvItem;
 struct VecItem;
 struct EnItem;
@@ -69,13 +70,14 @@ class Engine {
     // host copies of the item tables and their device blob
     std::vector<ProjItem> hproj;
     std::vector<BpItem> hbp[4];
+    std::vector<Eq2Item> heq;
     std::vector<VecItem> hdot;
     std::vector<std::vector<TvItem>> htv;
     std::vector<EnItem> hen;
     std::vector<long> tvtot;
     std::vector<CopyOp> copies;
     std::vector<Job *> tv_energy_jobs;
-    long ptotal = 0, dtotal = 0, bptotal[4] = {0, 0, 0, 0};
+    long ptotal = 0, dtotal = 0, bptotal[4] = {0, 0, 0, 0}, eqtotal = 0;
     int proj_threads = 32, max_m = 0;
     void *dblob = nullptr;
     size_t dblob_len = 0;
@@ -83,6 +85,8 @@ class Engine {
     long *d_pstart = nullptr;
     BpItem *d_bp[4] = {nullptr, nullptr, nullptr, nullptr};
     long *d_bstart[4] = {nullptr, nullptr, nullptr, nullptr};
+    Eq2Item *d_eq = nullptr;
+    long *d_eqstart = nullptr;
     VecItem *d_dot = nullptr;
     long *d_dstart = nullptr;
     std::vector<TvItem *> d_tv;

@@ -113,7 +113,12 @@ cbct_status ensure_workspace(Level *L, bool need_half);
 void free_level(Level *L);
 
 // kernel launchers (return cudaError_t of the launch)
-enum ProjMode { PROJ_PLAIN = 0, PROJ_RESID32 = 1, PROJ_RESID16 = 2, PROJ_SCALED = 3 };
+// RESID32/RESID16 store sec(phi) * (P f - Y) for the matched gather; the RAW variants
+// store P f - Y itself (the Eq. 2 adjoint interpolates the residual).
+enum ProjMode { PROJ_PLAIN = 0, PROJ_RESID32 = 1, PROJ_RESID16 = 2, PROJ_SCALED = 3, PROJ_RAW32 = 4, PROJ_RAW16 = 5 };
+__host__ __device__ __forceinline__ bool proj_is_resid(int mode) {
+    return mode == PROJ_RESID32 || mode == PROJ_RESID16 || mode == PROJ_RAW32 || mode == PROJ_RAW16;
+}
 cudaError_t launch_project(const GeoDev &g, const float *vol, const float *y32, const __half *y16,
                            float *out, double *partial, int mode, cudaStream_t s, int *nblocks_out);
 size_t project_partials(const GeoDev &g);
@@ -122,6 +127,12 @@ enum BpMode { BP_PLAIN = 0, BP_STEP = 1 };
 cudaError_t launch_backproject(const GeoDev &g, const float *rs, const float *fin, float *out, float c,
                                int mode, cudaStream_t s);
 int project_threads(const GeoDev &g);
+
+// Eq. 2 adjoint: out = cscale * B' r (BP_PLAIN) or fin - cscale * B' r (BP_STEP), where
+// B' is B without its dV/(du dv) factor and r = P f - Y unscaled.
+cudaError_t launch_backproject_eq2(const GeoDev &g, const float *r, const float *fin, float *out, float cscale,
+                                   int mode, cudaStream_t s);
+double eq2_scale(const Level *L);  // dV / (du dv)
 int bp_default_vpl(const GeoDev &g);
 
 struct TvArgs {
@@ -170,6 +181,8 @@ struct SolveParams {
     int M;
     int clamp_mode;
     int tv_mode;
+    int adjoint_mode;  // 0 exact transpose, 1 Eq. 2
+    float c_eq2;       // (gamma / beta) dV / (du dv)
     bool fp16;
     double inv_nv, mu_over_nr;
 };
@@ -179,7 +192,7 @@ double gamma_of(const Level *L, double mu);
 cbct_status ensure_trace(cbct_geometry *G, size_t n);
 TvArgs tv_args(const Level *L, const SolveParams &P);
 cbct_status solve_params(const Level *L, double mu, double beta, double eps, int M, int clamp_mode, bool fp16,
-                         SolveParams *P, int tv_mode = 0);
+                         SolveParams *P, int tv_mode = 0, int adjoint_mode = 0);
 cbct_status get_trace(cbct_geometry *G, size_t n, double **out);
 
 }  // namespace cbct

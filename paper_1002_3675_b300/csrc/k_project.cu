@@ -43,6 +43,8 @@ cudaError_t launch_project(const GeoDev &g, const float *vol, const float *y32, 
         cudaFuncSetAttribute(k_project<PROJ_RESID32>, cudaFuncAttributeMaxDynamicSharedMemorySize, PROJ_SMEM);
         cudaFuncSetAttribute(k_project<PROJ_RESID16>, cudaFuncAttributeMaxDynamicSharedMemorySize, PROJ_SMEM);
         cudaFuncSetAttribute(k_project<PROJ_SCALED>, cudaFuncAttributeMaxDynamicSharedMemorySize, PROJ_SMEM);
+        cudaFuncSetAttribute(k_project<PROJ_RAW32>, cudaFuncAttributeMaxDynamicSharedMemorySize, PROJ_SMEM);
+        cudaFuncSetAttribute(k_project<PROJ_RAW16>, cudaFuncAttributeMaxDynamicSharedMemorySize, PROJ_SMEM);
         attr_set[dev] = true;
     }
     const dim3 grid = project_grid(g), block((unsigned)project_threads(g));
@@ -50,6 +52,8 @@ cudaError_t launch_project(const GeoDev &g, const float *vol, const float *y32, 
         case PROJ_PLAIN: k_project<PROJ_PLAIN><<<grid, block, PROJ_SMEM, s>>>(g, vol, y32, y16, out, partial); break;
         case PROJ_RESID32: k_project<PROJ_RESID32><<<grid, block, PROJ_SMEM, s>>>(g, vol, y32, y16, out, partial); break;
         case PROJ_RESID16: k_project<PROJ_RESID16><<<grid, block, PROJ_SMEM, s>>>(g, vol, y32, y16, out, partial); break;
+        case PROJ_RAW32: k_project<PROJ_RAW32><<<grid, block, PROJ_SMEM, s>>>(g, vol, y32, y16, out, partial); break;
+        case PROJ_RAW16: k_project<PROJ_RAW16><<<grid, block, PROJ_SMEM, s>>>(g, vol, y32, y16, out, partial); break;
         default: k_project<PROJ_SCALED><<<grid, block, PROJ_SMEM, s>>>(g, vol, y32, y16, out, partial); break;
     }
     return cudaGetLastError();

@@ -302,13 +302,13 @@ __device__ __forceinline__ void project_tile(const GeoDev &G, const int mode, co
         } else if (mode == PROJ_SCALED) {
             out[o] = __fmul_rn(p, secp);
         } else {
-            const float yv = (mode == PROJ_RESID32) ? __ldg(y32 + o) : __half2float(y16[o]);
+            const float yv = (mode == PROJ_RESID32 || mode == PROJ_RAW32) ? __ldg(y32 + o) : __half2float(y16[o]);
             const float rr = __fsub_rn(p, yv);
             r2 = __fmul_rn(rr, rr);
-            out[o] = __fmul_rn(rr, secp);
+            out[o] = mode >= PROJ_RAW32 ? rr : __fmul_rn(rr, secp);
         }
     }
-    if (mode == PROJ_RESID32 || mode == PROJ_RESID16) {
+    if (proj_is_resid(mode)) {
         // float32 within a warp (pairwise tree), float64 across warps and blocks
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) r2 += __shfl_down_sync(0xffffffffu, r2, off);
