@@ -57,6 +57,34 @@ CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.ac
 # 1 max + 1 min, length: 1 sub, accumulate: 1 fma); projector 4 (pick next crossing:
 # 1 min, length: 1 sub, accumulate: 1 fma, advance the crossing: 1 fma).
 OPS_PER_NNZ = {"backproject": 8.0, "project": 4.0}
+# Sources of each timed kernel; the DRAM traffic recorded in profiles/ counts only while
+# they are unchanged since the capture.
+KERNEL_SOURCES = {
+    "backproject": ("k_backproject", ["k_backproject.cu", "bp_tile.cuh"]),
+    "project": ("k_project", ["k_project.cu", "project_tile.cuh"]),
+    "tv": ("k_tv_sweep", ["k_tv.cu", "tv_tile.cuh"]),
+}
+
+
+def profile_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, or None when there is no
+    summary for this workload or the kernel's sources changed since it was taken."""
+    import hashlib
+    import re
+    name, files = KERNEL_SOURCES[kernel]
+    try:
+        text = open(os.path.join(ROOT, "profiles", f"{name}_{workload}.md")).read()
+        h = hashlib.sha256()
+        for f in files:
+            with open(os.path.join(ROOT, "paper_1002_3675_b300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+    except OSError:
+        return None
+    t = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
+    s = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
+    if not t or not s or s.group(1) != h.hexdigest()[:16]:
+        return None
+    return int(t.group(1))
 
 
 def load_nnz(workload):
@@ -275,13 +303,13 @@ def run_gpu(args, world, rank, local):
     if dom in ("project", "backproject"):
         ach = per_kernel[dom]["alu_tops"]
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tlane-op/s",
-                "frac": ach / alu_peak, "traffic": None,
+                "frac": ach / alu_peak, "traffic": profile_traffic(dom, args.workload),
                 "basis": f"{OPS_PER_NNZ[dom]:.0f} lane-ops per nonzero x exact nnz; peak = {sm_count} SMs x 128 "
                          f"FP32 lanes x {clock_mhz:.0f} MHz (median SM clock in the timed region)"}
     else:
         ach = per_kernel["tv"]["gbs"]
         roof = {"kernel": "tv", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None}
+                "frac": ach / peaks["hbm_gbs"], "traffic": profile_traffic("tv", args.workload)}
     roof["peak_source"] = peak_kind
 
     # ---- CPU baseline: the oracle on a bounded sample ---------------------------------
