@@ -227,7 +227,8 @@ def run_gpu(args, world, rank, local):
     stream = torch.cuda.current_stream()
 
     def step(kernel_times):
-        return cbct.cbct_reconstruct(G, Y, mu, iters, levels, f_out=f, kernel_times=kernel_times)
+        return cbct.cbct_reconstruct(G, Y, mu, iters, levels, f_out=f, kernel_times=kernel_times,
+                                     tv_mode=args.tv_mode, adjoint_mode=args.adjoint_mode)
 
     for _ in range(args.warmup):
         step(False)
@@ -285,7 +286,9 @@ def run_gpu(args, world, rank, local):
         "project": sum(n * (iters + K_pi) for n in nnz),
         "backproject": sum(n * (iters + K_pi) for n in nnz),
     }
-    dom = max(("project", "backproject", "tv"), key=lambda k: kms.get(k, 0.0))
+    # the Eq. 2 adjoint variant mixes two adjoints in one class: no nonzero-based rate
+    candidates = ("project", "backproject", "tv") if args.adjoint_mode == 0 else ("project", "tv")
+    dom = max(candidates, key=lambda k: kms.get(k, 0.0))
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     clock_mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") \
         or peaks.get("sm_max_mhz", 2032.0)
@@ -293,6 +296,10 @@ def run_gpu(args, world, rank, local):
     per_kernel = {}
     for k in ("project", "backproject"):
         t = kms[k] / 1e3
+        if k == "backproject" and args.adjoint_mode == 1:
+            per_kernel[k] = {"ms_per_step": kms[k] / args.steps, "launches_per_step": klaunch[k] / args.steps,
+                             "note": "Eq. 2 adjoint in the FBS iterations, exact transpose in the power iterations"}
+            continue
         per_kernel[k] = {"ms_per_step": kms[k] / args.steps, "launches_per_step": klaunch[k] / args.steps,
                          "gnnz_per_s": units[k] * args.steps / t / 1e9,
                          "alu_tops": units[k] * args.steps * OPS_PER_NNZ[k] / t / 1e12}
@@ -329,6 +336,8 @@ def run_gpu(args, world, rank, local):
         "data": "synthetic (seeded ellipsoid phantom, analytic line integrals, Poisson/log noise); "
                 "stands in for the paper's NCAT/CatPhan data",
         "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "inner_iters": 10,
+                   "variant": {"tv_mode": ["isotropic", "anisotropic"][args.tv_mode],
+                               "adjoint": ["exact transpose", "Eq. 2 interpolation"][args.adjoint_mode]},
                    "beta": "auto per level (30 power iterations, recomputed every step)",
                    "fbs_iterations_per_step": n_iter, "l2": "flushed between steps (256 MiB write, untimed)",
                    "parallelism": f"replicas x{world}"},
@@ -507,8 +516,11 @@ def main():
     ap.add_argument("--workload", default="medium", choices=sorted(WORKLOAD_TEXT))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="step", choices=["step", "batch", "serve"])
+    ap.add_argument("--tv-mode", type=int, default=0, choices=[0, 1], help="E1: 0 isotropic, 1 anisotropic")
+    ap.add_argument("--adjoint-mode", type=int, default=0, choices=[0, 1],
+                    help="step-1 adjoint: 0 exact transpose, 1 Eq. 2 interpolation")
     ap.add_argument("--requests", type=int, default=16)
-    ap.add_argument("--load", type=float, default=1.5, help="serve: arrival rate / one-at-a-time capacity")
+    ap.add_argument("--load", type=float, default=0.8, help="serve: arrival rate / one-at-a-time capacity")
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--budget-gb", type=int, default=64)
     args = ap.parse_args()

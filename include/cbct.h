@@ -232,6 +232,8 @@ typedef struct {
     int bp_threads;    /* adjoint block size: 64, 128 or 256                           */
     float proj_ms;     /* autotune: measured time of one projection with the choice    */
     float bp_ms;       /* autotune: measured time of one adjoint with the choice       */
+    int proj_smem;     /* projector shared memory per block in bytes (multiple of 16, at
+                          most 110 KB); sets how many z-levels one pass holds          */
 } cbct_tuning;
 /* Time the candidate launch shapes of level `level` with CUDA events on `stream`
  * (synchronises), keep the fastest in the geometry and report it in *out. */
@@ -242,10 +244,13 @@ cbct_status cbct_set_tuning(cbct_geometry *geom, int level, const cbct_tuning *t
 /* Continuous-batching server.  A worker thread owns a stream and max_slots slots;
  * a slot keeps one geometry (tables and workspaces) resident and serves one request
  * at a time, and later requests with the same scan geometry reuse it.  Requests are
- * admitted in arrival order whenever a slot is free and the device memory of the
+ * admitted in arrival order whenever a slot is free, the device memory of the
  * geometries in use stays within hbm_budget_bytes (idle geometries are released,
- * least recently used first).  Admitted requests join the running batch between
- * iterations, so requests that arrive while others run overlap on the device; each
+ * least recently used first) and the running requests do not already fill the GPU
+ * (each is rated by the share of the SMs its finest-level adjoint keeps busy; a new
+ * request joins while the shares sum to less than one).  Admitted requests join the
+ * running batch between iterations, so small requests that arrive while others run
+ * overlap on the device and large ones are served first come, first served; each
  * result is bitwise the one cbct_reconstruct gives for the same request.  The
  * server uses the device that is current when it is created. */
 typedef struct cbct_server cbct_server;

@@ -428,6 +428,7 @@ cbct_status Engine::build_tables() {
     std::vector<std::vector<long>> tvstart;
     long ptot = 0, dtot = 0, bptot[4] = {0, 0, 0, 0};
     proj_threads = 32;
+    proj_smem = 0;
     max_m = 0;
     copies.clear();
     tv_energy_jobs.clear();
@@ -437,6 +438,7 @@ cbct_status Engine::build_tables() {
         const GeoDev &g = L->gd;
         const bool power = j->phase == PH_POWER;
         proj_threads = std::max(proj_threads, project_threads(g));
+        proj_smem = std::max(proj_smem, proj_smem_of(g));
         ProjItem pi;
         pi.G = g;
         pi.vol = power ? L->A : L->f;
@@ -506,6 +508,8 @@ cbct_status Engine::build_tables() {
         pstart.push_back(ptot);
         ptot += (long)g.nu * g.na * ((g.nv + project_threads(g) - 1) / project_threads(g));
     }
+    // resident projector blocks per SM (registers: 64 per thread; shared memory)
+    proj_blocks = std::max(1, std::min(65536 / (64 * proj_threads), (227 * 1024) / (std::max(proj_smem, 1) + 1024)));
     // TV sweeps: for each m, the jobs with m < M (ping-pong as in the single path)
     htv.assign(max_m, {});
     tvstart.assign(max_m, {});
@@ -630,7 +634,7 @@ cbct_status Engine::launch_stages() {
             cudaFuncSetAttribute(k_project_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, PROJ_SMEM);
             attr_done[dev] = true;
         }
-        k_project_batch<<<(unsigned)grid_for(ptotal, 2), proj_threads, PROJ_SMEM, s>>>(d_proj, d_pstart,
+        k_project_batch<<<(unsigned)grid_for(ptotal, proj_blocks), proj_threads, proj_smem, s>>>(d_proj, d_pstart,
                                                                                         (int)hproj.size(), ptotal);
         ECK(cudaGetLastError(), "batched projection");
     }
@@ -814,24 +818,30 @@ extern "C" cbct_status cbct_autotune(cbct_geometry *G, int level, cbct_tuning *o
     ECK(cudaEventCreate(&e0), "event");
     ECK(cudaEventCreate(&e1), "event");
     const int reps = 3;
-    // projector block size
+    // projector block size and shared memory (band size)
     const int need = std::min(PROJ_MAX_THREADS, 32 * ((g.nv + 31) / 32));
-    int best_t = 0;
+    int best_t = 0, best_m = 0;
     float best_p = 1e30f;
     for (int T : {need, 256, 320, 384, 448, 512}) {
         if (T < need || T > PROJ_MAX_THREADS) continue;
-        g.proj_threads = T;
-        launch_project(g, L->A, nullptr, nullptr, L->rs, nullptr, PROJ_SCALED, s, nullptr);
-        cudaEventRecord(e0, s);
-        for (int q = 0; q < reps; ++q) launch_project(g, L->A, nullptr, nullptr, L->rs, nullptr, PROJ_SCALED, s, nullptr);
-        cudaEventRecord(e1, s);
-        const float ms = time_ms(s, e0, e1) / reps;
-        if (ms < best_p) {
-            best_p = ms;
-            best_t = T;
+        for (int kb : {0, 110, 74, 56, 40}) {
+            g.proj_threads = T;
+            g.proj_smem = kb * 1024;
+            if (kb && proj_smem_of(g) != kb * 1024) continue;   // too small for this geometry
+            launch_project(g, L->A, nullptr, nullptr, L->rs, nullptr, PROJ_SCALED, s, nullptr);
+            cudaEventRecord(e0, s);
+            for (int q = 0; q < reps; ++q) launch_project(g, L->A, nullptr, nullptr, L->rs, nullptr, PROJ_SCALED, s, nullptr);
+            cudaEventRecord(e1, s);
+            const float ms = time_ms(s, e0, e1) / reps;
+            if (ms < best_p) {
+                best_p = ms;
+                best_t = T;
+                best_m = kb * 1024;
+            }
         }
     }
     g.proj_threads = best_t;
+    g.proj_smem = best_m;
     // adjoint voxels per lane and block size
     int best_v = 0, best_b = 0;
     float best_q = 1e30f;
@@ -855,9 +865,11 @@ extern "C" cbct_status cbct_autotune(cbct_geometry *G, int level, cbct_tuning *o
     cudaEventDestroy(e1);
     ECK(cudaGetLastError(), "autotune");
     L->gd.proj_threads = best_t;
+    L->gd.proj_smem = best_m;
     L->gd.bp_vpl = best_v;
     L->gd.bp_threads = best_b;
     out->proj_threads = best_t;
+    out->proj_smem = best_m;
     out->bp_vpl = best_v;
     out->bp_threads = best_b;
     out->proj_ms = best_p;
@@ -879,7 +891,16 @@ extern "C" cbct_status cbct_set_tuning(cbct_geometry *G, int level, const cbct_t
         set_error("tuning values out of range");
         return CBCT_ERR_INVALID_ARG;
     }
+    if (t->proj_smem) {
+        GeoDev g = L->gd;
+        g.proj_smem = t->proj_smem;
+        if (proj_smem_of(g) != t->proj_smem) {
+            set_error("proj_smem must be a multiple of 16 between the geometry's minimum and %d", PROJ_SMEM);
+            return CBCT_ERR_INVALID_ARG;
+        }
+    }
     L->gd.proj_threads = t->proj_threads;
+    L->gd.proj_smem = t->proj_smem;
     L->gd.bp_vpl = t->bp_vpl;
     L->gd.bp_threads = t->bp_threads;
     return CBCT_OK;

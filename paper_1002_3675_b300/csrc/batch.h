@@ -78,7 +78,7 @@ class Engine {
     std::vector<CopyOp> copies;
     std::vector<Job *> tv_energy_jobs;
     long ptotal = 0, dtotal = 0, bptotal[4] = {0, 0, 0, 0}, eqtotal = 0;
-    int proj_threads = 32, max_m = 0;
+    int proj_threads = 32, proj_smem = 0, proj_blocks = 2, max_m = 0;
     void *dblob = nullptr;
     size_t dblob_len = 0;
     ProjItem *d_proj = nullptr;

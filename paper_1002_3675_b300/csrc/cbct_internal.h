@@ -46,6 +46,7 @@ struct GeoDev {
     const float2 *view;          // [na]      cos, sin
     // launch shapes (0 = default); none of them changes any result bit
     int proj_threads;            // projector block size (>= 32 ceil(nv/32) up to 512, multiple of 32)
+    int proj_smem;               // projector dynamic shared memory, bytes (0 = default; see proj_smem_of)
     int bp_vpl;                  // adjoint voxels per lane (1..4)
     int bp_threads;              // adjoint block size (64, 128 or 256)
 };

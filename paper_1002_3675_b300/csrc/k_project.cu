@@ -12,11 +12,7 @@ k_project(GeoDev G, const float *__restrict__ vol, const float *__restrict__ y32
     project_tile(G, MODE, vol, y32, y16, out, partial, blockIdx.x, blockIdx.y, blockIdx.z, smem);
 }
 
-int project_threads(const GeoDev &g) {
-    const int need = min(PROJ_MAX_THREADS, 32 * ((g.nv + 31) / 32));
-    if (g.proj_threads >= need && g.proj_threads <= PROJ_MAX_THREADS && g.proj_threads % 32 == 0) return g.proj_threads;
-    return max(need, 256);
-}
+int project_threads(const GeoDev &g) { return proj_threads_of(g); }
 
 static dim3 project_grid(const GeoDev &g) {
     const int T = project_threads(g);
@@ -32,8 +28,8 @@ cudaError_t launch_project(const GeoDev &g, const float *vol, const float *y32, 
                            float *out, double *partial, int mode, cudaStream_t s, int *nblocks_out) {
     if (nblocks_out) *nblocks_out = (int)project_partials(g);
     // the segment list and one level of running sums must fit
-    if (8 * (g.nx + g.ny + 1) + 4 * (g.nx + g.ny + 1 + (g.nx + g.ny + 1 + CHUNK - 1) / CHUNK) > PROJ_SMEM)
-        return cudaErrorInvalidValue;
+    const int smem = proj_smem_of(g);
+    if (smem > PROJ_SMEM) return cudaErrorInvalidValue;
     static bool attr_set[64] = {};   // per device: the attribute belongs to the device's context
     int dev = 0;
     cudaGetDevice(&dev);
@@ -49,12 +45,12 @@ cudaError_t launch_project(const GeoDev &g, const float *vol, const float *y32, 
     }
     const dim3 grid = project_grid(g), block((unsigned)project_threads(g));
     switch (mode) {
-        case PROJ_PLAIN: k_project<PROJ_PLAIN><<<grid, block, PROJ_SMEM, s>>>(g, vol, y32, y16, out, partial); break;
-        case PROJ_RESID32: k_project<PROJ_RESID32><<<grid, block, PROJ_SMEM, s>>>(g, vol, y32, y16, out, partial); break;
-        case PROJ_RESID16: k_project<PROJ_RESID16><<<grid, block, PROJ_SMEM, s>>>(g, vol, y32, y16, out, partial); break;
-        case PROJ_RAW32: k_project<PROJ_RAW32><<<grid, block, PROJ_SMEM, s>>>(g, vol, y32, y16, out, partial); break;
-        case PROJ_RAW16: k_project<PROJ_RAW16><<<grid, block, PROJ_SMEM, s>>>(g, vol, y32, y16, out, partial); break;
-        default: k_project<PROJ_SCALED><<<grid, block, PROJ_SMEM, s>>>(g, vol, y32, y16, out, partial); break;
+        case PROJ_PLAIN: k_project<PROJ_PLAIN><<<grid, block, smem, s>>>(g, vol, y32, y16, out, partial); break;
+        case PROJ_RESID32: k_project<PROJ_RESID32><<<grid, block, smem, s>>>(g, vol, y32, y16, out, partial); break;
+        case PROJ_RESID16: k_project<PROJ_RESID16><<<grid, block, smem, s>>>(g, vol, y32, y16, out, partial); break;
+        case PROJ_RAW32: k_project<PROJ_RAW32><<<grid, block, smem, s>>>(g, vol, y32, y16, out, partial); break;
+        case PROJ_RAW16: k_project<PROJ_RAW16><<<grid, block, smem, s>>>(g, vol, y32, y16, out, partial); break;
+        default: k_project<PROJ_SCALED><<<grid, block, smem, s>>>(g, vol, y32, y16, out, partial); break;
     }
     return cudaGetLastError();
 }

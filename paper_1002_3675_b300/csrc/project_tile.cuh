@@ -125,11 +125,33 @@ using namespace proj_detail;
 
 // Shared memory per block: the segment list (t, offset) for nx + ny + 1 slots, the
 // chunk offsets, and in the rest the running slice integrals C of a band of z-levels.
-constexpr int PROJ_SMEM = 110 * 1024;
+// The size is a launch shape: it sets how many levels a band holds, and no result bit
+// depends on it (every ray adds its levels in ascending order whatever the bands).
+constexpr int PROJ_SMEM = 110 * 1024;   // largest size used
+constexpr int PROJ_SMEM_MIN = 16 * 1024;
 constexpr int PROJ_MAX_THREADS = 512;
 constexpr int CHUNK_LOG = 6;            // prefix chunks of 64 segments
 constexpr int CHUNK = 1 << CHUNK_LOG;
 constexpr int PROJ_BATCH = 8;           // voxel loads in flight per thread
+
+// Projector block size (rows per tile): G.proj_threads if valid, else the default.
+__host__ __device__ __forceinline__ int proj_threads_of(const GeoDev &g) {
+    const int need = min(PROJ_MAX_THREADS, 32 * ((g.nv + 31) / 32));
+    if (g.proj_threads >= need && g.proj_threads <= PROJ_MAX_THREADS && g.proj_threads % 32 == 0) return g.proj_threads;
+    return max(need, 256);
+}
+
+// Bytes of shared memory the projector tile may use: G.proj_smem if valid, else as much
+// as lets as many blocks share an SM as the registers allow (64 per thread, 64 K per
+// SM, 227 KB of shared memory with 1 KB reserved per block), at most PROJ_SMEM.
+__host__ __device__ __forceinline__ int proj_smem_of(const GeoDev &g) {
+    const int slots = g.nx + g.ny + 1;
+    const int least = (4 * (3 * slots + (slots + CHUNK - 1) / CHUNK) + 15) & ~15;  // one level per band
+    if (g.proj_smem >= least && g.proj_smem <= PROJ_SMEM && g.proj_smem % 16 == 0) return g.proj_smem;
+    const int blocks = max(1, 65536 / (64 * proj_threads_of(g)));
+    const int fit = ((227 * 1024) / blocks - 1024) & ~1023;
+    return max(least, min(PROJ_SMEM, fit));
+}
 
 // Level-kk running integral at t, seg_t[s-1] < t <= seg_t[s].  C holds chunk-local
 // running sums; coff[chunk][kk] adds the totals of the preceding chunks.  C is
@@ -217,7 +239,7 @@ __device__ __forceinline__ void project_tile(const GeoDev &G, const int mode, co
     __syncthreads();
 
     // ---- 2./3. bands of z-levels: running slice integrals, then the rays ---------------
-    const int c_cap = PROJ_SMEM / 4 - 2 * slots;
+    const int c_cap = proj_smem_of(G) / 4 - 2 * slots;
     const int kband = S > 0 ? max(1, min(G.nz, c_cap / (S + max_chunks))) : G.nz;
     for (int kb = 0; kb < G.nz && S > 0; kb += kband) {
         const int nk = min(kband, G.nz - kb);
@@ -260,15 +282,15 @@ __device__ __forceinline__ void project_tile(const GeoDev &G, const int mode, co
             }
         }
         __syncthreads();
-        // 3. each ray adds C_k(t_exit) - C_k(t_entry) over its levels in this band,
-        //    in travel order so that a shared boundary is located once
+        // 3. each ray adds C_k(t_exit) - C_k(t_entry) over its levels in this band, in
+        //    ascending k (so the sum does not depend on the band size); the plane shared
+        //    with the next level is located once
         const int k0 = max(klo, kb), k1 = min(khi, kb + nk - 1);
         if (k0 <= k1) {
-            const int step = cotp >= 0.f ? 1 : -1;
-            const int kstart = step > 0 ? k0 : k1, kend = step > 0 ? k1 : k0;
+            const bool up = cotp >= 0.f;  // rising ray: level k + 1 starts where k ends
             float last_t = -INFINITY;
             int last_s = 0;
-            for (int k = kstart;; k += step) {
+            for (int k = k0; k <= k1; ++k) {
                 float ta = c.tin, tb = c.tout;
                 if (cotp != 0.f) {
                     const float z1 = t_cross(plane_at(k, G.hz, G.z0), zO, cotp);
@@ -278,14 +300,13 @@ __device__ __forceinline__ void project_tile(const GeoDev &G, const int mode, co
                 }
                 if (tb > ta) {
                     const int sa = ta == last_t ? last_s : seg_find(seg_t, S, c.tin, scale, ta);
-                    const int sb = seg_find(seg_t, S, c.tin, scale, tb);
+                    const int sb = tb == last_t ? last_s : seg_find(seg_t, S, c.tin, scale, tb);
                     const int kq = k - kb;
                     acc += eval_c(seg_t, C, coff, nk, kq, c.tin, tb, sb) -
                            eval_c(seg_t, C, coff, nk, kq, c.tin, ta, sa);
-                    last_t = tb;
-                    last_s = sb;
+                    last_t = up ? tb : ta;
+                    last_s = up ? sb : sa;
                 }
-                if (k == kend) break;
             }
         }
         __syncthreads();

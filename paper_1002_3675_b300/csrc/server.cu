@@ -4,11 +4,15 @@
 // holds one geometry (ray tables and device workspaces) and serves one request at a
 // time; a later request with the same scan geometry reuses it, keeping its tables,
 // workspaces and cached step size resident.  Requests are admitted in arrival order
-// whenever a slot is free and the device memory of the geometries in use stays
-// within the budget (idle geometries are released, least recently used first, to
-// make room).  Admitted requests join the engine between ticks, so work of requests
-// that arrived at different times overlaps on the device; each request's arithmetic
-// is exactly that of its own cbct_reconstruct call.
+// whenever a slot is free, the device memory of the geometries in use stays within
+// the budget (idle geometries are released, least recently used first, to make
+// room), and the requests already running do not fill the GPU: each request's
+// per-tick work is rated against what keeps every SM busy, and a new request joins
+// only while the running ones sum to less than one GPU.  Small requests therefore
+// run side by side, large ones one after another (first come, first served).
+// Admitted requests join the engine between ticks, so work of requests that arrived
+// at different times overlaps on the device; each request's arithmetic is exactly
+// that of its own cbct_reconstruct call.
 #include <math.h>
 #include <string.h>
 
@@ -50,6 +54,7 @@ struct Pending {
     Clock::time_point t_submit;
     Clock::time_point t_admit;
     int slot = -1;
+    double fill = 0.0;  // share of the GPU one tick of this request keeps busy
     Job job;
     cbct_result result{};
     bool done = false;
@@ -74,12 +79,20 @@ size_t geometry_bytes(const cbct_geometry_desc &d, int n_angles, int levels, boo
     return total + (1 << 20);
 }
 
+// Share of the GPU the finest level's adjoint of a request keeps busy: its warp tiles
+// (z-columns in chunks of 64 voxels) against two waves of 32 resident warps per SM.
+double gpu_fill(const cbct_geometry_desc &d, int sm_count) {
+    const double tiles = (double)d.nx * d.ny * ((d.nz + 63) / 64);
+    return std::min(1.0, tiles / (2.0 * 32.0 * std::max(sm_count, 1)));
+}
+
 }  // namespace
 
 struct cbct_server {
     size_t budget = 0;
     int max_slots = 0;
     int device = 0;
+    int sm_count = 148;
     cudaStream_t stream = nullptr;
     bool use_graphs = false;
     std::vector<Slot> slots;
@@ -185,9 +198,12 @@ void cbct_server::run() {
     Engine E(stream, use_graphs);
     std::unique_lock<std::mutex> lk(mu);
     for (;;) {
-        // admit in arrival order while slots and memory allow
+        // admit in arrival order while slots and memory allow and the GPU is not full
         while (!queue.empty() && !stop) {
             std::shared_ptr<Pending> p = queue.front();
+            double load = 0.0;
+            for (auto &q : running) load += q->fill;
+            if (!running.empty() && load >= 1.0) break;
             if (!try_admit(p, lk)) break;
             queue.pop_front();
             if (p->done) {  // set-up failed
@@ -195,6 +211,7 @@ void cbct_server::run() {
                 continue;
             }
             p->t_admit = Clock::now();
+            p->fill = gpu_fill(p->req.desc, sm_count);
             Job &j = p->job;
             j.G = slots[p->slot].G;
             j.Y = p->req.Y_dev;
@@ -271,6 +288,9 @@ extern "C" cbct_status cbct_server_create(size_t hbm_budget_bytes, int max_slots
         set_error("no CUDA device available for the server");
         return CBCT_ERR_CUDA;
     }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S->device) == cudaSuccess && sms > 0)
+        S->sm_count = sms;
     S->worker = std::thread([S] { S->run(); });
     *out = S;
     return CBCT_OK;
