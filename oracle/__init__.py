@@ -72,7 +72,12 @@ def _load():
             "or_power_iteration": (C.c_double, [G, C.c_int]),
             "or_auto_beta": (C.c_double, [G, C.c_double, C.c_int]),
             "or_fbs": (None, [G, _D, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
-                              C.c_double, C.c_int, _D, _D]),
+                              C.c_double, C.c_int, _D, _D, _D]),
+            "or_restrict_vol": (None, [C.c_int, C.c_int, C.c_int, _D, _D]),
+            "or_prolong_vol_adjoint": (None, [C.c_int] * 6 + [_D, _D]),
+            "or_energy_grad": (None, [G, _D, _D, C.c_double, C.c_double, _D]),
+            "or_vcycle": (None, [G, _D, C.c_double, C.c_int, C.c_int, _D, C.c_double, C.c_int, C.c_int, C.c_int,
+                                 C.c_int, C.c_int, _D, _D, C.POINTER(C.c_int)]),
             "or_restrict_sino": (None, [C.c_int, C.c_int, C.c_int, _D, _D]),
             "or_prolong_vol": (None, [C.c_int, C.c_int, C.c_int, _D, C.c_int, C.c_int, C.c_int, _D]),
             "or_level_geom": (None, [G, C.c_int, G]),
@@ -253,12 +258,16 @@ def auto_beta(geom, mu, K=30):
     return _load().or_auto_beta(C.byref(h.s), mu, K)
 
 
-def fbs(geom, Y, mu, beta, eps, M, iters, f0=None, clamp_mode=0, tv_weight=1.0, tv_mode=0, adjoint_mode=0):
+def fbs(geom, Y, mu, beta, eps, M, iters, f0=None, clamp_mode=0, tv_weight=1.0, tv_mode=0, adjoint_mode=0,
+        v=None):
+    """Algorithm A1; v (optional volume) adds the linear term -<v, f> to the energy."""
     Y = _f64(Y)
     f = _f64(f0).copy() if f0 is not None else np.zeros(vol_shape(geom))
     trace = np.empty((iters, 3))
+    vv = _f64(v) if v is not None else None
     h = _g(geom, tv_mode, adjoint_mode)
-    _load().or_fbs(C.byref(h.s), _ptr(Y), mu, beta, eps, M, clamp_mode, tv_weight, iters, _ptr(f), _ptr(trace))
+    _load().or_fbs(C.byref(h.s), _ptr(Y), mu, beta, eps, M, clamp_mode, tv_weight, iters, _ptr(f), _ptr(trace),
+                   _ptr(vv))
     return f, trace
 
 
@@ -299,3 +308,43 @@ def reconstruct(geom, Y, mu, iters, levels, betas=None, eps=0.0, M=10, clamp_mod
     _load().or_reconstruct(C.byref(h.s), _ptr(Y), mu, iters, levels, _ptr(b), eps, M, clamp_mode,
                            K_pi, _ptr(f), _ptr(trace))
     return f, trace
+
+
+# --- V-cycle (full-approximation multigrid reading of the cited method) --------------
+
+def restrict_vol(f):
+    f = _f64(f)
+    nz, ny, nx = f.shape
+    out = np.empty(((nz + 1) // 2, (ny + 1) // 2, (nx + 1) // 2))
+    _load().or_restrict_vol(nx, ny, nz, _ptr(f), _ptr(out))
+    return out
+
+
+def prolong_vol_adjoint(x, coarse_shape):
+    x = _f64(x)
+    nz, ny, nx = x.shape
+    nzc, nyc, nxc = coarse_shape
+    out = np.empty(coarse_shape)
+    _load().or_prolong_vol_adjoint(nxc, nyc, nzc, nx, ny, nz, _ptr(x), _ptr(out))
+    return out
+
+
+def energy_grad(geom, Y, f, mu, eps):
+    Y, f = _f64(Y), _f64(f)
+    out = np.empty_like(f)
+    h = _g(geom)
+    _load().or_energy_grad(C.byref(h.s), _ptr(Y), _ptr(f), mu, eps, _ptr(out))
+    return out
+
+
+def vcycle(geom, Y, mu, cycles, levels, betas=None, eps=0.0, M=10, pre=2, post=2, coarse=10, K_pi=30):
+    """Returns (f, trace [cycles][3], accepted [levels])."""
+    Y = _f64(Y)
+    f = np.empty(vol_shape(geom))
+    trace = np.empty((cycles, 3))
+    acc = (C.c_int * levels)()
+    b = _f64(betas) if betas is not None else None
+    h = _g(geom)
+    _load().or_vcycle(C.byref(h.s), _ptr(Y), mu, cycles, levels, _ptr(b), eps, M, pre, post, coarse, K_pi,
+                      _ptr(f), _ptr(trace), acc)
+    return f, trace, np.array(acc[:])

@@ -610,9 +610,11 @@ double or_auto_beta(const or_geom *g, double mu, int K)
  * Algorithm A1 for `iters` iterations from the volume in f (updated in place).
  * trace (optional, 3 * iters): {E, E1, E2-term} of the iterate entering each iteration.
  * Step 1 uses the exact transpose, or B of Eq. 2 when g->adjoint_mode is 1.
+ * lin (optional, one value per voxel) adds the linear term -<lin, f> to the energy
+ * (the coarse-level model of a multigrid cycle); the trace reports E without it.
  */
 void or_fbs(const or_geom *g, const double *Y, double mu, double beta, double eps, int M,
-            int clamp_mode, double tv_weight, int iters, double *f, double *trace)
+            int clamp_mode, double tv_weight, int iters, double *f, double *trace, const double *lin)
 {
     const long nvox = (long)g->nx * g->ny * g->nz;
     const long nr = (long)g->na * g->nv * g->nu;
@@ -642,6 +644,8 @@ void or_fbs(const or_geom *g, const double *Y, double mu, double beta, double ep
             or_backproject(g, r, bp);
         double c = gamma / beta;
         for (long j = 0; j < nvox; ++j) gv[j] = f[j] - c * bp[j];
+        if (lin) /* linear term -<lin, f> of a coarse model, times Nv / beta */
+            for (long j = 0; j < nvox; ++j) gv[j] += (double)nvox / beta * lin[j];
         /* steps 2 and 3 */
         or_prox(&v, gv, f, beta, eps, M, clamp_mode, tv_weight, NULL);
     }
@@ -768,13 +772,203 @@ void or_reconstruct(const or_geom *g, const double *Y, double mu, int iters, int
         double beta = betas ? betas[l] : or_auto_beta(&lg[l], mu, K_pi);
         double e = eps > 0 ? eps : or_default_eps(&lg[l]);
         double *tr = trace ? trace + 3 * iters * (levels - 1 - l) : NULL;
-        or_fbs(&lg[l], Ys[l], mu, beta, e, M, clamp_mode, 1.0, iters, f, tr);
+        or_fbs(&lg[l], Ys[l], mu, beta, e, M, clamp_mode, 1.0, iters, f, tr, NULL);
     }
     memcpy(f_out, f, sizeof(double) * (size_t)g->nx * g->ny * g->nz);
     free(f);
     for (int l = 1; l < levels; ++l) free(Ys[l]);
     free(Ys);
     free(lg);
+}
+
+/* ------------------------------------------------------------------------------ */
+/* V-cycle (a full-approximation reading of the cited multigrid method)            */
+/* ------------------------------------------------------------------------------ */
+
+/* Mean over the existing fine voxels of each 2x2x2 block: [nz][ny][nx] -> ceil halves. */
+void or_restrict_vol(int nx, int ny, int nz, const double *f, double *fc)
+{
+    int nxc = (nx + 1) / 2, nyc = (ny + 1) / 2, nzc = (nz + 1) / 2;
+    for (int k = 0; k < nzc; ++k)
+        for (int j = 0; j < nyc; ++j)
+            for (int i = 0; i < nxc; ++i) {
+                double s = 0.0;
+                int c = 0;
+                for (int dk = 0; dk < 2; ++dk)
+                    for (int dj = 0; dj < 2; ++dj)
+                        for (int di = 0; di < 2; ++di) {
+                            int ii = 2 * i + di, jj = 2 * j + dj, kk = 2 * k + dk;
+                            if (ii < nx && jj < ny && kk < nz) {
+                                s += f[((long)kk * ny + jj) * nx + ii];
+                                ++c;
+                            }
+                        }
+                fc[((long)k * nyc + j) * nxc + i] = s / c;
+            }
+}
+
+/* Transpose of or_prolong_vol: fc[c] = sum over fine voxels of (weight of coarse voxel c
+ * in that fine voxel) * x[fine]; accumulated serially in fine raster order. */
+void or_prolong_vol_adjoint(int nxc, int nyc, int nzc, int nx, int ny, int nz, const double *x, double *fc)
+{
+    memset(fc, 0, sizeof(double) * (size_t)nxc * nyc * nzc);
+    for (int k = 0; k < nz; ++k) {
+        int k0, k1;
+        double wk;
+        prolong_weights(k, nz, nzc, &k0, &k1, &wk);
+        for (int j = 0; j < ny; ++j) {
+            int j0, j1;
+            double wj;
+            prolong_weights(j, ny, nyc, &j0, &j1, &wj);
+            for (int i = 0; i < nx; ++i) {
+                int i0, i1;
+                double wi;
+                prolong_weights(i, nx, nxc, &i0, &i1, &wi);
+                double xv = x[((long)k * ny + j) * nx + i];
+                int ii[2] = {i0, i1}, jj[2] = {j0, j1}, kk[2] = {k0, k1};
+                double w_i[2] = {1 - wi, wi}, w_j[2] = {1 - wj, wj}, w_k[2] = {1 - wk, wk};
+                for (int c = 0; c < 2; ++c)
+                    for (int b = 0; b < 2; ++b)
+                        for (int a = 0; a < 2; ++a)
+                            fc[((long)kk[c] * nyc + jj[b]) * nxc + ii[a]] += w_k[c] * w_j[b] * w_i[a] * xv;
+            }
+        }
+    }
+}
+
+/* Gradient of the grid energy of Eq. 1: (grad TV_eps(f) + gamma P^T (P f - Y)) / Nv. */
+void or_energy_grad(const or_geom *g, const double *Y, const double *f, double mu, double eps, double *grad)
+{
+    const long nvox = (long)g->nx * g->ny * g->nz;
+    const long nr = (long)g->na * g->nv * g->nu;
+    or_vol v = vol_of(g);
+    double *r = (double *)malloc(sizeof(double) * nr);
+    double *bp = (double *)malloc(sizeof(double) * nvox);
+    or_project(g, f, r);
+    for (long t = 0; t < nr; ++t) r[t] -= Y[t];
+    or_backproject(g, r, bp);
+    or_tv_grad(&v, f, eps, grad);
+    double gam = or_gamma(g, mu);
+    for (long j = 0; j < nvox; ++j) grad[j] = (grad[j] + gam * bp[j]) / (double)nvox;
+    free(r);
+    free(bp);
+}
+
+/* E(f) - <v, f> (v may be null). */
+static double model_energy(const or_geom *g, const double *Y, const double *f, double mu, double eps,
+                           const double *v)
+{
+    double e[3];
+    or_energy(g, Y, f, mu, eps, e, NULL);
+    double lin = 0.0;
+    if (v)
+        for (long j = 0; j < (long)g->nx * g->ny * g->nz; ++j) lin += v[j] * f[j];
+    return e[0] - lin;
+}
+
+typedef struct {
+    const or_geom *lg;
+    double **Ys;
+    const double *betas, *epss;
+    double mu;
+    int levels, M, pre, post, coarse;
+    int *accepted; /* per level: coarse corrections taken */
+} vc_ctx;
+
+/*
+ * One V-cycle on level l for the model E_l(f) - <v, f> (v null on the finest level):
+ * `pre` iterations of Algorithm A1; then the coarse model
+ *   E_{l+1}(x) - <v_c, x>,  v_c = grad E_{l+1}(R f) - Q^T (grad E_l(f) - v),
+ * with R the 2x2x2 mean and Q^T the transpose of the trilinear prolongation Q, whose
+ * gradient at R f equals Q^T of the fine model's gradient at f (first-order
+ * coherence); it is reduced by a V-cycle on level l+1 (`coarse` iterations of A1 on
+ * the coarsest), and the correction f + Q(x - R f), clamped at 0, is kept when it
+ * lowers the fine model; then `post` iterations of A1.
+ */
+static void vcycle(const vc_ctx *C, int l, double *f, const double *v)
+{
+    const or_geom *g = &C->lg[l];
+    if (l == C->levels - 1) {
+        or_fbs(g, C->Ys[l], C->mu, C->betas[l], C->epss[l], C->M, 0, 1.0, C->coarse, f, NULL, v);
+        return;
+    }
+    or_fbs(g, C->Ys[l], C->mu, C->betas[l], C->epss[l], C->M, 0, 1.0, C->pre, f, NULL, v);
+    const or_geom *gc = &C->lg[l + 1];
+    const long n = (long)g->nx * g->ny * g->nz, nc = (long)gc->nx * gc->ny * gc->nz;
+    double *gr = (double *)malloc(sizeof(double) * n);
+    double *x0 = (double *)malloc(sizeof(double) * nc);
+    double *x = (double *)malloc(sizeof(double) * nc);
+    double *vc = (double *)malloc(sizeof(double) * nc);
+    double *gc_grad = (double *)malloc(sizeof(double) * nc);
+    double *corr = (double *)malloc(sizeof(double) * n);
+    double *ftry = (double *)malloc(sizeof(double) * n);
+    or_energy_grad(g, C->Ys[l], f, C->mu, C->epss[l], gr);
+    if (v)
+        for (long j = 0; j < n; ++j) gr[j] -= v[j];
+    or_restrict_vol(g->nx, g->ny, g->nz, f, x0);
+    or_prolong_vol_adjoint(gc->nx, gc->ny, gc->nz, g->nx, g->ny, g->nz, gr, vc);
+    or_energy_grad(gc, C->Ys[l + 1], x0, C->mu, C->epss[l + 1], gc_grad);
+    for (long j = 0; j < nc; ++j) {
+        vc[j] = gc_grad[j] - vc[j];
+        x[j] = x0[j];
+    }
+    vcycle(C, l + 1, x, vc);
+    for (long j = 0; j < nc; ++j) x[j] -= x0[j];
+    or_prolong_vol(gc->nx, gc->ny, gc->nz, x, g->nx, g->ny, g->nz, corr);
+    for (long j = 0; j < n; ++j) {
+        double t = f[j] + corr[j];
+        ftry[j] = t > 0.0 ? t : 0.0;
+    }
+    if (model_energy(g, C->Ys[l], ftry, C->mu, C->epss[l], v) < model_energy(g, C->Ys[l], f, C->mu, C->epss[l], v)) {
+        memcpy(f, ftry, sizeof(double) * n);
+        if (C->accepted) C->accepted[l] += 1;
+    }
+    or_fbs(g, C->Ys[l], C->mu, C->betas[l], C->epss[l], C->M, 0, 1.0, C->post, f, NULL, v);
+    free(gr);
+    free(x0);
+    free(x);
+    free(vc);
+    free(gc_grad);
+    free(corr);
+    free(ftry);
+}
+
+/*
+ * `cycles` V-cycles over `levels` levels from f = 0 on the finest level.  betas
+ * (optional, per level) as in or_reconstruct; eps <= 0 takes the per-level default.
+ * trace (optional, 3 * cycles): {E, E1, E2-term} of the finest iterate after each
+ * cycle; accepted (optional, levels values) counts the coarse corrections taken.
+ */
+void or_vcycle(const or_geom *g, const double *Y, double mu, int cycles, int levels, const double *betas,
+               double eps, int M, int pre, int post, int coarse, int K_pi, double *f_out, double *trace,
+               int *accepted)
+{
+    or_geom *lg = (or_geom *)malloc(sizeof(or_geom) * levels);
+    double **Ys = (double **)malloc(sizeof(double *) * levels);
+    double *bt = (double *)malloc(sizeof(double) * levels);
+    double *ep = (double *)malloc(sizeof(double) * levels);
+    for (int l = 0; l < levels; ++l) {
+        or_level_geom(g, l, &lg[l]);
+        bt[l] = betas ? betas[l] : or_auto_beta(&lg[l], mu, K_pi);
+        ep[l] = eps > 0 ? eps : or_default_eps(&lg[l]);
+    }
+    Ys[0] = (double *)Y;
+    for (int l = 1; l < levels; ++l) {
+        Ys[l] = (double *)malloc(sizeof(double) * (size_t)g->na * lg[l].nv * lg[l].nu);
+        or_restrict_sino(g->na, lg[l - 1].nv, lg[l - 1].nu, Ys[l - 1], Ys[l]);
+    }
+    if (accepted) memset(accepted, 0, sizeof(int) * levels);
+    vc_ctx C = {lg, Ys, bt, ep, mu, levels, M, pre, post, coarse, accepted};
+    memset(f_out, 0, sizeof(double) * (size_t)g->nx * g->ny * g->nz);
+    for (int c = 0; c < cycles; ++c) {
+        vcycle(&C, 0, f_out, NULL);
+        if (trace) or_energy(&lg[0], Y, f_out, mu, ep[0], trace + 3 * c, NULL);
+    }
+    for (int l = 1; l < levels; ++l) free(Ys[l]);
+    free(Ys);
+    free(lg);
+    free(bt);
+    free(ep);
 }
 
 int or_num_threads(void)

@@ -501,6 +501,10 @@ def test_fbs_converges_to_lbfgsb_minimiser():
     f, _ = oracle.fbs(g, Y, mu, beta, eps, 50, 1500)
     fo = res.x.reshape(8, 8, 8)
     assert np.linalg.norm(f - fo) / np.linalg.norm(fo) < 1e-5
+    # the V-cycle (8^3 over 4^3) has the same minimiser
+    fv, tr, acc = oracle.vcycle(g, Y, mu, 400, 2, eps=eps, M=50, pre=2, post=2, coarse=5)
+    assert np.linalg.norm(fv - fo) / np.linalg.norm(fo) < 1e-5
+    assert acc[0] >= 1
     assert obj(f.ravel())[0] <= res.fun * (1 + 1e-9)
 
 
@@ -577,3 +581,106 @@ def test_poisson_noise_statistics():
     lam = I0 * math.exp(-1.5)
     assert abs(N.mean() - lam) < 3 * math.sqrt(lam / N.size)
     assert abs(N.var() / lam - 1.0) < 3 * math.sqrt(2.0 / N.size)
+
+
+# ---------------------------------------------------------------------------------
+# V-cycle: a full-approximation (coarse model with a first-order correction) reading
+# of the multigrid method the paper cites
+# ---------------------------------------------------------------------------------
+
+def test_prolongation_adjoint_is_the_transpose():
+    rng = np.random.default_rng(70)
+    for fine, coarse in [((7, 9, 10), (4, 5, 5)), ((8, 8, 8), (4, 4, 4))]:
+        x = rng.normal(size=coarse)
+        y = rng.normal(size=fine)
+        lhs = float(np.sum(oracle.prolong_vol(x, fine) * y))
+        rhs = float(np.sum(x * oracle.prolong_vol_adjoint(y, coarse)))
+        assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(x) * np.linalg.norm(y) * 8
+
+
+def test_volume_restriction_is_the_block_mean():
+    rng = np.random.default_rng(71)
+    f = rng.normal(size=(6, 4, 8))
+    fc = oracle.restrict_vol(f)
+    assert np.allclose(fc, f.reshape(3, 2, 2, 2, 4, 2).mean(axis=(1, 3, 5)), rtol=0, atol=1e-14)
+    g = rng.normal(size=(5, 3, 7))        # odd sizes: the edge blocks average what exists
+    gc = oracle.restrict_vol(g)
+    assert gc.shape == (3, 2, 4)
+    assert abs(gc[2, 1, 3] - g[4, 2, 6]) <= 1e-15
+    assert abs(gc[0, 1, 3] - g[0:2, 2, 6].mean()) <= 1e-15
+    assert np.all(oracle.restrict_vol(np.full((5, 3, 7), 2.5)) == 2.5)
+
+
+def _tiny_case(seed):
+    g = tiny_geometry(n=8, h=4.0, nu=10, nv=10, du=6.0, dv=6.0, n_angles=6)
+    rng = np.random.default_rng(seed)
+    f = rng.uniform(0.0, 0.02, size=(8, 8, 8))
+    Y = oracle.project(g, f) + rng.normal(scale=0.01, size=(6, 10, 10))
+    return g, Y, rng
+
+
+def test_energy_gradient_matches_finite_differences():
+    g, Y, rng = _tiny_case(72)
+    f = rng.uniform(0.0, 0.03, size=(8, 8, 8))
+    mu, eps = 0.7, 3e-3
+    gr = oracle.energy_grad(g, Y, f, mu, eps)
+    d = 1e-5
+    for _ in range(12):
+        k, j, i = rng.integers(0, 8, size=3)
+        fp, fm = f.copy(), f.copy()
+        fp[k, j, i] += d
+        fm[k, j, i] -= d
+        fd = (oracle.energy(g, Y, fp, mu, eps)[0] - oracle.energy(g, Y, fm, mu, eps)[0]) / (2 * d)
+        assert abs(fd - gr[k, j, i]) <= 1e-6 * np.abs(gr).max()
+
+
+def test_fbs_linear_term_without_tv_is_shifted_landweber():
+    """TV weight 0, one inner step: A1 on E - <v, f> is
+    f <- max(0, f - (gamma/beta) A^T (A f - Y) + (Nv/beta) v)."""
+    g = tiny_geometry()
+    A = system_matrix(g)
+    rng = np.random.default_rng(73)
+    Y = rng.uniform(0, 3, size=(6, 8, 8))
+    v = rng.normal(scale=1e-3, size=(8, 8, 8))
+    mu, beta = 1.5, 4000.0
+    f, _ = oracle.fbs(g, Y, mu, beta, 1e-3, 1, 12, tv_weight=0.0, v=v)
+    gam = 2 * mu * 512 / (6 * 64)
+    x = np.zeros(512)
+    for _ in range(12):
+        x = np.maximum(0.0, x - gam / beta * (A.T @ (A @ x - Y.ravel())) + 512 / beta * v.ravel())
+    assert np.abs(f.ravel() - x).max() <= 1e-12 * max(1.0, np.abs(x).max())
+
+
+def test_coarse_model_is_first_order_coherent():
+    """The coarse model's gradient at R f, grad E_c(R f) - v_c, equals Q^T grad E(f),
+    and Q^T grad E(f) is the derivative of x -> E(f + Q x) (finite differences of the
+    fine energy along prolonged coarse unit vectors)."""
+    g, Y, rng = _tiny_case(74)
+    gc = oracle.level_geom(g, 1)
+    Yc = oracle.restrict_sino(Y)
+    f = rng.uniform(0.0, 0.03, size=(8, 8, 8))
+    mu = 0.7
+    eps, epsc = oracle.default_eps(g), oracle.default_eps(gc)
+    qt = oracle.prolong_vol_adjoint(oracle.energy_grad(g, Y, f, mu, eps), (4, 4, 4))
+    vc = oracle.energy_grad(gc, Yc, oracle.restrict_vol(f), mu, epsc) - qt
+    model_grad = oracle.energy_grad(gc, Yc, oracle.restrict_vol(f), mu, epsc) - vc
+    assert np.abs(model_grad - qt).max() <= 1e-15 * max(1.0, np.abs(qt).max()) * 100
+    d = 1e-5
+    for _ in range(6):
+        e = np.zeros((4, 4, 4))
+        e[tuple(rng.integers(0, 4, size=3))] = 1.0
+        q = oracle.prolong_vol(e, (8, 8, 8))
+        fd = (oracle.energy(g, Y, f + d * q, mu, eps)[0] - oracle.energy(g, Y, f - d * q, mu, eps)[0]) / (2 * d)
+        assert abs(fd - float(np.sum(qt * e))) <= 1e-6 * np.abs(qt).max()
+
+
+def test_vcycle_decreases_the_energy_faster_than_single_grid():
+    case = synth.make_case("small")
+    g = case["geom"]
+    mu = case["mu"]
+    f, tr, acc = oracle.vcycle(g, case["Y"], mu, 4, 2, pre=2, post=2, coarse=10)
+    assert np.all(np.diff(tr[:, 0]) < 0) and (f >= 0).all()
+    assert acc[0] >= 1                                    # coarse corrections were taken
+    beta, eps = oracle.auto_beta(g, mu), oracle.default_eps(g)
+    f1, _ = oracle.fbs(g, case["Y"], mu, beta, eps, 10, 16)    # the same fine-level work
+    assert tr[-1, 0] < 0.5 * oracle.energy(g, case["Y"], f1, mu, eps)[0]
