@@ -107,6 +107,22 @@ typedef struct {
                              P^T [default]; 1 the voxel-driven interpolation of Eq. 2
                              (see cbct_backproject_eq2).  The automatic beta always
                              comes from lambda_max(P^T P).                        */
+    int mg_cycle;         /* multigrid: 0 the coarse-to-fine cascade [default]: `iters`
+                             iterations of Algorithm A1 per level, coarsest first;
+                             1 `iters` V-cycles from f = 0 (or f_init with start_level
+                             0) on the finest level: on level l, mg_pre iterations of
+                             A1, then the coarse model E_{l+1}(x) - <lin, x> with
+                             lin = grad E_{l+1}(R f) - Q^T(grad E_l(f) - lin_l) (R the
+                             2x2x2 mean, Q the trilinear prolongation) reduced by a cycle
+                             on level l+1 (mg_coarse iterations of A1 on the coarsest),
+                             the correction f + Q(x - R f) clamped at 0 and kept when it
+                             lowers the level's model, then mg_post iterations.  Needs
+                             clamp_mode 0 and adjoint_mode 0; cbct_reconstruct only.
+                             energy_trace then receives [iters][3]: E, E1, mu*E2 of the
+                             finest iterate after each cycle.                     */
+    int mg_pre, mg_post;  /* smoothing iterations per level; 0 -> 2 each             */
+    int mg_coarse;        /* iterations on the coarsest level; 0 -> 10               */
+    int *mg_accepted;     /* optional host out [levels]: coarse corrections kept     */
 } cbct_options;
 
 /* Kernel classes reported through cbct_options.kernel_ms. */

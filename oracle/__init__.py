@@ -337,14 +337,14 @@ def energy_grad(geom, Y, f, mu, eps):
     return out
 
 
-def vcycle(geom, Y, mu, cycles, levels, betas=None, eps=0.0, M=10, pre=2, post=2, coarse=10, K_pi=30):
+def vcycle(geom, Y, mu, cycles, levels, betas=None, eps=0.0, M=10, pre=2, post=2, coarse=10, K_pi=30, tv_mode=0):
     """Returns (f, trace [cycles][3], accepted [levels])."""
     Y = _f64(Y)
     f = np.empty(vol_shape(geom))
     trace = np.empty((cycles, 3))
     acc = (C.c_int * levels)()
     b = _f64(betas) if betas is not None else None
-    h = _g(geom)
+    h = _g(geom, tv_mode)
     _load().or_vcycle(C.byref(h.s), _ptr(Y), mu, cycles, levels, _ptr(b), eps, M, pre, post, coarse, K_pi,
                       _ptr(f), _ptr(trace), acc)
     return f, trace, np.array(acc[:])

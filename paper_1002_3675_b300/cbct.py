@@ -44,7 +44,8 @@ class Options(C.Structure):
                 ("use_graphs", C.c_int), ("energy_trace", C.POINTER(C.c_double)),
                 ("beta_out", C.POINTER(C.c_double)), ("kernel_ms", C.POINTER(C.c_float)),
                 ("kernel_launches", C.POINTER(C.c_int)), ("reuse_lambda", C.c_int), ("tv_mode", C.c_int),
-                ("adjoint_mode", C.c_int)]
+                ("adjoint_mode", C.c_int), ("mg_cycle", C.c_int), ("mg_pre", C.c_int), ("mg_post", C.c_int),
+                ("mg_coarse", C.c_int), ("mg_accepted", C.POINTER(C.c_int))]
 
 
 class Request(C.Structure):
@@ -247,7 +248,7 @@ def cbct_energy(g: Geometry, Y, f, mu, eps, tv_mode=0):
 
 def make_options(levels, *, beta=0.0, betas=None, eps=0.0, inner_iters=0, clamp_mode=0, sino_fp16=False,
                  power_iters=0, f_init=None, start_level=0, use_graphs=False, reuse_lambda=False, tv_mode=0,
-                 adjoint_mode=0, keep=None):
+                 adjoint_mode=0, mg_cycle=0, mg_pre=0, mg_post=0, mg_coarse=0, keep=None):
     """cbct_options from keyword arguments; `keep` (a list) holds arrays the struct points to."""
     o = Options()
     o.beta = beta
@@ -267,15 +268,17 @@ def make_options(levels, *, beta=0.0, betas=None, eps=0.0, inner_iters=0, clamp_
     o.reuse_lambda = int(bool(reuse_lambda))
     o.tv_mode = int(tv_mode)
     o.adjoint_mode = int(adjoint_mode)
+    o.mg_cycle, o.mg_pre, o.mg_post, o.mg_coarse = int(mg_cycle), int(mg_pre), int(mg_post), int(mg_coarse)
     return o
 
 
 def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=None, *, beta=0.0,
                      betas=None, eps=0.0, inner_iters=0, clamp_mode=0, sino_fp16=False, power_iters=0,
                      f_init=None, start_level=0, use_graphs=False, trace=False, kernel_times=False,
-                     reuse_lambda=False, tv_mode=0, adjoint_mode=0):
+                     reuse_lambda=False, tv_mode=0, adjoint_mode=0, mg_cycle=0, mg_pre=0, mg_post=0, mg_coarse=0):
     """Returns f_out, or (f_out, info) when trace/kernel_times is requested; info holds
-    'trace' [levels][iters][3], 'betas' [levels], 'kernel_ms'/'kernel_launches'."""
+    'trace' [levels][iters][3] ([iters][3] after each V-cycle when mg_cycle=1),
+    'betas' [levels], 'accepted' [levels] (V-cycles), 'kernel_ms'/'kernel_launches'."""
     f_out = _empty(g.vol_shape) if f_out is None else f_out
     o = Options()
     o.beta = beta
@@ -293,6 +296,9 @@ def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=N
     o.reuse_lambda = int(bool(reuse_lambda))
     o.tv_mode = int(tv_mode)
     o.adjoint_mode = int(adjoint_mode)
+    o.mg_cycle, o.mg_pre, o.mg_post, o.mg_coarse = int(mg_cycle), int(mg_pre), int(mg_post), int(mg_coarse)
+    acc = (C.c_int * 8)()
+    o.mg_accepted = acc
     tr = np.full((levels, max(iters, 1), 3), np.nan) if trace else None
     if trace:
         o.energy_trace = tr.ctypes.data_as(C.POINTER(C.c_double))
@@ -308,8 +314,10 @@ def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=N
     if not (trace or kernel_times):
         return f_out
     info = {"betas": bo}
+    if mg_cycle:
+        info["accepted"] = np.array(acc[:levels])
     if trace:
-        info["trace"] = tr[:, :iters]
+        info["trace"] = tr.reshape(-1, 3)[:iters] if mg_cycle else tr[:, :iters]
     if kernel_times:
         info["kernel_ms"] = dict(zip(KERNEL_CLASSES, list(km)))
         info["kernel_launches"] = dict(zip(KERNEL_CLASSES, list(kl)))
@@ -325,7 +333,8 @@ def cbct_reconstruct_batch(requests, use_graphs=False):
         g = r["geom"]
         levels = r["levels"]
         kw = {k: v for k, v in r.items() if k in ("beta", "betas", "eps", "inner_iters", "clamp_mode", "sino_fp16",
-                                                  "power_iters", "f_init", "start_level", "reuse_lambda", "tv_mode", "adjoint_mode")}
+                                                  "power_iters", "f_init", "start_level", "reuse_lambda", "tv_mode", "adjoint_mode",
+                                                  "mg_cycle", "mg_pre", "mg_post", "mg_coarse")}
         o = make_options(levels, keep=keep, **kw)
         info = {"betas": np.zeros(levels)}
         o.beta_out = info["betas"].ctypes.data_as(C.POINTER(C.c_double))

@@ -188,6 +188,10 @@ cbct_status enqueue_iteration(cbct_geometry *G, Level *L, const SolveParams &P, 
         else
             CK(launch_backproject(gd, L->rs, L->f, L->g, P.c, BP_STEP, s), "backprojection");
     }
+    if (P.lin) {  // coarse model of a V-cycle: step 1 of A1 on E - <lin, f>
+        Launch l(prof, CBCT_K_REDUCE);
+        CK(launch_axpy(L->g, P.lin, P.lin_scale, vol_elems(gd), s), "linear term");
+    }
     ST(enqueue_prox(L, P, P.clamp_mode == 0 ? L->f : L->g, P.clamp_mode == 0 ? pt : nullptr,
                     P.clamp_mode == 0 ? &nb_t : nullptr, prof, s));
     {
@@ -287,6 +291,128 @@ cbct_status check_geometry_desc(const cbct_geometry_desc *d) {
     return CBCT_OK;
 }
 
+
+// ---------------------------------------------------------------------------------
+// V-cycle: a full-approximation reading of the multigrid method the paper cites.
+// Level l minimises the model E_l(f) - <lin_l, f> (lin_0 = 0); a cycle smooths with
+// `pre` iterations of Algorithm A1, builds the coarse model
+//   E_{l+1}(x) - <lin_{l+1}, x>,  lin_{l+1} = grad E_{l+1}(R f) - Q^T (grad E_l(f) - lin_l)
+// (R: 2x2x2 mean, Q: trilinear prolongation), whose gradient at R f is Q^T of the
+// fine model's gradient at f, reduces it by a cycle on level l+1 (`coarse` iterations
+// of A1 on the coarsest level), keeps the correction f + Q(x - R f), clamped at 0,
+// when it lowers the fine model, and smooths with `post` iterations.
+// ---------------------------------------------------------------------------------
+
+struct VCycle {
+    cbct_geometry *G;
+    std::vector<Level *> Ls;
+    std::vector<SolveParams> P;   // per level
+    int levels, pre, post, coarse;
+    bool graphs;
+    double mu;
+    double *dtrace;
+    Prof *prof;
+    cudaStream_t s;
+    int accepted[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+
+    float *lin(int l) { return Ls[l]->mg; }
+    float *x0(int l) { return Ls[l]->mg + vol_elems(Ls[l]->gd); }
+    float *t1(int l) { return Ls[l]->mg + 2 * vol_elems(Ls[l]->gd); }
+    float *t2(int l) { return Ls[l]->mg + 3 * vol_elems(Ls[l]->gd); }
+
+    // out = grad E_l(f) - lin (lin may be null); uses the level's residual buffer
+    cbct_status grad(int l, const float *f, const float *lv, float *out) {
+        Level *L = Ls[l];
+        const GeoDev &g = L->gd;
+        const SolveParams &Q = P[l];
+        {
+            Launch lz(*prof, CBCT_K_PROJECT);
+            CK(launch_project(g, f, Q.fp16 ? nullptr : L->Y, Q.fp16 ? L->Yh : nullptr, L->rs, L->partial,
+                              Q.fp16 ? PROJ_RESID16 : PROJ_RESID32, s, nullptr),
+               "projection");
+        }
+        {
+            Launch lz(*prof, CBCT_K_BACKPROJECT);
+            CK(launch_backproject(g, L->rs, nullptr, out, 0.f, BP_PLAIN, s), "backprojection");
+        }
+        Launch lz(*prof, CBCT_K_REDUCE);
+        CK(launch_energy_grad(tv_args(L, Q), f, out, (float)gamma_of(L, mu), (float)Q.inv_nv, lv, out, s),
+           "energy gradient");
+        return CBCT_OK;
+    }
+
+    // host values {E, E1, mu E2} of f on level l, and <lin, f> (0 without lin)
+    cbct_status energy(int l, const float *f, const float *lv, double out[4]) {
+        Level *L = Ls[l];
+        const GeoDev &g = L->gd;
+        const SolveParams &Q = P[l];
+        const size_t np = project_partials(g);
+        int nb_p = 0, nb_t = 0;
+        double *scratch = G->dscalars + 8;
+        CK(cudaMemsetAsync(G->dcounter + 1, 0, sizeof(int), s), "counter");
+        {
+            Launch lz(*prof, CBCT_K_PROJECT);
+            CK(launch_project(g, f, Q.fp16 ? nullptr : L->Y, Q.fp16 ? L->Yh : nullptr, L->rs, L->partial,
+                              Q.fp16 ? PROJ_RESID16 : PROJ_RESID32, s, &nb_p),
+               "projection");
+        }
+        Launch lz(*prof, CBCT_K_REDUCE);
+        CK(launch_tv_energy(tv_args(L, Q), f, L->partial + np, s, &nb_t), "tv energy");
+        CK(launch_energy_finalize(L->partial, nb_p, L->partial + np, nb_t, Q.inv_nv, Q.mu_over_nr, scratch,
+                                  G->dcounter + 1, s),
+           "energy");
+        if (lv) CK(launch_dot(lv, f, vol_elems(g), L->mg_partial, scratch + 3, s), "linear term");
+        else CK(cudaMemsetAsync(scratch + 3, 0, sizeof(double), s), "linear term");
+        CK(cudaMemcpyAsync(out, scratch, 4 * sizeof(double), cudaMemcpyDeviceToHost, s), "energy copy");
+        CK(cudaStreamSynchronize(s), "energy sync");
+        return CBCT_OK;
+    }
+
+    cbct_status smooth(int l, int iters, const float *lv) {
+        if (iters <= 0) return CBCT_OK;
+        SolveParams Q = P[l];
+        Q.lin = lv;
+        Q.lin_scale = lv ? (float)((double)vol_elems(Ls[l]->gd) / (double)Q.beta) : 0.f;
+        return run_level(G, Ls[l], Q, iters, dtrace, graphs, *prof, s);
+    }
+
+    cbct_status cycle(int l, const float *lv) {
+        if (l == levels - 1) return smooth(l, coarse, lv);
+        ST(smooth(l, pre, lv));
+        Level *Lf = Ls[l], *Lc = Ls[l + 1];
+        const GeoDev &gf = Lf->gd, &gc = Lc->gd;
+        const size_t nf = vol_elems(gf), nc = vol_elems(gc);
+        ST(grad(l, Lf->f, lv, t1(l)));
+        {
+            Launch lz(*prof, CBCT_K_TRANSFER);
+            CK(launch_restrict_vol(Lf->f, gf.nx, gf.ny, gf.nz, x0(l + 1), s), "volume restriction");
+            CK(cudaMemcpyAsync(Lc->f, x0(l + 1), nc * 4, cudaMemcpyDeviceToDevice, s), "copy");
+            CK(launch_prolong_adjoint(t1(l), gf.nx, gf.ny, gf.nz, t1(l + 1), gc.nx, gc.ny, gc.nz, s),
+               "prolongation transpose");
+        }
+        ST(grad(l + 1, x0(l + 1), nullptr, t2(l + 1)));
+        {
+            Launch lz(*prof, CBCT_K_REDUCE);
+            CK(launch_sub(t2(l + 1), t1(l + 1), lin(l + 1), nc, s), "coarse linear term");
+        }
+        ST(cycle(l + 1, lin(l + 1)));
+        {
+            Launch lz(*prof, CBCT_K_TRANSFER);
+            CK(launch_sub(Lc->f, x0(l + 1), t1(l + 1), nc, s), "coarse change");
+            CK(launch_prolong(t1(l + 1), gc.nx, gc.ny, gc.nz, t1(l), gf.nx, gf.ny, gf.nz, s), "prolongation");
+            CK(launch_add_clamp(Lf->f, t1(l), t2(l), nf, s), "correction");
+        }
+        double e_try[4], e_cur[4];
+        ST(energy(l, t2(l), lv, e_try));
+        ST(energy(l, Lf->f, lv, e_cur));
+        if (e_try[0] - e_try[3] < e_cur[0] - e_cur[3]) {
+            CK(cudaMemcpyAsync(Lf->f, t2(l), nf * 4, cudaMemcpyDeviceToDevice, s), "accept correction");
+            accepted[l] += 1;
+        }
+        return smooth(l, post, lv);
+    }
+};
+
 }  // namespace
 
 // Device energy-trace buffer owned by the geometry (grown on demand).
@@ -342,6 +468,8 @@ cbct_status cbct::solve_params(const Level *L, double mu, double beta, double ep
     P->tv_mode = tv_mode;
     P->adjoint_mode = adjoint_mode;
     P->c_eq2 = (float)(gam / beta * eq2_scale(L));
+    P->lin = nullptr;
+    P->lin_scale = 0.f;
     P->fp16 = fp16;
     P->inv_nv = 1.0 / (double)vol_elems(L->gd);
     P->mu_over_nr = mu / (double)sino_elems(L->gd);
@@ -384,6 +512,10 @@ cbct_status cbct::validate_request(cbct_geometry *G, const float *Y_dev, double 
         if (o->adjoint_mode != 0 && o->adjoint_mode != 1) {
             set_error("adjoint_mode must be 0 or 1");
             return CBCT_ERR_INVALID_ARG;
+        }
+        if (o->mg_cycle != 0) {
+            set_error("V-cycles (mg_cycle 1) run through cbct_reconstruct only");
+            return CBCT_ERR_UNSUPPORTED;
         }
         if (o->inner_iters < 0 || o->inner_iters > 10000 || o->power_iters < 0) {
             set_error("inner_iters must be in 0..10000 and power_iters >= 0");
@@ -676,6 +808,20 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
         start = o.start_level;
     }
 
+    if (o.mg_cycle != 0 && o.mg_cycle != 1) {
+        set_error("mg_cycle must be 0 or 1");
+        return CBCT_ERR_INVALID_ARG;
+    }
+    if (o.mg_cycle == 1) {
+        if (o.mg_pre < 0 || o.mg_post < 0 || o.mg_coarse < 0 || (o.f_init_dev && o.start_level != 0)) {
+            set_error("V-cycles need mg_pre, mg_post, mg_coarse >= 0 and start from level 0");
+            return CBCT_ERR_INVALID_ARG;
+        }
+        if (o.clamp_mode != 0 || o.adjoint_mode != 0) {
+            set_error("V-cycles use clamp_mode 0 and the exact adjoint");
+            return CBCT_ERR_UNSUPPORTED;
+        }
+    }
     std::vector<Level *> Ls(levels);
     for (int l = 0; l < levels; ++l) {
         ST(ensure_level(G, l, &Ls[l]));
@@ -703,6 +849,72 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
         if (fp16) CK(launch_to_half(Ls[l]->Y, Ls[l]->Yh, sino_elems(Ls[l]->gd), s), "half copy");
     }
 
+    auto level_beta = [&](int l, double *beta) -> cbct_status {
+        Level *L = Ls[l];
+        if (o.betas) {
+            *beta = o.betas[l];
+        } else if (o.beta > 0) {
+            *beta = o.beta;
+        } else {
+            double lam = 0.0;
+            if (o.reuse_lambda && L->lambda_iters == K) {
+                lam = L->lambda;
+            } else {
+                ST(power_iteration(G, L, K, &lam, prof, s));
+                L->lambda = lam;
+                L->lambda_iters = K;
+            }
+            *beta = std::max(10.0 * mu, 1.05 * gamma_of(L, mu) * lam);
+        }
+        if (o.beta_out) o.beta_out[l] = *beta;
+        return CBCT_OK;
+    };
+
+    if (o.mg_cycle == 1) {  // V-cycles from f = 0 on the finest level
+        VCycle V;
+        V.G = G;
+        V.Ls = Ls;
+        V.levels = levels;
+        V.pre = o.mg_pre > 0 ? o.mg_pre : 2;
+        V.post = o.mg_post > 0 ? o.mg_post : 2;
+        V.coarse = o.mg_coarse > 0 ? o.mg_coarse : 10;
+        V.graphs = o.use_graphs != 0;
+        V.mu = mu;
+        V.prof = &prof;
+        V.s = s;
+        ST(get_trace(G, 3 * (size_t)std::max({V.pre, V.post, V.coarse, 1}), &V.dtrace));
+        V.P.resize(levels);
+        for (int l = 0; l < levels; ++l) {
+            ST(ensure_mg_workspace(Ls[l]));
+            double beta;
+            ST(level_beta(l, &beta));
+            const double eps = o.eps > 0 ? o.eps : default_eps(Ls[l]);
+            ST(solve_params(Ls[l], mu, beta, eps, M, 0, fp16, &V.P[l], o.tv_mode, 0));
+        }
+        if (o.f_init_dev) {
+            const GeoDev &g0 = Ls[0]->gd;
+            CK(launch_vol_to_internal(o.f_init_dev, Ls[0]->f, g0.nx, g0.ny, g0.nz, s), "volume layout");
+        } else {
+            CK(cudaMemsetAsync(Ls[0]->f, 0, vol_elems(Ls[0]->gd) * 4, s), "zero start");
+        }
+        for (int c = 0; c < iters; ++c) {
+            ST(V.cycle(0, nullptr));
+            if (o.energy_trace) {
+                double e[4];
+                ST(V.energy(0, Ls[0]->f, nullptr, e));
+                for (int q = 0; q < 3; ++q) o.energy_trace[3 * (size_t)c + q] = e[q];
+            }
+        }
+        if (o.mg_accepted)
+            for (int l = 0; l < levels; ++l) o.mg_accepted[l] = V.accepted[l];
+        {
+            Launch lz(prof, CBCT_K_TRANSFER);
+            const GeoDev &g0 = Ls[0]->gd;
+            CK(launch_vol_to_api(Ls[0]->f, f_out_dev, g0.nx, g0.ny, g0.nz, s), "volume layout");
+        }
+        return prof.collect(o.kernel_ms, o.kernel_launches);
+    }
+
     for (int l = start; l >= 0; --l) {
         Level *L = Ls[l];
         const GeoDev &g = L->gd;
@@ -718,22 +930,7 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
             CK(launch_prolong(Ls[l + 1]->f, gc.nx, gc.ny, gc.nz, L->f, g.nx, g.ny, g.nz, s), "prolongation");
         }
         double beta;
-        if (o.betas) {
-            beta = o.betas[l];
-        } else if (o.beta > 0) {
-            beta = o.beta;
-        } else {
-            double lam = 0.0;
-            if (o.reuse_lambda && L->lambda_iters == K) {
-                lam = L->lambda;
-            } else {
-                ST(power_iteration(G, L, K, &lam, prof, s));
-                L->lambda = lam;
-                L->lambda_iters = K;
-            }
-            beta = std::max(10.0 * mu, 1.05 * gamma_of(L, mu) * lam);
-        }
-        if (o.beta_out) o.beta_out[l] = beta;
+        ST(level_beta(l, &beta));
         const double eps = o.eps > 0 ? o.eps : default_eps(L);
         SolveParams P;
         ST(solve_params(L, mu, beta, eps, M, o.clamp_mode, fp16, &P, o.tv_mode, o.adjoint_mode));

@@ -106,11 +106,18 @@ __global__ void __launch_bounds__(PROJ_MAX_THREADS, 2)
 k_project_batch(const ProjItem *__restrict__ items, const long *__restrict__ start, int n, long total) {
     extern __shared__ float smem[];
     __shared__ ProjItem it;
+    int cur = -1;
+    long first = 0, next = 0;
     for (long t = blockIdx.x; t < total; t += gridDim.x) {
-        const int r = find_item(start, n, t);
-        copy_words(&it, items + r, sizeof(ProjItem), threadIdx.x, blockDim.x);
-        __syncthreads();
-        const long local = t - start[r];
+        if (cur < 0 || t >= next) {  // the item changes rarely along a block's tiles
+            const int r = find_item(start, n, t);
+            copy_words(&it, items + r, sizeof(ProjItem), threadIdx.x, blockDim.x);
+            __syncthreads();
+            cur = r;
+            first = __ldg(start + r);
+            next = r + 1 < n ? __ldg(start + r + 1) : total;
+        }
+        const long local = t - first;
         const int a = (int)(local % it.G.nu);
         const long rest = local / it.G.nu;
         const int ia = (int)(rest % it.G.na), zc = (int)(rest / it.G.na);
@@ -125,12 +132,19 @@ k_bp_batch(const BpItem *__restrict__ items, const long *__restrict__ start, int
     __shared__ BpItem it[BP_THREADS / 32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long stride = (long)gridDim.x * (BP_THREADS / 32);
+    int cur = -1;
+    long first = 0, next = 0;
     for (long t = (long)blockIdx.x * (BP_THREADS / 32) + w; t < total; t += stride) {
-        const int r = find_item(start, n, t);
-        copy_words(&it[w], items + r, sizeof(BpItem), lane, 32);
-        __syncwarp();
-        bp_warp<VPL>(it[w].G, it[w].mode, it[w].rs, it[w].fin, it[w].out, it[w].c, t - start[r]);
-        __syncwarp();
+        if (cur < 0 || t >= next) {  // the item changes rarely along a warp's tiles
+            const int r = find_item(start, n, t);
+            __syncwarp();
+            copy_words(&it[w], items + r, sizeof(BpItem), lane, 32);
+            __syncwarp();
+            cur = r;
+            first = __ldg(start + r);
+            next = r + 1 < n ? __ldg(start + r + 1) : total;
+        }
+        bp_warp<VPL>(it[w].G, it[w].mode, it[w].rs, it[w].fin, it[w].out, it[w].c, t - first);
     }
 }
 
@@ -148,10 +162,21 @@ k_eq2_batch(const Eq2Item *__restrict__ items, const long *__restrict__ start, i
 
 __global__ void __launch_bounds__(TV_THREADS)
 k_tv_batch(const TvItem *__restrict__ items, const long *__restrict__ start, int n, long total) {
+    __shared__ TvItem it;
+    __shared__ long first;
+    int cur = -1;
     for (long t = blockIdx.x; t < total; t += gridDim.x) {
-        const int r = find_item(start, n, t);
-        const TvItem it = items[r];
-        const long blk = t - start[r];
+        // the item changes rarely along a block's tiles: look it up only when it does
+        const int r = (cur >= 0 && t >= first && (cur + 1 >= n || t < __ldg(start + cur + 1))) ? cur
+                                                                                            : find_item(start, n, t);
+        if (r != cur) {
+            __syncthreads();
+            copy_words(&it, items + r, sizeof(TvItem), threadIdx.x, blockDim.x);
+            if (threadIdx.x == 0) first = start[r];
+            cur = r;
+            __syncthreads();
+        }
+        const long blk = t - first;
         if (it.clamp) {
             if (it.e1) tv_block<true, true>(it.A, it.fin, it.g, it.fout, it.partial, blk);
             else tv_block<true, false>(it.A, it.fin, it.g, it.fout, it.partial, blk);
@@ -427,8 +452,7 @@ cbct_status Engine::build_tables() {
     long eqtot = 0;
     std::vector<std::vector<long>> tvstart;
     long ptot = 0, dtot = 0, bptot[4] = {0, 0, 0, 0};
-    proj_threads = 32;
-    proj_smem = 0;
+    std::vector<std::pair<ProjItem, long>> pitems;  // item, tiles
     max_m = 0;
     copies.clear();
     tv_energy_jobs.clear();
@@ -437,8 +461,6 @@ cbct_status Engine::build_tables() {
         Level *L = j->Ls[j->level];
         const GeoDev &g = L->gd;
         const bool power = j->phase == PH_POWER;
-        proj_threads = std::max(proj_threads, project_threads(g));
-        proj_smem = std::max(proj_smem, proj_smem_of(g));
         ProjItem pi;
         pi.G = g;
         pi.vol = power ? L->A : L->f;
@@ -449,7 +471,7 @@ cbct_status Engine::build_tables() {
         const bool eq2 = !power && j->P.adjoint_mode == 1;
         pi.mode = power ? PROJ_SCALED
                         : (j->fp16 ? (eq2 ? PROJ_RAW16 : PROJ_RESID16) : (eq2 ? PROJ_RAW32 : PROJ_RESID32));
-        hproj.push_back(pi);
+        pitems.push_back({pi, (long)g.nu * g.na * ((g.nv + project_threads(g) - 1) / project_threads(g))});
         if (eq2) {
             Eq2Item ei;
             ei.G = g;
@@ -505,11 +527,34 @@ cbct_status Engine::build_tables() {
             ei.counter = j->G->dcounter;
             hen.push_back(ei);
         }
-        pstart.push_back(ptot);
-        ptot += (long)g.nu * g.na * ((g.nv + project_threads(g) - 1) / project_threads(g));
     }
-    // resident projector blocks per SM (registers: 64 per thread; shared memory)
-    proj_blocks = std::max(1, std::min(65536 / (64 * proj_threads), (227 * 1024) / (std::max(proj_smem, 1) + 1024)));
+    // projector items grouped by block size (the tile height of a request must be its
+    // single-request value), one launch per group; resident blocks per SM from the
+    // registers (64 per thread) and the group's largest shared-memory size
+    std::stable_sort(pitems.begin(), pitems.end(), [](const std::pair<ProjItem, long> &x,
+                                                      const std::pair<ProjItem, long> &y) {
+        return project_threads(x.first.G) < project_threads(y.first.G);
+    });
+    pgroups.clear();
+    for (const auto &it : pitems) {
+        const int T = project_threads(it.first.G);
+        if (pgroups.empty() || pgroups.back().threads != T) {
+            ProjGroup pg;
+            pg.threads = T;
+            pg.first = (int)hproj.size();
+            pgroups.push_back(pg);
+            ptot = 0;
+        }
+        ProjGroup &pg = pgroups.back();
+        pg.smem = std::max(pg.smem, proj_smem_of(it.first.G));
+        pstart.push_back(ptot);
+        hproj.push_back(it.first);
+        ptot += it.second;
+        pg.count += 1;
+        pg.tiles = ptot;
+    }
+    for (ProjGroup &pg : pgroups)
+        pg.blocks = std::max(1, std::min(65536 / (64 * pg.threads), (227 * 1024) / (pg.smem + 1024)));
     // TV sweeps: for each m, the jobs with m < M (ping-pong as in the single path)
     htv.assign(max_m, {});
     tvstart.assign(max_m, {});
@@ -540,7 +585,6 @@ cbct_status Engine::build_tables() {
         }
         if (src != L->f) copies.push_back({L->f, src, vol_elems(L->gd) * 4});
     }
-    ptotal = ptot;
     dtotal = dtot;
     for (int v = 0; v < 4; ++v) bptotal[v] = bptot[v];
     eqtotal = eqtot;
@@ -634,8 +678,9 @@ cbct_status Engine::launch_stages() {
             cudaFuncSetAttribute(k_project_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, PROJ_SMEM);
             attr_done[dev] = true;
         }
-        k_project_batch<<<(unsigned)grid_for(ptotal, proj_blocks), proj_threads, proj_smem, s>>>(d_proj, d_pstart,
-                                                                                        (int)hproj.size(), ptotal);
+        for (const ProjGroup &pg : pgroups)
+            k_project_batch<<<(unsigned)grid_for(pg.tiles, pg.blocks), pg.threads, pg.smem, s>>>(
+                d_proj + pg.first, d_pstart + pg.first, pg.count, pg.tiles);
         ECK(cudaGetLastError(), "batched projection");
     }
     for (int v = 0; v < 4; ++v) {

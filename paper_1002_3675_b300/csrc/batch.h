@@ -68,6 +68,11 @@ class Engine {
     int same_ticks = 0;
     cudaGraphExec_t gexec = nullptr;
     // host copies of the item tables and their device blob
+    struct ProjGroup {  // projector items with one block size: one launch
+        int threads = 0, smem = 0, blocks = 1, first = 0, count = 0;
+        long tiles = 0;
+    };
+    std::vector<ProjGroup> pgroups;
     std::vector<ProjItem> hproj;
     std::vector<BpItem> hbp[4];
     std::vector<Eq2Item> heq;
@@ -77,8 +82,8 @@ class Engine {
     std::vector<long> tvtot;
     std::vector<CopyOp> copies;
     std::vector<Job *> tv_energy_jobs;
-    long ptotal = 0, dtotal = 0, bptotal[4] = {0, 0, 0, 0}, eqtotal = 0;
-    int proj_threads = 32, proj_smem = 0, proj_blocks = 2, max_m = 0;
+    long dtotal = 0, bptotal[4] = {0, 0, 0, 0}, eqtotal = 0;
+    int max_m = 0;
     void *dblob = nullptr;
     size_t dblob_len = 0;
     ProjItem *d_proj = nullptr;

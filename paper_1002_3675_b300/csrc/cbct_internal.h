@@ -79,6 +79,8 @@ struct Level {
     size_t partial_len = 0;
     double lambda = 0.0;          // cached lambda_max(P^T P) (0 = unknown)
     int lambda_iters = 0;
+    float *mg = nullptr;          // V-cycle volumes: linear term, restricted iterate, 2 scratch
+    double *mg_partial = nullptr; // V-cycle dot-product partials
 };
 
 struct EventPool {
@@ -111,6 +113,7 @@ cbct_status cuda_fail(cudaError_t e, const char *what);
 // level management (geometry.cu)
 cbct_status ensure_level(cbct_geometry *G, int level, Level **out);
 cbct_status ensure_workspace(Level *L, bool need_half);
+cbct_status ensure_mg_workspace(Level *L);
 void free_level(Level *L);
 
 // kernel launchers (return cudaError_t of the launch)
@@ -169,8 +172,21 @@ cudaError_t launch_power_finalize(const double *partial, int nblk, double *lam, 
                                   cudaStream_t s);
 cudaError_t launch_scale(const float *y, const float *scale, float *x, size_t n, cudaStream_t s);
 cudaError_t launch_fill(float *x, float v, size_t n, cudaStream_t s);
+
+// V-cycle kernels (k_mg.cu); volumes [n0][n1][n2], coarse sizes ceil(n / 2)
+cudaError_t launch_restrict_vol(const float *f, int n0, int n1, int n2, float *fc, cudaStream_t s);
+cudaError_t launch_prolong_adjoint(const float *x, int n0, int n1, int n2, float *out, int c0, int c1, int c2,
+                                   cudaStream_t s);
+cudaError_t launch_axpy(float *y, const float *x, float a, size_t n, cudaStream_t s);
+cudaError_t launch_sub(const float *a, const float *b, float *out, size_t n, cudaStream_t s);
+cudaError_t launch_add_clamp(const float *f, const float *c, float *out, size_t n, cudaStream_t s);
+size_t dot_partials(size_t n);
+cudaError_t launch_dot(const float *x, const float *y, size_t n, double *partial, double *out, cudaStream_t s);
 cudaError_t launch_tv_energy(const TvArgs &a, const float *f, double *partial, cudaStream_t s,
                              int *nblocks_out);
+// out = (grad TV_eps(f) + gamma bp) / Nv - lin (lin optional; out may alias bp)
+cudaError_t launch_energy_grad(const TvArgs &a, const float *f, const float *bp, float gamma, float inv_nv,
+                               const float *lin, float *out, cudaStream_t s);
 
 
 // Solver constants of one level (Algorithm A1, discrete scaling of Eq. 1).
@@ -184,6 +200,8 @@ struct SolveParams {
     int tv_mode;
     int adjoint_mode;  // 0 exact transpose, 1 Eq. 2
     float c_eq2;       // (gamma / beta) dV / (du dv)
+    const float *lin;  // V-cycle coarse model: linear term -<lin, f> (null: none)
+    float lin_scale;   // Nv / beta: its share of step 1
     bool fp16;
     double inv_nv, mu_over_nr;
 };

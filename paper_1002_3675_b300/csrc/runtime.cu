@@ -75,6 +75,8 @@ void free_level(Level *L) {
     cudaFree(L->Y);
     cudaFree(L->Yh);
     cudaFree(L->partial);
+    cudaFree(L->mg);
+    cudaFree(L->mg_partial);
     delete L;
 }
 
@@ -259,6 +261,17 @@ cbct_status ensure_workspace(Level *L, bool need_half) {
         if ((st = dmalloc((void **)&L->partial, need * sizeof(double), "partials")) != CBCT_OK) return st;
         L->partial_len = need;
     }
+    return CBCT_OK;
+}
+
+cbct_status ensure_mg_workspace(Level *L) {
+    const size_t nvox = vol_elems(L->gd);
+    cbct_status st = CBCT_OK;
+    if (!L->mg && (st = dmalloc((void **)&L->mg, 4 * nvox * 4, "multigrid volumes")) != CBCT_OK) return st;
+    if (!L->mg_partial &&
+        (st = dmalloc((void **)&L->mg_partial, (dot_partials(nvox) + 8) * sizeof(double), "multigrid partials")) !=
+            CBCT_OK)
+        return st;
     return CBCT_OK;
 }
 
