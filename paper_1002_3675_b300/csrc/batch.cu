@@ -1,11 +1,13 @@
 // Batched reconstruction: many requests advance together, one Algorithm A1
-// iteration (or one power-iteration step) per tick, every stage of every request in
-// one persistent launch per stage.
+// iteration (or one power-iteration step) per tick.  A stage of a request that fills
+// the GPU by itself (enough tiles for several waves) runs as its own single-request
+// launch; the stages of the smaller requests share one persistent launch per stage,
+// sized to the blocks that stay resident on every SM.
 //
-// Each launch reads a device table of per-request items (geometry block, buffers,
-// mode) and a prefix table of per-request tile counts; a block (or warp) maps its
-// global tile index to (request, local tile) and runs the same tile body as the
-// single-request kernels.  Every request is computed with exactly the arithmetic of
+// Each persistent launch reads a device table of per-request items (geometry block,
+// buffers, mode) and a prefix table of per-request tile counts; a block (or warp)
+// maps its global tile index to (request, local tile) and runs the same tile body as
+// the single-request kernels.  Every request is computed with exactly the arithmetic of
 // a single-request call, in the same order, so its result is bitwise the same alone
 // and in any mix.  The item tables are rebuilt only when the set of active stages
 // changes; while it does not, a tick's launches can be replayed as a CUDA graph.
@@ -301,11 +303,6 @@ static int sm_count() {
     return n;
 }
 
-static long grid_for(long total, int per_sm) {
-    const long cap = (long)sm_count() * per_sm;
-    return std::max(1L, std::min(total, cap));
-}
-
 #define ECK(call, what)                                      \
     do {                                                     \
         cudaError_t e__ = (call);                            \
@@ -453,6 +450,11 @@ cbct_status Engine::build_tables() {
     std::vector<std::vector<long>> tvstart;
     long ptot = 0, dtot = 0, bptot[4] = {0, 0, 0, 0};
     std::vector<std::pair<ProjItem, long>> pitems;  // item, tiles
+    solo_proj.clear();
+    solo_bp.clear();
+    solo_eq.clear();
+    solo_tv.clear();
+    const long sms = sm_count();
     max_m = 0;
     copies.clear();
     tv_energy_jobs.clear();
@@ -471,7 +473,11 @@ cbct_status Engine::build_tables() {
         const bool eq2 = !power && j->P.adjoint_mode == 1;
         pi.mode = power ? PROJ_SCALED
                         : (j->fp16 ? (eq2 ? PROJ_RAW16 : PROJ_RESID16) : (eq2 ? PROJ_RAW32 : PROJ_RESID32));
-        pitems.push_back({pi, (long)g.nu * g.na * ((g.nv + project_threads(g) - 1) / project_threads(g))});
+        // a stage that fills the GPU by itself runs as its own single-request launch (the
+        // same tile bodies, so the same bits); the others share a persistent launch
+        const long ptiles = (long)g.nu * g.na * ((g.nv + project_threads(g) - 1) / project_threads(g));
+        if (ptiles >= 8 * sms) solo_proj.push_back(pi);
+        else pitems.push_back({pi, ptiles});
         if (eq2) {
             Eq2Item ei;
             ei.G = g;
@@ -480,9 +486,14 @@ cbct_status Engine::build_tables() {
             ei.out = L->g;
             ei.cscale = j->P.c_eq2;
             ei.mode = BP_STEP;
-            heq.push_back(ei);
-            eqstart.push_back(eqtot);
-            eqtot += (long)((vol_elems(g) + EQ2_THREADS - 1) / EQ2_THREADS);
+            const long eblocks = (long)((vol_elems(g) + EQ2_THREADS - 1) / EQ2_THREADS);
+            if (eblocks >= 16 * sms) {
+                solo_eq.push_back(ei);
+            } else {
+                heq.push_back(ei);
+                eqstart.push_back(eqtot);
+                eqtot += eblocks;
+            }
         }
         const int vpl = (g.bp_vpl >= 1 && g.bp_vpl <= 4) ? g.bp_vpl : bp_default_vpl(g);
         if (!eq2) {
@@ -493,11 +504,15 @@ cbct_status Engine::build_tables() {
             bi.out = power ? L->B : L->g;
             bi.c = power ? 0.f : j->P.c;
             bi.mode = power ? BP_PLAIN : BP_STEP;
-            hbp[vpl - 1].push_back(bi);
-            bpstart[vpl - 1].push_back(bptot[vpl - 1]);
             long wt = vpl == 1 ? bp_warp_tiles<1>(g) : vpl == 2 ? bp_warp_tiles<2>(g) : vpl == 3 ? bp_warp_tiles<3>(g)
                                                                                           : bp_warp_tiles<4>(g);
-            bptot[vpl - 1] += wt;
+            if (wt >= 64 * sms) {
+                solo_bp.push_back(bi);
+            } else {
+                hbp[vpl - 1].push_back(bi);
+                bpstart[vpl - 1].push_back(bptot[vpl - 1]);
+                bptot[vpl - 1] += wt;
+            }
         }
         if (power) {
             VecItem vi;
@@ -557,6 +572,7 @@ cbct_status Engine::build_tables() {
         pg.blocks = std::max(1, std::min(65536 / (64 * pg.threads), (227 * 1024) / (pg.smem + 1024)));
     // TV sweeps: for each m, the jobs with m < M (ping-pong as in the single path)
     htv.assign(max_m, {});
+    solo_tv.assign(max_m, {});
     tvstart.assign(max_m, {});
     tvtot.assign(max_m, 0);
     for (Job *j : jobs) {
@@ -578,9 +594,13 @@ cbct_status Engine::build_tables() {
             ti.partial = L->partial + np;
             ti.clamp = (j->P.clamp_mode == 0 || last) ? 1 : 0;
             ti.e1 = (m == 0 && j->P.clamp_mode == 0) ? 1 : 0;
-            htv[m].push_back(ti);
-            tvstart[m].push_back(tvtot[m]);
-            tvtot[m] += nb;
+            if (nb >= 16 * sms) {
+                solo_tv[m].push_back(ti);
+            } else {
+                htv[m].push_back(ti);
+                tvstart[m].push_back(tvtot[m]);
+                tvtot[m] += nb;
+            }
             src = dst;
         }
         if (src != L->f) copies.push_back({L->f, src, vol_elems(L->gd) * 4});
@@ -663,50 +683,89 @@ cbct_status Engine::build_tables() {
 
 static bool attr_done[64] = {};
 
+// Blocks of `kernel` that stay resident on one SM with this block size and dynamic
+// shared memory (persistent grids are sized to exactly fill the GPU once).
+template <class K>
+static int resident_blocks(K kernel, int threads, size_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return n;
+}
+
+static long persistent_grid(long tiles, int per_sm) { return std::max(1L, std::min(tiles, (long)sm_count() * per_sm)); }
+
 // The batched stages of one tick (no host synchronisation; capturable).
 cbct_status Engine::launch_stages() {
     cudaStream_t s = stream;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+        cudaFuncSetAttribute(k_project_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, PROJ_SMEM);
+        attr_done[dev] = true;
+    }
     for (Job *j : tv_energy_jobs) {  // literal clamp mode: E1 of f_k needs its own pass
         Level *L = j->Ls[j->level];
         int nb = 0;
         ECK(launch_tv_energy(tv_args(L, j->P), L->f, L->partial + project_partials(L->gd), s, &nb), "tv energy");
     }
-    if (!hproj.empty()) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-            cudaFuncSetAttribute(k_project_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, PROJ_SMEM);
-            attr_done[dev] = true;
-        }
-        for (const ProjGroup &pg : pgroups)
-            k_project_batch<<<(unsigned)grid_for(pg.tiles, pg.blocks), pg.threads, pg.smem, s>>>(
-                d_proj + pg.first, d_pstart + pg.first, pg.count, pg.tiles);
+    // projection
+    for (const ProjItem &it : solo_proj)
+        ECK(launch_project(it.G, it.vol, it.y32, it.y16, it.out, it.partial, it.mode, s, nullptr), "projection");
+    for (const ProjGroup &pg : pgroups) {
+        const int per_sm = resident_blocks(k_project_batch, pg.threads, pg.smem);
+        k_project_batch<<<(unsigned)persistent_grid(pg.tiles, per_sm), pg.threads, pg.smem, s>>>(
+            d_proj + pg.first, d_pstart + pg.first, pg.count, pg.tiles);
         ECK(cudaGetLastError(), "batched projection");
     }
+    // adjoint (+ gradient step)
+    for (const BpItem &it : solo_bp)
+        ECK(launch_backproject(it.G, it.rs, it.fin, it.out, it.c, it.mode, s), "backprojection");
+    for (const Eq2Item &it : solo_eq)
+        ECK(launch_backproject_eq2(it.G, it.r, it.fin, it.out, it.cscale, it.mode, s), "eq2 backprojection");
     for (int v = 0; v < 4; ++v) {
         if (hbp[v].empty()) continue;
-        const long nblk = grid_for((bptotal[v] + 3) / 4, 8);
         const int n = (int)hbp[v].size();
-        if (v == 0) k_bp_batch<1><<<(unsigned)nblk, BP_THREADS, 0, s>>>(d_bp[0], d_bstart[0], n, bptotal[0]);
-        if (v == 1) k_bp_batch<2><<<(unsigned)nblk, BP_THREADS, 0, s>>>(d_bp[1], d_bstart[1], n, bptotal[1]);
-        if (v == 2) k_bp_batch<3><<<(unsigned)nblk, BP_THREADS, 0, s>>>(d_bp[2], d_bstart[2], n, bptotal[2]);
-        if (v == 3) k_bp_batch<4><<<(unsigned)nblk, BP_THREADS, 0, s>>>(d_bp[3], d_bstart[3], n, bptotal[3]);
+        const long warps = bptotal[v];
+        const int wpb = BP_THREADS / 32;
+        if (v == 0) {
+            const long nb = persistent_grid((warps + wpb - 1) / wpb, resident_blocks(k_bp_batch<1>, BP_THREADS, 0));
+            k_bp_batch<1><<<(unsigned)nb, BP_THREADS, 0, s>>>(d_bp[0], d_bstart[0], n, warps);
+        } else if (v == 1) {
+            const long nb = persistent_grid((warps + wpb - 1) / wpb, resident_blocks(k_bp_batch<2>, BP_THREADS, 0));
+            k_bp_batch<2><<<(unsigned)nb, BP_THREADS, 0, s>>>(d_bp[1], d_bstart[1], n, warps);
+        } else if (v == 2) {
+            const long nb = persistent_grid((warps + wpb - 1) / wpb, resident_blocks(k_bp_batch<3>, BP_THREADS, 0));
+            k_bp_batch<3><<<(unsigned)nb, BP_THREADS, 0, s>>>(d_bp[2], d_bstart[2], n, warps);
+        } else {
+            const long nb = persistent_grid((warps + wpb - 1) / wpb, resident_blocks(k_bp_batch<4>, BP_THREADS, 0));
+            k_bp_batch<4><<<(unsigned)nb, BP_THREADS, 0, s>>>(d_bp[3], d_bstart[3], n, warps);
+        }
         ECK(cudaGetLastError(), "batched backprojection");
     }
     if (!heq.empty()) {
-        k_eq2_batch<<<(unsigned)grid_for(eqtotal, 8), EQ2_THREADS, 0, s>>>(d_eq, d_eqstart, (int)heq.size(), eqtotal);
+        const long nb = persistent_grid(eqtotal, resident_blocks(k_eq2_batch, EQ2_THREADS, 0));
+        k_eq2_batch<<<(unsigned)nb, EQ2_THREADS, 0, s>>>(d_eq, d_eqstart, (int)heq.size(), eqtotal);
         ECK(cudaGetLastError(), "batched eq2 backprojection");
     }
     if (!hdot.empty()) {
         const int n = (int)hdot.size();
-        k_dot_batch<<<(unsigned)grid_for(dtotal, 8), 256, 0, s>>>(d_dot, d_dstart, n, dtotal);
+        k_dot_batch<<<(unsigned)persistent_grid(dtotal, 8), 256, 0, s>>>(d_dot, d_dstart, n, dtotal);
         k_pfin_batch<<<(unsigned)n, 256, 0, s>>>(d_dot);
-        k_scale_batch<<<(unsigned)grid_for(dtotal, 8), 256, 0, s>>>(d_dot, d_dstart, n, dtotal);
+        k_scale_batch<<<(unsigned)persistent_grid(dtotal, 8), 256, 0, s>>>(d_dot, d_dstart, n, dtotal);
         ECK(cudaGetLastError(), "batched power iteration");
     }
+    // TV prox sweeps
+    const int tv_per_sm = resident_blocks(k_tv_batch, TV_THREADS, 0);
     for (int m = 0; m < max_m; ++m) {
-        k_tv_batch<<<(unsigned)grid_for(tvtot[m], 8), TV_THREADS, 0, s>>>(d_tv[m], d_tstart[m], (int)htv[m].size(),
-                                                                       tvtot[m]);
+        for (const TvItem &it : solo_tv[m])
+            ECK(launch_tv_sweep(it.A, it.fin, it.g, it.fout, it.clamp != 0, it.e1 ? it.partial : nullptr, s, nullptr),
+                "tv sweep");
+        if (htv[m].empty()) continue;
+        k_tv_batch<<<(unsigned)persistent_grid(tvtot[m], tv_per_sm), TV_THREADS, 0, s>>>(d_tv[m], d_tstart[m],
+                                                                                         (int)htv[m].size(), tvtot[m]);
         ECK(cudaGetLastError(), "batched tv sweep");
     }
     for (const auto &c : copies) ECK(cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToDevice, s), "copy");

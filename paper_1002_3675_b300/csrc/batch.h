@@ -74,6 +74,11 @@ class Engine {
     };
     std::vector<ProjGroup> pgroups;
     std::vector<ProjItem> hproj;
+    // stages that fill the GPU by themselves: their own single-request launches
+    std::vector<ProjItem> solo_proj;
+    std::vector<BpItem> solo_bp;
+    std::vector<Eq2Item> solo_eq;
+    std::vector<std::vector<TvItem>> solo_tv;
     std::vector<BpItem> hbp[4];
     std::vector<Eq2Item> heq;
     std::vector<VecItem> hdot;
