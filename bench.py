@@ -23,6 +23,8 @@ Two serving modes print their own line (reconstructions/s):
   the one-at-a-time capacity and go through the continuous-batching server; latency
   percentiles are compared with a one-at-a-time FIFO queue fed the same arrival times
   and the measured per-request service times.
+* ``--mode vcycle``: V-cycles (mg_cycle 1) against the cascade on the workload: time
+  per reconstruction and the energy of Eq. 1 each reaches.
 """
 from __future__ import annotations
 
@@ -507,6 +509,52 @@ def run_serve(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_vcycle(args, world, rank, local):
+    """V-cycles against the cascade on the same workload: time and the energy of Eq. 1
+    each reaches (float64 energies from the library)."""
+    import torch
+
+    from paper_1002_3675_b300 import cbct
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = synth.CONFIGS[args.workload]
+    case = synth.make_case(args.workload)
+    G = cbct.cbct_geometry_create(case["geom"])
+    levels, iters, mu = cfg["levels"], cfg["iters"], cfg["mu"]
+    Y = torch.tensor(np.asarray(case["Y"], dtype=np.float32), device=dev)
+    f = torch.empty((cfg["vol"][2], cfg["vol"][1], cfg["vol"][0]), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    eps = 2e-5 / min(case["geom"]["hx"], case["geom"]["hy"], case["geom"]["hz"])
+    runs = {"vcycle": dict(iters=args.cycles, mg_cycle=1, mg_pre=2, mg_post=2, mg_coarse=10),
+            "cascade": dict(iters=iters)}
+    out = {}
+    for name, kw in runs.items():
+        for _ in range(args.warmup):
+            cbct.cbct_reconstruct(G, Y, mu, levels=levels, f_out=f, reuse_lambda=True, **kw)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cbct.cbct_reconstruct(G, Y, mu, levels=levels, f_out=f, reuse_lambda=True, **kw)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        E = cbct.cbct_energy(G, Y, f, mu, eps)
+        out[name] = {"ms": statistics.median(ms), "energy": float(E[0]), **kw}
+    if rank == 0:
+        v = out["vcycle"]
+        line = {"mode": "vcycle", "metric": "V-cycles/s", "value": args.cycles / (v["ms"] / 1e3), "unit": "cycle/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": v["ms"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded ellipsoid phantom, analytic line integrals, Poisson/log noise)",
+                "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}",
+                           "beta": "auto per level, lambda cached across steps"},
+                "vcycle": v, "cascade": out["cascade"]}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -515,7 +563,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="medium", choices=sorted(WORKLOAD_TEXT))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve"])
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "vcycle"])
+    ap.add_argument("--cycles", type=int, default=10, help="vcycle: V-cycles per step")
     ap.add_argument("--tv-mode", type=int, default=0, choices=[0, 1], help="E1: 0 isotropic, 1 anisotropic")
     ap.add_argument("--adjoint-mode", type=int, default=0, choices=[0, 1],
                     help="step-1 adjoint: 0 exact transpose, 1 Eq. 2 interpolation")
@@ -531,6 +580,8 @@ def main():
         run_batch(args, world, rank, local)
     elif args.mode == "serve":
         run_serve(args, world, rank, local)
+    elif args.mode == "vcycle":
+        run_vcycle(args, world, rank, local)
     else:
         run_gpu(args, world, rank, local)
     if world > 1:
