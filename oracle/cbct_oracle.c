@@ -24,7 +24,7 @@
  *   - E1 (Eq. 1) is the isotropic TV with forward differences, Neumann boundary,
  *     smoothed as sqrt(|grad f|^2 + eps^2) (tv_mode 0).  tv_mode 1 is the anisotropic
  *     reading of the l1 norm of the gradient, sum_d sqrt((D_d f)^2 + eps^2).
- *   - step 2 of Algorithm A1 ("simple gradient descent") is projected gradient on
+ *   - step 2 of Algorithm A1 (a plain gradient descent in the paper) is projected gradient on
  *     TV_eps(f) + beta/2 |f - g|^2 over f >= 0 from f0 = f_k, step 1/(beta + L_TV),
  *     L_TV = (4/eps) sum_d h_d^-2; clamp_mode 1 instead descends from g without the
  *     bound and clamps afterwards (step 3 taken literally).

@@ -1,7 +1,7 @@
 """Scan geometries, ellipsoid phantoms, analytic line integrals and noise.
 
-Geometry convention (the paper states none; Sec. "problem statement", around Eq. 1,
-only says that P^theta projects f onto an imager at angle theta):
+Geometry convention (the paper fixes none; the text introducing Eq. 1 defines P^theta
+only as the cone-beam projection onto the imager at angle theta):
 
 * millimetres throughout; the rotation axis is z and the volume is centred on the
   origin.  Voxel (i, j, k) has centre ((i - (nx-1)/2) hx, (j - (ny-1)/2) hy,
@@ -43,9 +43,8 @@ __all__ = [
 
 
 # ----------------------------------------------------------------------------------
-# Workload definitions.  Sizes are those of the five benchmark configurations; mu is
-# an input of the method ("chosen manually", Sec. "problem statement") frozen per
-# configuration.
+# Workload definitions.  mu weighs E2 against E1 in Eq. 1; the paper sets it by hand
+# for image quality, so each workload freezes one value.
 # ----------------------------------------------------------------------------------
 CONFIGS = {
     # 64^3 at 4 mm, 20 views of 64x48 at 8 mm, noise-free, single grid, 20 iterations
