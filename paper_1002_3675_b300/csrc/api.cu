@@ -65,6 +65,7 @@ TvArgs tv_args(const Level *L, const SolveParams &P) {
     a.beta = P.beta;
     a.eps2 = P.eps2;
     a.aniso = P.tv_mode;
+    a.jc = tv_rows_per_tile(a.nx, a.ny, a.nz);
     return a;
 }
 

@@ -535,7 +535,7 @@ cbct_status Engine::build_tables() {
             ei.pe2 = L->partial;
             ei.n2 = (int)np;
             ei.pe1 = L->partial + np;
-            ei.n1 = (int)tv_partials(g.nx, g.ny, g.nz);
+            ei.n1 = (int)(j->P.clamp_mode == 1 ? tv_energy_partials(g.nx, g.ny, g.nz) : tv_partials(g.nx, g.ny, g.nz));
             ei.inv_nv = j->P.inv_nv;
             ei.mu_over_nr = j->P.mu_over_nr;
             ei.trace = j->G->dtrace;
@@ -580,7 +580,7 @@ cbct_status Engine::build_tables() {
         Level *L = j->Ls[j->level];
         const TvArgs ta = tv_args(L, j->P);
         const float *src = j->P.clamp_mode == 0 ? L->f : L->g;
-        const long nb = (long)tv_partials(L->nx, L->ny, L->nz);
+        const long nb = (long)tv_blocks(L->nx, L->ny, L->nz);
         const size_t np = project_partials(L->gd);
         for (int m = 0; m < j->P.M; ++m) {
             const bool last = m == j->P.M - 1;

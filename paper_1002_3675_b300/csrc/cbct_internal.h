@@ -144,10 +144,20 @@ struct TvArgs {
     float ihx, ihy, ihz;     // 1/h
     float s, beta, eps2;
     int aniso;               // 0: isotropic E1, 1: anisotropic E1
+    int jc;                  // rows per warp tile of the sweep (tv_rows_per_tile; 0: per voxel)
 };
+// Rows per warp tile of the TV sweep: walks of 16 rows when that still gives at least
+// 8192 warp tiles (measured on B300: 1.3-1.5x faster than one thread per voxel from
+// 256x256x48 up); 0 selects the one-thread-per-voxel form, faster for smaller volumes.
+// A function of the sizes alone, so every launch of a level uses the same tiles.
+__host__ __device__ __forceinline__ int tv_rows_per_tile(int nx, int ny, int nz) {
+    return (long)nx * ((ny + 15) / 16) * ((nz + 31) / 32) >= 8192 ? 16 : 0;
+}
 cudaError_t launch_tv_sweep(const TvArgs &a, const float *fin, const float *g, float *fout, bool clamp,
                             double *partial_e1, cudaStream_t s, int *nblocks_out);
-size_t tv_partials(int nx, int ny, int nz);
+size_t tv_partials(int nx, int ny, int nz);         // E1 partials written by a sweep
+size_t tv_blocks(int nx, int ny, int nz);           // blocks of one sweep launch
+size_t tv_energy_partials(int nx, int ny, int nz);  // partials written by launch_tv_energy
 
 // layout changes
 cudaError_t launch_vol_to_internal(const float *api, float *in, int nx, int ny, int nz, cudaStream_t s);

@@ -102,7 +102,7 @@ __global__ void k_energy_grad(TvArgs A, const float *__restrict__ f, const float
     const size_t n = (size_t)A.nx * A.ny * A.nz;
     for (size_t o = grid_stride_start(); o < n; o += grid_stride()) {
         float unused = 0.f;
-        const float div = tv_div<false>(A, f, o, unused);
+        const float div = A.aniso ? tv_div<false, true>(A, f, o, unused) : tv_div<false, false>(A, f, o, unused);
         float gr = __fmul_rn(__fmaf_rn(gamma, bp[o], div), inv_nv);
         if (lin) gr = __fsub_rn(gr, lin[o]);
         out[o] = gr;

@@ -3,11 +3,23 @@
 
 namespace cbct {
 
-template <bool CLAMP, bool E1>
+template <bool CLAMP, bool E1, bool ANISO, bool WARP>
 __global__ void __launch_bounds__(TV_THREADS)
 k_tv_sweep(TvArgs A, const float *__restrict__ fin, const float *__restrict__ g, float *__restrict__ fout,
            double *__restrict__ partial) {
-    tv_block<CLAMP, E1>(A, fin, g, fout, partial, blockIdx.x);
+    tv_block_t<CLAMP, E1, ANISO, WARP>(A, fin, g, fout, partial, blockIdx.x);
+}
+
+template <bool CLAMP, bool E1>
+static void launch_sweep(const TvArgs &a, dim3 grid, const float *fin, const float *g, float *fout, double *p,
+                         cudaStream_t s) {
+    if (a.aniso) {
+        if (a.jc) k_tv_sweep<CLAMP, E1, true, true><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p);
+        else k_tv_sweep<CLAMP, E1, true, false><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p);
+    } else {
+        if (a.jc) k_tv_sweep<CLAMP, E1, false, true><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p);
+        else k_tv_sweep<CLAMP, E1, false, false><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p);
+    }
 }
 
 // E1 alone: float64 partial sums of |grad f|_eps.
@@ -44,26 +56,30 @@ k_tv_energy(TvArgs A, const float *__restrict__ fin, double *__restrict__ partia
     }
 }
 
-size_t tv_partials(int nx, int ny, int nz) { return ((size_t)nx * ny * nz + TV_THREADS - 1) / TV_THREADS; }
+size_t tv_partials(int nx, int ny, int nz) {
+    const long wt = tv_warp_tiles(nx, ny, nz);
+    return (size_t)(tv_rows_per_tile(nx, ny, nz) == 0 ? wt / TV_WARPS : wt);
+}
+size_t tv_blocks(int nx, int ny, int nz) { return (size_t)((tv_warp_tiles(nx, ny, nz) + TV_WARPS - 1) / TV_WARPS); }
+size_t tv_energy_partials(int nx, int ny, int nz) { return ((size_t)nx * ny * nz + TV_THREADS - 1) / TV_THREADS; }
 
 cudaError_t launch_tv_sweep(const TvArgs &a, const float *fin, const float *g, float *fout, bool clamp,
                             double *partial_e1, cudaStream_t s, int *nblocks_out) {
-    const size_t nb = tv_partials(a.nx, a.ny, a.nz);
-    if (nblocks_out) *nblocks_out = (int)nb;
-    dim3 grid((unsigned)nb), block(TV_THREADS);
+    if (nblocks_out) *nblocks_out = (int)tv_partials(a.nx, a.ny, a.nz);
+    dim3 grid((unsigned)tv_blocks(a.nx, a.ny, a.nz)), block(TV_THREADS);
     if (clamp) {
-        if (partial_e1) k_tv_sweep<true, true><<<grid, block, 0, s>>>(a, fin, g, fout, partial_e1);
-        else k_tv_sweep<true, false><<<grid, block, 0, s>>>(a, fin, g, fout, nullptr);
+        if (partial_e1) launch_sweep<true, true>(a, grid, fin, g, fout, partial_e1, s);
+        else launch_sweep<true, false>(a, grid, fin, g, fout, nullptr, s);
     } else {
-        if (partial_e1) k_tv_sweep<false, true><<<grid, block, 0, s>>>(a, fin, g, fout, partial_e1);
-        else k_tv_sweep<false, false><<<grid, block, 0, s>>>(a, fin, g, fout, nullptr);
+        if (partial_e1) launch_sweep<false, true>(a, grid, fin, g, fout, partial_e1, s);
+        else launch_sweep<false, false>(a, grid, fin, g, fout, nullptr, s);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_tv_energy(const TvArgs &a, const float *f, double *partial, cudaStream_t s,
                              int *nblocks_out) {
-    const size_t nb = tv_partials(a.nx, a.ny, a.nz);
+    const size_t nb = tv_energy_partials(a.nx, a.ny, a.nz);
     if (nblocks_out) *nblocks_out = (int)nb;
     k_tv_energy<<<(unsigned)nb, TV_THREADS, 0, s>>>(a, f, partial);
     return cudaGetLastError();

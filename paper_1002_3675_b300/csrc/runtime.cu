@@ -251,7 +251,8 @@ cbct_status ensure_workspace(Level *L, bool need_half) {
     if (!L->rs && (st = dmalloc((void **)&L->rs, nr * 4, "residual")) != CBCT_OK) return st;
     if (!L->Y && (st = dmalloc((void **)&L->Y, nr * 4, "data")) != CBCT_OK) return st;
     if (need_half && !L->Yh && (st = dmalloc((void **)&L->Yh, nr * 2, "half data")) != CBCT_OK) return st;
-    size_t need = project_partials(L->gd) + tv_partials(L->nx, L->ny, L->nz);
+    size_t need = project_partials(L->gd) +
+                  std::max(tv_partials(L->nx, L->ny, L->nz), tv_energy_partials(L->nx, L->ny, L->nz));
     size_t dp = 2 * ((nvox + 255) / 256) + 16;
     if (dp > need) need = dp;
     need += 64;

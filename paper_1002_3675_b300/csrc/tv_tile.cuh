@@ -23,7 +23,7 @@ constexpr int TV_THREADS = 256;
 // grad TV_eps at voxel idx (internal layout) and, if E1, the voxel's term of TV_eps
 // itself (|grad f|_eps, or the sum over the axes in the anisotropic reading).  Shared
 // by the prox sweep and the energy gradient of the multigrid cycle.
-template <bool E1>
+template <bool E1, bool ANISO>
 __device__ __forceinline__ float tv_div(const TvArgs &A, const float *__restrict__ fin, const size_t idx, float &e1) {
     const int k = (int)(idx % A.nz);
     const size_t t = idx / A.nz;
@@ -39,7 +39,7 @@ __device__ __forceinline__ float tv_div(const TvArgs &A, const float *__restrict
     const float gy = __fmul_rn(__fsub_rn(yp ? __ldg(fin + idx + sy) : f0, f0), A.ihy);
     const float gz = __fmul_rn(__fsub_rn(zp ? __ldg(fin + idx + 1) : f0, f0), A.ihz);
     float div;
-    if (A.aniso) {
+    if (ANISO) {
         // each axis smoothed on its own: p_d = D_d f / sqrt((D_d f)^2 + eps^2)
         const float qx = __fmaf_rn(gx, gx, A.eps2), qy = __fmaf_rn(gy, gy, A.eps2), qz = __fmaf_rn(gz, gz, A.eps2);
         const float rx = rsqrtf(qx), ry = rsqrtf(qy), rz = rsqrtf(qz);
@@ -94,33 +94,184 @@ __device__ __forceinline__ float tv_div(const TvArgs &A, const float *__restrict
     return div;
 }
 
-// One block of TV_THREADS voxels (block index blk).  Shared by the single-request
-// and batched kernels.
-template <bool CLAMP, bool E1>
-__device__ __forceinline__ void tv_block(const TvArgs &A, const float *__restrict__ fin, const float *__restrict__ g,
-                                         float *__restrict__ fout, double *__restrict__ partial, const long blk) {
+// Warp tile of the sweep: lanes are 32 consecutive z-voxels of the column (i, j) and
+// the warp walks j over A.jc rows (tv_rows_per_tile).  Every voxel gets exactly the arithmetic above
+// (same expressions, same order), but the terms shared between neighbours are not
+// recomputed: the p_y term at (i, j-1) is the previous row's own term, the p_z term
+// at (i, j, k-1) is the lower lane's own term (lane 0 of a tile that does not start
+// at k = 0 computes it), and f(i, j, k), f(i-1, j, k) come from the previous row's
+// loads.  Each tile writes one float64 partial of the E1 terms of its voxels
+// (float32 along the rows, then over the lanes).
+constexpr int TV_WARPS = TV_THREADS / 32;
+
+// Warp tiles of a sweep (row walks), or, for the per-voxel form, 8 per block of
+// TV_THREADS voxels; E1 partials: one per warp tile, or one per block.
+__host__ __device__ __forceinline__ long tv_warp_tiles(int nx, int ny, int nz) {
+    const int jc = tv_rows_per_tile(nx, ny, nz);
+    if (jc == 0) return TV_WARPS * (((long)nx * ny * nz + TV_THREADS - 1) / TV_THREADS);
+    return (long)nx * ((ny + jc - 1) / jc) * ((nz + 31) / 32);
+}
+
+// own term of voxel (i, j, k) from its value c and its +x, +y, +z neighbours (the
+// neighbour equals c where the difference is zero): the py/pz pieces D_d f * w_d, the
+// -(sum_d p_d / h_d) part of the divergence and the voxel's E1 term
+struct TvOwn {
+    float py, pz, div, e1;
+};
+template <bool E1, bool ANISO>
+__device__ __forceinline__ TvOwn tv_own(const TvArgs &A, float c, float fxp, float fyp, float fzp) {
+    TvOwn o;
+    const float gx = __fmul_rn(__fsub_rn(fxp, c), A.ihx);
+    const float gy = __fmul_rn(__fsub_rn(fyp, c), A.ihy);
+    const float gz = __fmul_rn(__fsub_rn(fzp, c), A.ihz);
+    o.e1 = 0.f;
+    if (ANISO) {
+        const float qx = __fmaf_rn(gx, gx, A.eps2), qy = __fmaf_rn(gy, gy, A.eps2), qz = __fmaf_rn(gz, gz, A.eps2);
+        const float rx = rsqrtf(qx), ry = rsqrtf(qy), rz = rsqrtf(qz);
+        o.py = __fmul_rn(gy, ry);
+        o.pz = __fmul_rn(gz, rz);
+        o.div = -__fmaf_rn(__fmul_rn(gx, rx), A.ihx, __fmaf_rn(o.py, A.ihy, __fmul_rn(o.pz, A.ihz)));
+        if (E1) o.e1 = __fadd_rn(__fadd_rn(__fmul_rn(qx, rx), __fmul_rn(qy, ry)), __fmul_rn(qz, rz));
+    } else {
+        const float q0 = __fmaf_rn(gx, gx, __fmaf_rn(gy, gy, __fmaf_rn(gz, gz, A.eps2)));
+        const float n0 = rsqrtf(q0);
+        o.py = __fmul_rn(gy, n0);
+        o.pz = __fmul_rn(gz, n0);
+        o.div = -__fmul_rn(__fmaf_rn(gx, A.ihx, __fmaf_rn(gy, A.ihy, __fmul_rn(gz, A.ihz))), n0);
+        if (E1) o.e1 = __fmul_rn(q0, n0);
+    }
+    return o;
+}
+
+// p_x piece of voxel (i-1, j, k) (value m) as the voxel (i, j, k) (value c) sees it
+template <bool ANISO>
+__device__ __forceinline__ float tv_px_minus(const TvArgs &A, float c, float m, float myp, float mzp) {
+    const float ax = __fmul_rn(__fsub_rn(c, m), A.ihx);
+    if (ANISO) return __fmul_rn(ax, rsqrtf(__fmaf_rn(ax, ax, A.eps2)));
+    const float ay = __fmul_rn(__fsub_rn(myp, m), A.ihy);
+    const float az = __fmul_rn(__fsub_rn(mzp, m), A.ihz);
+    return __fmul_rn(ax, rsqrtf(__fmaf_rn(ax, ax, __fmaf_rn(ay, ay, __fmaf_rn(az, az, A.eps2)))));
+}
+
+template <bool CLAMP, bool E1, bool ANISO>
+__device__ __forceinline__ void tv_warp(const TvArgs &A, const float *__restrict__ fin, const float *__restrict__ g,
+                                        float *__restrict__ fout, double *__restrict__ partial, const long wtile) {
+    const int lane = threadIdx.x & 31;
+    const int nkb = (A.nz + 31) >> 5, njc = (A.ny + A.jc - 1) / A.jc;
+    const int kb = (int)(wtile % nkb);
+    const long tt = wtile / nkb;
+    const int jc = (int)(tt % njc), i = (int)(tt / njc);
+    const int k = kb * 32 + lane;
+    const bool kin = k < A.nz;
+    const int kq = kin ? k : A.nz - 1;               // idle lanes read a valid address
+    const int j0 = jc * A.jc, j1 = min(j0 + A.jc, A.ny);
+    const size_t sx = (size_t)A.ny * A.nz, sy = A.nz;
+    const bool xp = i < A.nx - 1, xm = i > 0, zp = kq < A.nz - 1, zm = kq > 0;
+    const bool halo = lane == 0 && zm;               // p_z at k-1 is not in this tile
+    size_t o = ((size_t)i * A.ny + j0) * A.nz + kq;  // (i, j, k)
+    float e1 = 0.f;
+    float c = __ldg(fin + o);                        // f(i, j, k)
+    float m = xm ? __ldg(fin + o - sx) : 0.f;        // f(i-1, j, k)
+    float py_prev = 0.f;                             // p_y piece of (i, j-1, k)
+    if (j0 > 0) {
+        const float b = __ldg(fin + o - sy);
+        const float bxp = xp ? __ldg(fin + o - sy + sx) : b;
+        const float bzp = zp ? __ldg(fin + o - sy + 1) : b;
+        py_prev = tv_own<false, ANISO>(A, b, bxp, c, bzp).py;
+    }
+#pragma unroll 1
+    for (int j = j0; j < j1; ++j) {
+        const bool yp = j < A.ny - 1;
+        const float fyp = yp ? __ldg(fin + o + sy) : c;
+        const float fxp = xp ? __ldg(fin + o + sx) : c;
+        const float fzp = zp ? __ldg(fin + o + 1) : c;
+        const TvOwn own = tv_own<E1, ANISO>(A, c, fxp, fyp, fzp);
+        float div = own.div;
+        float myp = 0.f;
+        if (xm) {
+            myp = yp ? __ldg(fin + o - sx + sy) : m;
+            const float mzp = zp ? __ldg(fin + o - sx + 1) : m;
+            div = __fmaf_rn(tv_px_minus<ANISO>(A, c, m, myp, mzp), A.ihx, div);
+        }
+        if (j > 0) div = __fmaf_rn(py_prev, A.ihy, div);
+        float pz_lo = __shfl_up_sync(0xffffffffu, own.pz, 1);
+        if (halo) {  // own term of (i, j, k-1)
+            const float d = __ldg(fin + o - 1);
+            const float dxp = xp ? __ldg(fin + o - 1 + sx) : d;
+            const float dyp = yp ? __ldg(fin + o - 1 + sy) : d;
+            pz_lo = tv_own<false, ANISO>(A, d, dxp, dyp, c).pz;
+        }
+        if (zm) div = __fmaf_rn(pz_lo, A.ihz, div);
+        if (kin) {
+            const float x = __fmaf_rn(-A.s, __fmaf_rn(A.beta, __fsub_rn(c, __ldg(g + o)), div), c);
+            fout[o] = CLAMP ? fmaxf(x, 0.f) : x;
+            if (E1) e1 = __fadd_rn(e1, own.e1);
+        }
+        py_prev = own.py;
+        c = fyp;
+        m = myp;
+        o += sy;
+    }
+    if (E1) {
+        // float32 along the rows, a pairwise tree over the lanes, one float64 per tile
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) e1 += __shfl_down_sync(0xffffffffu, e1, off);
+        if (lane == 0) partial[wtile] = (double)e1;
+    }
+}
+
+// One thread per voxel (small or oddly sized volumes): the same arithmetic, one E1
+// partial per block (float32 within a warp, float64 across the warps).
+template <bool CLAMP, bool E1, bool ANISO>
+__device__ __forceinline__ void tv_voxels(const TvArgs &A, const float *__restrict__ fin, const float *__restrict__ g,
+                                          float *__restrict__ fout, double *__restrict__ partial, const long blk) {
     const size_t n = (size_t)A.nx * A.ny * A.nz;
     const size_t idx = (size_t)blk * TV_THREADS + threadIdx.x;
     float e1 = 0.f;
     if (idx < n) {
         const float f0 = __ldg(fin + idx);
-        const float div = tv_div<E1>(A, fin, idx, e1);
+        const float div = tv_div<E1, ANISO>(A, fin, idx, e1);
         const float x = __fmaf_rn(-A.s, __fmaf_rn(A.beta, __fsub_rn(f0, __ldg(g + idx)), div), f0);
         fout[idx] = CLAMP ? fmaxf(x, 0.f) : x;
     }
     if (E1) {
-        // float32 within a warp (pairwise tree), float64 across warps and blocks
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) e1 += __shfl_down_sync(0xffffffffu, e1, off);
-        __shared__ double red[TV_THREADS / 32];
+        __shared__ double red[TV_WARPS];
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)e1;
         __syncthreads();
         if (threadIdx.x == 0) {
             double s = 0.0;
 #pragma unroll
-            for (int w = 0; w < TV_THREADS / 32; ++w) s += red[w];
+            for (int w = 0; w < TV_WARPS; ++w) s += red[w];
             partial[blk] = s;
         }
+    }
+}
+
+// One block of the sweep (block index blk): TV_WARPS row-walking warp tiles (WARP), or
+// TV_THREADS voxels in the per-voxel form.
+template <bool CLAMP, bool E1, bool ANISO, bool WARP>
+__device__ __forceinline__ void tv_block_t(const TvArgs &A, const float *__restrict__ fin, const float *__restrict__ g,
+                                           float *__restrict__ fout, double *__restrict__ partial, const long blk) {
+    if (!WARP) {
+        tv_voxels<CLAMP, E1, ANISO>(A, fin, g, fout, partial, blk);
+        return;
+    }
+    const long wt = blk * TV_WARPS + (threadIdx.x >> 5);
+    if (wt < tv_warp_tiles(A.nx, A.ny, A.nz)) tv_warp<CLAMP, E1, ANISO>(A, fin, g, fout, partial, wt);
+}
+
+// The same with the reading and the form chosen at run time (batched kernels).
+template <bool CLAMP, bool E1>
+__device__ __forceinline__ void tv_block(const TvArgs &A, const float *__restrict__ fin, const float *__restrict__ g,
+                                         float *__restrict__ fout, double *__restrict__ partial, const long blk) {
+    if (A.aniso) {
+        if (A.jc) tv_block_t<CLAMP, E1, true, true>(A, fin, g, fout, partial, blk);
+        else tv_block_t<CLAMP, E1, true, false>(A, fin, g, fout, partial, blk);
+    } else {
+        if (A.jc) tv_block_t<CLAMP, E1, false, true>(A, fin, g, fout, partial, blk);
+        else tv_block_t<CLAMP, E1, false, false>(A, fin, g, fout, partial, blk);
     }
 }
 
