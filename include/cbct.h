@@ -97,6 +97,10 @@ typedef struct {
                              device time per kernel class, measured with CUDA events
                              on `stream` (synchronises at the end of the call)    */
     int *kernel_launches; /* optional host out [CBCT_NUM_KERNEL_CLASSES]          */
+    unsigned kernel_mask; /* kernel classes (bit c: class c) that kernel_ms times with
+                             events around each launch; 0 -> all.  Launches of every
+                             class are counted.  Timing fewer classes keeps the event
+                             overhead out of the others.                         */
     int reuse_lambda;     /* 1: reuse lambda_max(P^T P) of a level computed by an
                              earlier call on this geometry with the same power_iters
                              (the estimate is deterministic, so results are unchanged) */

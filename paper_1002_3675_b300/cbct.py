@@ -43,7 +43,8 @@ class Options(C.Structure):
                 ("power_iters", C.c_int), ("start_level", C.c_int), ("f_init_dev", C.c_void_p),
                 ("use_graphs", C.c_int), ("energy_trace", C.POINTER(C.c_double)),
                 ("beta_out", C.POINTER(C.c_double)), ("kernel_ms", C.POINTER(C.c_float)),
-                ("kernel_launches", C.POINTER(C.c_int)), ("reuse_lambda", C.c_int), ("tv_mode", C.c_int),
+                ("kernel_launches", C.POINTER(C.c_int)), ("kernel_mask", C.c_uint), ("reuse_lambda", C.c_int),
+                ("tv_mode", C.c_int),
                 ("adjoint_mode", C.c_int), ("mg_cycle", C.c_int), ("mg_pre", C.c_int), ("mg_post", C.c_int),
                 ("mg_coarse", C.c_int), ("mg_accepted", C.POINTER(C.c_int))]
 
@@ -275,7 +276,8 @@ def make_options(levels, *, beta=0.0, betas=None, eps=0.0, inner_iters=0, clamp_
 def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=None, *, beta=0.0,
                      betas=None, eps=0.0, inner_iters=0, clamp_mode=0, sino_fp16=False, power_iters=0,
                      f_init=None, start_level=0, use_graphs=False, trace=False, kernel_times=False,
-                     reuse_lambda=False, tv_mode=0, adjoint_mode=0, mg_cycle=0, mg_pre=0, mg_post=0, mg_coarse=0):
+                     reuse_lambda=False, tv_mode=0, adjoint_mode=0, mg_cycle=0, mg_pre=0, mg_post=0, mg_coarse=0,
+                     kernel_mask=0):
     """Returns f_out, or (f_out, info) when trace/kernel_times is requested; info holds
     'trace' [levels][iters][3] ([iters][3] after each V-cycle when mg_cycle=1),
     'betas' [levels], 'accepted' [levels] (V-cycles), 'kernel_ms'/'kernel_launches'."""
@@ -309,6 +311,7 @@ def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=N
     if kernel_times:
         o.kernel_ms = km
         o.kernel_launches = kl
+        o.kernel_mask = int(kernel_mask)
     _check(lib.cbct_reconstruct(g.handle, _ptr(Y, "Y"), g.angles.ctypes.data_as(C.POINTER(C.c_double)),
                                 len(g.angles), mu, iters, levels, C.byref(o), _ptr(f_out, "f_out"), _stream()))
     if not (trace or kernel_times):

@@ -100,20 +100,26 @@ struct Prof {
     cbct_geometry *G = nullptr;
     cudaStream_t s = 0;
     bool on = false;
-    std::vector<int> cls;
+    unsigned mask = ~0u;     // kernel classes timed with events (all launches are counted)
+    bool timing = false;     // the current launch is timed
+    std::vector<int> cls, all;
     std::vector<cudaEvent_t> a, b;
     void begin(int c) {
         if (!on) return;
+        all.push_back(c);
+        timing = (mask >> c) & 1u;
+        if (!timing) return;
         cudaEvent_t e0 = G->events.get();
         cudaEventRecord(e0, s);
         a.push_back(e0);
         cls.push_back(c);
     }
     void end() {
-        if (!on) return;
+        if (!on || !timing) return;
         cudaEvent_t e1 = G->events.get();
         cudaEventRecord(e1, s);
         b.push_back(e1);
+        timing = false;
     }
     cbct_status collect(float *ms, int *cnt) {
         if (!on) return CBCT_OK;
@@ -126,8 +132,9 @@ struct Prof {
             float t = 0.f;
             cudaEventElapsedTime(&t, a[q], b[q]);
             if (ms) ms[cls[q]] += t;
-            if (cnt) cnt[cls[q]] += 1;
         }
+        for (int c : all)
+            if (cnt) cnt[c] += 1;
         G->events.release_all();
         return CBCT_OK;
     }
@@ -834,6 +841,7 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
     prof.G = G;
     prof.s = s;
     prof.on = o.kernel_ms != nullptr || o.kernel_launches != nullptr;
+    if (o.kernel_mask) prof.mask = o.kernel_mask;
     if (prof.on) G->events.release_all();
 
     // data pyramid: finest level from the caller's stack, coarser by 2x2 binning
