@@ -10,10 +10,10 @@
 // g = f - c P^T r with c = gamma / beta.
 //
 // Work decomposition.  One warp owns 32*VPL voxels of one z-column (i, j); lane l
-// holds voxels k = base + l + 32 v, v < VPL.  Per view, the detector columns whose ray
-// plane meets the xy-cell come from a precomputed table; for each, the part of the
-// rays' horizontal parameter t inside the cell, [tlo, thi], is the same for the whole
-// z-column.
+// holds the consecutive voxels k = base + VPL l + v, v < VPL.  Per view, the detector
+// columns whose ray plane meets the xy-cell come from a precomputed table; for each,
+// the part of the rays' horizontal parameter t inside the cell, [tlo, thi], is the
+// same for the whole z-column.
 //
 // Plane sweep.  In detector-row units, a ray b sits at row b and the plane z at
 // rho_z(t) = z D / ((tS + t) dv) + cv, monotone in t.  Ray b is inside voxel k at t iff
@@ -23,7 +23,8 @@
 // t* = (z - zO_b) cot_b otherwise (at most one row per plane here).  Hence
 //   sum_b r_b len = (thi - tlo) sum_{b in [N(z_k), N(z_k+1))} r_b + P(z_k+1) - P(z_k),
 // with N(z) the rows below both ends and P(z) the partial rows' sum.  Each lane
-// evaluates the plane below its voxel and takes the plane above from its neighbour.
+// evaluates the planes below its voxels and takes the plane above its last voxel from
+// its neighbour.
 // The residual is pre-scaled by sec(phi) (3D length = t-length * sec(phi)).  Sums are
 // taken in a fixed order with no atomics, so results are deterministic.
 #include "cbct_internal.h"
@@ -55,32 +56,32 @@ __host__ __device__ __forceinline__ long bp_warp_tiles(const GeoDev &G) {
     return (long)G.nx * G.ny * ((G.nz + 32 * VPL - 1) / (32 * VPL));
 }
 
-// One warp tile (warp-uniform): z-chunk kc of xy-cell colid.  mode: BP_PLAIN writes
-// P^T rs, BP_STEP writes fin - c P^T rs.  Shared by the single-request and batched
-// kernels, so a request's result does not depend on what else is in the launch.
+// One warp tile (warp-uniform): z-chunk kc of xy-cell colid.  Lane l holds the VPL
+// consecutive voxels base + VPL l + v and evaluates the planes below them; the plane
+// above its last voxel is the next lane's first plane (the chunk's top plane for lane
+// 31).  mode: BP_PLAIN writes P^T rs, BP_STEP writes fin - c P^T rs.  Shared by the
+// single-request and batched kernels, so a request's result does not depend on what
+// else is in the launch.
 template <int VPL>
 __device__ __forceinline__ void bp_warp(const GeoDev &G, const int mode, const float *__restrict__ rs,
-                                        const float *__restrict__ fin, float *__restrict__ out, const float c,
-                                        const long wtile) {
+                                         const float *__restrict__ fin, float *__restrict__ out, const float c,
+                                         const long wtile) {
     const int lane = threadIdx.x & 31;
     const int nkc = (G.nz + 32 * VPL - 1) / (32 * VPL);
-    const long gwarp = wtile;
-    const int kc = (int)(gwarp % nkc);
-    const long colid = gwarp / nkc;
+    const int kc = (int)(wtile % nkc);
+    const long colid = wtile / nkc;
     const int j = (int)(colid % G.ny);
     const int i = (int)(colid / G.ny);
-    const int base = kc * 32 * VPL;
-
+    const int base = kc * 32 * VPL + lane * VPL;     // first voxel of this lane
     float zb[VPL], acc[VPL];
 #pragma unroll
     for (int v = 0; v < VPL; ++v) {
-        zb[v] = plane_at(base + lane + 32 * v, G.hz, G.z0);  // plane below voxel base + lane + 32 v
+        zb[v] = plane_at(base + v, G.hz, G.z0);
         acc[v] = 0.f;
     }
-    const float ztop = plane_at(base + 32 * VPL, G.hz, G.z0);  // plane above the warp's last voxel
+    const float ztop = plane_at(kc * 32 * VPL + 32 * VPL, G.hz, G.z0);
     const float xl = plane_at(i, G.hx, G.x0), xh = plane_at(i + 1, G.hx, G.x0);
     const float yl = plane_at(j, G.hy, G.y0), yh = plane_at(j + 1, G.hy, G.y0);
-
 #pragma unroll 1
     for (int ia = 0; ia < G.na; ++ia) {
         const short2 ar = G.arange[((size_t)ia * G.nx + i) * G.ny + j];
@@ -105,46 +106,39 @@ __device__ __forceinline__ void bp_warp(const GeoDev &G, const int mode, const f
             }
             if (!(thi > tlo)) continue;
             const float2 Dt = G.col[a];
-            // rows per mm of z at tlo and thi (fast division: a ~1e-4 row error only moves
-            // a row between "full" and "partial" when its crossing lies within ~1e-4 of the
-            // cell's ends, where both give the same length to that precision)
             const float q1 = __fdividef(Dt.x, Dt.y + tlo) * G.inv_dv;
             const float q2 = __fdividef(Dt.x, Dt.y + thi) * G.inv_dv;
             const float w = thi - tlo;
             const float2 *rzp = G.ray_zc + (size_t)a * G.nv;
             const float *rsp = rsv + (size_t)a * G.nv;
-            int nb[VPL];
-            float pb[VPL];
+            int nb[VPL + 1];
+            float pb[VPL + 1];
 #pragma unroll
             for (int v = 0; v < VPL; ++v) eval_plane(zb[v], q1, q2, G.cv, G.nv, tlo, thi, rzp, rsp, nb[v], pb[v]);
             int nt;
             float pt;
             eval_plane(ztop, q1, q2, G.cv, G.nv, tlo, thi, rzp, rsp, nt, pt);
+            nb[VPL] = __shfl_down_sync(0xffffffffu, nb[0], 1);
+            pb[VPL] = __shfl_down_sync(0xffffffffu, pb[0], 1);
+            if (lane == 31) {
+                nb[VPL] = nt;
+                pb[VPL] = pt;
+            }
 #pragma unroll
             for (int v = 0; v < VPL; ++v) {
-                // the plane above voxel (lane, v) is the plane below the next voxel
-                int ntop = __shfl_down_sync(0xffffffffu, nb[v], 1);
-                float ptop = __shfl_down_sync(0xffffffffu, pb[v], 1);
-                const int nn = (v + 1 < VPL) ? __shfl_sync(0xffffffffu, nb[(v + 1) % VPL], 0) : nt;
-                const float pn = (v + 1 < VPL) ? __shfl_sync(0xffffffffu, pb[(v + 1) % VPL], 0) : pt;
-                if (lane == 31) {
-                    ntop = nn;
-                    ptop = pn;
-                }
                 float full = 0.f;
-                for (int b = nb[v]; b < ntop; ++b) full += __ldg(rsp + b);
-                acc[v] += __fmaf_rn(w, full, ptop - pb[v]);
+                for (int b = nb[v]; b < nb[v + 1]; ++b) full += __ldg(rsp + b);
+                acc[v] += __fmaf_rn(w, full, pb[v + 1] - pb[v]);
             }
         }
     }
 #pragma unroll
     for (int v = 0; v < VPL; ++v) {
-        const int k = base + lane + 32 * v;
+        const int k = base + v;
         if (k >= G.nz) continue;
         const size_t o = ((size_t)i * G.ny + j) * G.nz + k;
         out[o] = (mode == BP_PLAIN) ? acc[v] : __fmaf_rn(-c, acc[v], __ldg(fin + o));
     }
 }
-
 
 }  // namespace cbct

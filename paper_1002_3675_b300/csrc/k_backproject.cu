@@ -3,8 +3,9 @@
 
 namespace cbct {
 
+// at most 51 registers per thread (48 used): 10 blocks of 128 threads per SM
 template <int MODE, int VPL>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, 5)
 k_backproject(GeoDev G, const float *__restrict__ rs, const float *__restrict__ fin,
               float *__restrict__ out, float c) {
     const long gwarp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
