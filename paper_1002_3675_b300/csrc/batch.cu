@@ -725,6 +725,8 @@ cbct_status Engine::launch_stages() {
         ECK(launch_backproject(it.G, it.rs, it.fin, it.out, it.c, it.mode, s), "backprojection");
     for (const Eq2Item &it : solo_eq)
         ECK(launch_backproject_eq2(it.G, it.r, it.fin, it.out, it.cscale, it.mode, s), "eq2 backprojection");
+    for (int v = 0; v < 4; ++v)  // column running sums the batched gathers read
+        for (const BpItem &it : hbp[v]) ECK(launch_row_prefix(it.G, it.rs, s), "row sums");
     for (int v = 0; v < 4; ++v) {
         if (hbp[v].empty()) continue;
         const int n = (int)hbp[v].size();

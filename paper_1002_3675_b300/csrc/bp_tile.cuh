@@ -22,7 +22,9 @@
 // rows below both ends of rho_z, 0 for rows above both, and the exact crossing
 // t* = (z - zO_b) cot_b otherwise (at most one row per plane here).  Hence
 //   sum_b r_b len = (thi - tlo) sum_{b in [N(z_k), N(z_k+1))} r_b + P(z_k+1) - P(z_k),
-// with N(z) the rows below both ends and P(z) the partial rows' sum.  Each lane
+// with N(z) the rows below both ends and P(z) the partial rows' sum.  The sum over
+// full rows is a difference of running sums along the detector column (kept in
+// float64 and stored as a float32 pair, so the difference keeps float32 accuracy).  Each lane
 // evaluates the planes below its voxels and takes the plane above its last voxel from
 // its neighbour.
 // The residual is pre-scaled by sec(phi) (3D length = t-length * sec(phi)).  Sums are
@@ -111,6 +113,7 @@ __device__ __forceinline__ void bp_warp(const GeoDev &G, const int mode, const f
             const float w = thi - tlo;
             const float2 *rzp = G.ray_zc + (size_t)a * G.nv;
             const float *rsp = rsv + (size_t)a * G.nv;
+            const float2 *cum = G.rowsum + ((size_t)ia * G.nu + a) * (G.nv + 1);
             int nb[VPL + 1];
             float pb[VPL + 1];
 #pragma unroll
@@ -124,11 +127,13 @@ __device__ __forceinline__ void bp_warp(const GeoDev &G, const int mode, const f
                 nb[VPL] = nt;
                 pb[VPL] = pt;
             }
+            float2 c0 = __ldg(cum + nb[0]);
 #pragma unroll
             for (int v = 0; v < VPL; ++v) {
-                float full = 0.f;
-                for (int b = nb[v]; b < nb[v + 1]; ++b) full += __ldg(rsp + b);
+                const float2 c1 = __ldg(cum + nb[v + 1]);
+                const float full = __fadd_rn(__fsub_rn(c1.x, c0.x), __fsub_rn(c1.y, c0.y));
                 acc[v] += __fmaf_rn(w, full, pb[v + 1] - pb[v]);
+                c0 = c1;
             }
         }
     }

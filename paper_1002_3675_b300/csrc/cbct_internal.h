@@ -44,6 +44,8 @@ struct GeoDev {
     const float2 *col;           // [nu]      D = |d_xy|, t_S (source-to-O distance)
     const short2 *arange;        // [na][nx][ny] first/last detector column meeting each xy-cell
     const float2 *view;          // [na]      cos, sin
+    float2 *rowsum;              // [na][nu][nv+1] running sums of the scaled residual along each
+                                 // detector column, float64 split as (hi, lo) float32 (workspace)
     // launch shapes (0 = default); none of them changes any result bit
     int proj_threads;            // projector block size (>= 32 ceil(nv/32) up to 512, multiple of 32)
     int proj_smem;               // projector dynamic shared memory, bytes (0 = default; see proj_smem_of)
@@ -128,8 +130,10 @@ cudaError_t launch_project(const GeoDev &g, const float *vol, const float *y32, 
 size_t project_partials(const GeoDev &g);
 
 enum BpMode { BP_PLAIN = 0, BP_STEP = 1 };
+// (launches the column running sums of rs into g.rowsum first)
 cudaError_t launch_backproject(const GeoDev &g, const float *rs, const float *fin, float *out, float c,
                                int mode, cudaStream_t s);
+cudaError_t launch_row_prefix(const GeoDev &g, const float *rs, cudaStream_t s);
 int project_threads(const GeoDev &g);
 
 // Eq. 2 adjoint: out = cscale * B' r (BP_PLAIN) or fin - cscale * B' r (BP_STEP), where

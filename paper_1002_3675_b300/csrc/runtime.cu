@@ -72,6 +72,7 @@ void free_level(Level *L) {
     cudaFree(L->A);
     cudaFree(L->B);
     cudaFree(L->rs);
+    cudaFree(L->gd.rowsum);
     cudaFree(L->Y);
     cudaFree(L->Yh);
     cudaFree(L->partial);
@@ -249,6 +250,10 @@ cbct_status ensure_workspace(Level *L, bool need_half) {
     if (!L->A && (st = dmalloc((void **)&L->A, nvox * 4, "volume A")) != CBCT_OK) return st;
     if (!L->B && (st = dmalloc((void **)&L->B, nvox * 4, "volume B")) != CBCT_OK) return st;
     if (!L->rs && (st = dmalloc((void **)&L->rs, nr * 4, "residual")) != CBCT_OK) return st;
+    if (!L->gd.rowsum &&
+        (st = dmalloc((void **)&L->gd.rowsum, (size_t)L->na * L->nu * (L->nv + 1) * sizeof(float2), "row sums")) !=
+            CBCT_OK)
+        return st;
     if (!L->Y && (st = dmalloc((void **)&L->Y, nr * 4, "data")) != CBCT_OK) return st;
     if (need_half && !L->Yh && (st = dmalloc((void **)&L->Yh, nr * 2, "half data")) != CBCT_OK) return st;
     size_t need = project_partials(L->gd) +
