@@ -18,7 +18,8 @@ Two serving modes print their own line (reconstructions/s):
 
 * ``--mode batch``: 16 heterogeneous requests (six volume sizes from 128^3 to
   384x384x64, 20-60 views, random start angles, 2 levels x 30 iterations), run one at
-  a time through ``cbct_reconstruct`` and together through ``cbct_reconstruct_batch``.
+  a time through ``cbct_reconstruct`` and together through ``cbct_reconstruct_batch``;
+  ``--batch-mix small --requests 32`` takes 32 requests of the small workload instead.
 * ``--mode serve``: requests (by default drawn uniformly from the medium workload and
   the large one at 20, 30 and 40 views; ``--mix batch16`` takes the 16 requests above)
   arrive as a Poisson stream at a fixed fraction of the one-at-a-time capacity and go
@@ -429,6 +430,17 @@ def _sequential(cbct, reqs, stream):
     return times
 
 
+def _small_requests(n, seed):
+    """n requests of the small workload (64^3, 20 views) with random start angles."""
+    rng = np.random.default_rng(seed)
+    cfg = synth.CONFIGS["small"]
+    out = []
+    for _ in range(n):
+        c = synth.make_case("small", theta0=float(rng.uniform(0.0, 2.0 * np.pi / cfg["n_angles"])))
+        out.append(dict(geom=c["geom"], Y=c["Y"], mu=cfg["mu"], levels=cfg["levels"], iters=cfg["iters"]))
+    return out
+
+
 def run_batch(args, world, rank, local):
     import torch
 
@@ -436,7 +448,10 @@ def run_batch(args, world, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    reqs = _upload_requests(synth.make_request_set(1003 + rank, args.requests), dev)
+    if args.batch_mix == "small":
+        reqs = _upload_requests(_small_requests(args.requests, 1005 + rank), dev)
+    else:
+        reqs = _upload_requests(synth.make_request_set(1003 + rank, args.requests), dev)
     for r in reqs:
         r["G"] = cbct.cbct_geometry_create(r["geom"])
     stream = torch.cuda.current_stream()
@@ -505,6 +520,11 @@ def run_serve(args, world, rank, local):
         order = [int(q) for q in rng.integers(0, len(base), size=n)]
         text = (f"{n} requests drawn uniformly from the medium workload and the large one at 20, 30 and 40 views "
                 f"({', '.join(names)})")
+    elif args.mix == "small":
+        base = _upload_requests(_small_requests(8, 1006 + rank), dev)
+        n = args.serve_requests
+        order = [q % len(base) for q in range(n)]
+        text = _request_text(base) + f" (8 small-workload scans); {n} arrivals cycling through them"
     else:
         base = _upload_requests(synth.make_request_set(1003 + rank, args.requests), dev)
         n = args.serve_requests
@@ -627,9 +647,11 @@ def main():
     ap.add_argument("--load", type=float, default=0.8, help="serve: arrival rate / one-at-a-time capacity")
     ap.add_argument("--slots", type=int, default=16, help="serve: slots (one per distinct scan geometry keeps all resident)")
     ap.add_argument("--budget-gb", type=int, default=150)
-    ap.add_argument("--mix", default="clinical", choices=["clinical", "batch16"],
+    ap.add_argument("--mix", default="clinical", choices=["clinical", "batch16", "small"],
                     help="serve: request mix (medium/large workloads, or the 16 heterogeneous requests)")
     ap.add_argument("--serve-requests", type=int, default=40, help="serve: arrivals")
+    ap.add_argument("--batch-mix", default="hetero", choices=["hetero", "small"],
+                    help="batch: the 16 heterogeneous requests, or --requests copies of the small workload")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
