@@ -35,7 +35,8 @@ namespace cbct {
 
 constexpr int BP_THREADS = 128;
 
-// N(z) and P(z) of one plane for detector column rzp/rsp over [tlo, thi].
+// N(z) and P(z) of one plane for detector column rzp/rsp over [tlo, thi].  At most one
+// row is partial on almost every plane, so the first one is taken without a loop.
 __device__ __forceinline__ void eval_plane(float z, float q1, float q2, float cv, int nv, float tlo, float thi,
                                            const float2 *__restrict__ rzp, const float *__restrict__ rsp,
                                            int &nmin, float &part) {
@@ -45,10 +46,15 @@ __device__ __forceinline__ void eval_plane(float z, float q1, float q2, float cv
     const int nmax = min(max((int)ceilf(hi), 0), nv);
     const bool dec = r1 > r2;  // rho falls with t: the row is below the plane before t*
     part = 0.f;
-    for (int b = nmin; b < nmax; ++b) {
-        const float2 rz = __ldg(rzp + b);
+    if (nmax > nmin) {
+        const float2 rz = __ldg(rzp + nmin);
         const float ts = fminf(fmaxf(t_cross(z, rz.x, rz.y), tlo), thi);
-        part = __fmaf_rn(__ldg(rsp + b), dec ? ts - tlo : thi - ts, part);
+        part = __fmul_rn(__ldg(rsp + nmin), dec ? ts - tlo : thi - ts);
+        for (int b = nmin + 1; b < nmax; ++b) {
+            const float2 rz2 = __ldg(rzp + b);
+            const float ts2 = fminf(fmaxf(t_cross(z, rz2.x, rz2.y), tlo), thi);
+            part = __fmaf_rn(__ldg(rsp + b), dec ? ts2 - tlo : thi - ts2, part);
+        }
     }
 }
 
