@@ -75,6 +75,23 @@ def test_batch_equals_single_requests(lib, cuda):
             assert np.array_equal(ia["betas"], ib["betas"])
 
 
+def test_batch_mixes_single_request_and_persistent_launches(lib, cuda):
+    """A request large enough to fill the GPU runs its stages as single-request
+    launches, the small ones share persistent launches; each stays bitwise equal to
+    its own cbct_reconstruct call."""
+    rng = np.random.default_rng(52)
+    big = _geom(256, 256, 64, (1, 1, 2.5), 40, 256, 192, 1.6)
+    cases = [dict(geom=big, Y=rng.uniform(0.0, 3.0, size=(40, 192, 256)).astype(np.float32), mu=5.0, levels=2,
+                  iters=3)] + _cases()[:2]
+    alone = [_alone(lib, c) for c in cases]
+    reqs = [dict(geom=lib.cbct_geometry_create(c["geom"]), Y=dev(c["Y"]), mu=c["mu"], iters=c["iters"],
+                 levels=c["levels"], trace=True) for c in cases]
+    outs, infos = lib.cbct_reconstruct_batch(reqs, use_graphs=True)
+    for (fa, ia), fb, ib in zip(alone, outs, infos):
+        assert np.array_equal(fa, host(fb))
+        assert np.array_equal(ia["trace"], ib["trace"])
+
+
 def test_batch_rejects_shared_geometry(lib):
     c = _cases()[0]
     G = lib.cbct_geometry_create(c["geom"])

@@ -339,6 +339,11 @@ def test_kernel_timing_report(lib):
     assert n["project"] == 2 * (3 + 30) and n["backproject"] == 2 * (3 + 30)
     assert n["tv"] == 2 * 3 * 10
     assert all(ms[k] > 0 for k in ("project", "backproject", "tv"))
+    # a class mask times only the chosen classes and still counts every launch
+    mask = 1 << lib.KERNEL_CLASSES.index("backproject")
+    _, m = lib.cbct_reconstruct(G, dev(case["Y"]), case["mu"], 3, 2, kernel_times=True, kernel_mask=mask)
+    assert m["kernel_launches"] == n
+    assert m["kernel_ms"]["backproject"] > 0 and m["kernel_ms"]["tv"] == 0 and m["kernel_ms"]["project"] == 0
 
 
 def test_invalid_arguments_on_device(lib):
