@@ -53,6 +53,10 @@ WORKLOAD_TEXT = {
               "x 50 FBS iterations per level",
     "large": "512x512x96 @ 0.5x0.5x2.5 mm, 40 views 512x384 @ 0.8 mm, Poisson I0=2.5e4, 3-level multigrid "
              "x 50 FBS iterations per level",
+    "large30": "512x512x96 @ 0.5x0.5x2.5 mm, 30 views 512x384 @ 0.8 mm, Poisson I0=2.5e4, 3-level multigrid "
+               "x 50 FBS iterations per level",
+    "large20": "512x512x96 @ 0.5x0.5x2.5 mm, 20 views 512x384 @ 0.8 mm, Poisson I0=2.5e4, 3-level multigrid "
+               "x 50 FBS iterations per level",
 }
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -237,7 +241,7 @@ def run_gpu(args, world, rank, local):
 
     def step(kernel_times, mask=timed_mask):
         return cbct.cbct_reconstruct(G, Y, mu, iters, levels, f_out=f, kernel_times=kernel_times, kernel_mask=mask,
-                                     tv_mode=args.tv_mode, adjoint_mode=args.adjoint_mode)
+                                     tv_mode=args.tv_mode, adjoint_mode=args.adjoint_mode, sino_fp16=args.sino_fp16)
 
     for _ in range(args.warmup):
         step(False)
@@ -375,7 +379,8 @@ def run_gpu(args, world, rank, local):
                 "stands in for the paper's NCAT/CatPhan data",
         "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "inner_iters": 10,
                    "variant": {"tv_mode": ["isotropic", "anisotropic"][args.tv_mode],
-                               "adjoint": ["exact transpose", "Eq. 2 interpolation"][args.adjoint_mode]},
+                               "adjoint": ["exact transpose", "Eq. 2 interpolation"][args.adjoint_mode],
+                               "data_storage": "float16" if args.sino_fp16 else "float32"},
                    "beta": "auto per level (30 power iterations, recomputed every step)",
                    "fbs_iterations_per_step": n_iter, "l2": "flushed between steps (256 MiB write, untimed)",
                    "parallelism": f"replicas x{world}"},
@@ -641,6 +646,7 @@ def main():
     ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "vcycle"])
     ap.add_argument("--cycles", type=int, default=10, help="vcycle: V-cycles per step")
     ap.add_argument("--tv-mode", type=int, default=0, choices=[0, 1], help="E1: 0 isotropic, 1 anisotropic")
+    ap.add_argument("--sino-fp16", action="store_true", help="keep the projection data in half precision")
     ap.add_argument("--adjoint-mode", type=int, default=0, choices=[0, 1],
                     help="step-1 adjoint: 0 exact transpose, 1 Eq. 2 interpolation")
     ap.add_argument("--requests", type=int, default=16)

@@ -19,7 +19,7 @@ import synth  # noqa: E402
 
 def main():
     out = {}
-    for name in ("small", "medium", "large"):
+    for name in ("small", "medium", "large", "large30", "large20"):
         cfg = synth.CONFIGS[name]
         g = synth.geometry_for(cfg)
         per_level = []
