@@ -29,64 +29,6 @@ namespace cbct {
 // batched kernels
 // ---------------------------------------------------------------------------------
 
-struct ProjItem {
-    GeoDev G;
-    const float *vol;
-    const float *y32;
-    const __half *y16;
-    float *out;
-    double *partial;
-    int mode;
-};
-
-struct BpItem {
-    GeoDev G;
-    const float *rs;
-    const float *fin;
-    float *out;
-    float c;
-    int mode;
-};
-
-struct Eq2Item {  // Eq. 2 adjoint + gradient step of one request
-    GeoDev G;
-    const float *r;
-    const float *fin;
-    float *out;
-    float cscale;
-    int mode;
-};
-
-struct TvItem {
-    TvArgs A;
-    const float *fin;
-    const float *g;
-    float *fout;
-    double *partial;
-    int clamp;
-    int e1;
-};
-
-struct VecItem {  // power-iteration helpers on one volume
-    const float *x;
-    const float *y;
-    float *out;
-    double *partial;
-    double *lam;
-    float *scale;
-    long n;
-    int nblk;
-};
-
-struct EnItem {
-    const double *pe2;
-    const double *pe1;
-    double *trace;
-    int *counter;
-    double inv_nv, mu_over_nr;
-    int n2, n1;
-};
-
 // largest r with start[r] <= t
 __device__ __forceinline__ int find_item(const long *__restrict__ start, int n, long t) {
     int lo = 0, hi = n - 1;
@@ -319,6 +261,8 @@ Engine::Engine(cudaStream_t s, bool graphs) : stream(s), use_graphs(graphs && s 
 Engine::~Engine() {
     reset_graph();
     cudaFree(dblob);
+    for (cudaStream_t st : side) cudaStreamDestroy(st);
+    for (cudaEvent_t e : side_events) cudaEventDestroy(e);
 }
 
 void Engine::reset_graph() {
@@ -454,6 +398,7 @@ cbct_status Engine::build_tables() {
     solo_bp.clear();
     solo_eq.clear();
     solo_tv.clear();
+    chains.clear();
     const long sms = sm_count();
     max_m = 0;
     copies.clear();
@@ -476,6 +421,60 @@ cbct_status Engine::build_tables() {
         // a stage that fills the GPU by itself runs as its own single-request launch (the
         // same tile bodies, so the same bits); the others share a persistent launch
         const long ptiles = (long)g.nu * g.na * ((g.nv + project_threads(g) - 1) / project_threads(g));
+        const int vpl0 = (g.bp_vpl >= 1 && g.bp_vpl <= 4) ? g.bp_vpl : bp_default_vpl(g);
+        const long wt0 = vpl0 == 1 ? bp_warp_tiles<1>(g) : vpl0 == 2 ? bp_warp_tiles<2>(g)
+                                                         : vpl0 == 3 ? bp_warp_tiles<3>(g) : bp_warp_tiles<4>(g);
+        const long eblocks0 = (long)((vol_elems(g) + EQ2_THREADS - 1) / EQ2_THREADS);
+        const bool indep = ptiles >= 8 * sms && (eq2 ? eblocks0 >= 16 * sms : wt0 >= 64 * sms) &&
+                           (power || (long)tv_blocks(g.nx, g.ny, g.nz) >= 16 * sms);
+        if (indep) {  // the whole tick of this job on a side stream
+            Chain ch;
+            ch.job = j;
+            ch.power = power;
+            ch.eq2 = eq2;
+            ch.proj = pi;
+            if (eq2) {
+                ch.eq.G = g;
+                ch.eq.r = L->rs;
+                ch.eq.fin = L->f;
+                ch.eq.out = L->g;
+                ch.eq.cscale = j->P.c_eq2;
+                ch.eq.mode = BP_STEP;
+            } else {
+                ch.bp.G = g;
+                ch.bp.rs = L->rs;
+                ch.bp.fin = power ? nullptr : L->f;
+                ch.bp.out = power ? L->B : L->g;
+                ch.bp.c = power ? 0.f : j->P.c;
+                ch.bp.mode = power ? BP_PLAIN : BP_STEP;
+            }
+            if (power) {
+                ch.vec.x = L->A;
+                ch.vec.y = L->B;
+                ch.vec.out = L->A;
+                ch.vec.partial = L->partial;
+                ch.vec.lam = j->G->dscalars;
+                ch.vec.scale = (float *)(j->G->dscalars + 1);
+                ch.vec.n = (long)vol_elems(g);
+                ch.vec.nblk = (int)((ch.vec.n + 255) / 256);
+            } else {
+                max_m = std::max(max_m, j->P.M);
+                const size_t np = project_partials(g);
+                EnItem ei;
+                ei.pe2 = L->partial;
+                ei.n2 = (int)np;
+                ei.pe1 = L->partial + np;
+                ei.n1 = (int)(j->P.clamp_mode == 1 ? tv_energy_partials(g.nx, g.ny, g.nz)
+                                                   : tv_partials(g.nx, g.ny, g.nz));
+                ei.inv_nv = j->P.inv_nv;
+                ei.mu_over_nr = j->P.mu_over_nr;
+                ei.trace = j->G->dtrace;
+                ei.counter = j->G->dcounter;
+                hen.push_back(ei);
+            }
+            chains.push_back(ch);
+            continue;
+        }
         if (ptiles >= 8 * sms) solo_proj.push_back(pi);
         else pitems.push_back({pi, ptiles});
         if (eq2) {
@@ -530,7 +529,7 @@ cbct_status Engine::build_tables() {
         } else {
             max_m = std::max(max_m, j->P.M);
             if (j->P.clamp_mode == 1) tv_energy_jobs.push_back(j);
-            const size_t np = project_partials(g);
+            const size_t np = project_partials(g);  // (jobs on side streams took the branch above)
             EnItem ei;
             ei.pe2 = L->partial;
             ei.n2 = (int)np;
@@ -579,6 +578,9 @@ cbct_status Engine::build_tables() {
         if (j->phase != PH_FBS) continue;
         Level *L = j->Ls[j->level];
         const TvArgs ta = tv_args(L, j->P);
+        Chain *chain = nullptr;
+        for (Chain &ch : chains)
+            if (ch.job == j) chain = &ch;
         const float *src = j->P.clamp_mode == 0 ? L->f : L->g;
         const long nb = (long)tv_blocks(L->nx, L->ny, L->nz);
         const size_t np = project_partials(L->gd);
@@ -594,7 +596,9 @@ cbct_status Engine::build_tables() {
             ti.partial = L->partial + np;
             ti.clamp = (j->P.clamp_mode == 0 || last) ? 1 : 0;
             ti.e1 = (m == 0 && j->P.clamp_mode == 0) ? 1 : 0;
-            if (nb >= 16 * sms) {
+            if (chain) {
+                chain->tv.push_back(ti);
+            } else if (nb >= 16 * sms) {
                 solo_tv[m].push_back(ti);
             } else {
                 htv[m].push_back(ti);
@@ -603,7 +607,7 @@ cbct_status Engine::build_tables() {
             }
             src = dst;
         }
-        if (src != L->f) copies.push_back({L->f, src, vol_elems(L->gd) * 4});
+        if (src != L->f) (chain ? chain->copies : copies).push_back({L->f, src, vol_elems(L->gd) * 4});
     }
     dtotal = dtot;
     for (int v = 0; v < 4; ++v) bptotal[v] = bptot[v];
@@ -678,6 +682,7 @@ cbct_status Engine::build_tables() {
         d_tstart[m] = (long *)(b + o_tst[m]);
     }
     d_en = (EnItem *)(b + o_en);
+    if (!chains.empty()) EST(ensure_side(chains.size()));
     return CBCT_OK;
 }
 
@@ -697,9 +702,60 @@ static int resident_blocks(K kernel, int threads, size_t smem) {
 
 static long persistent_grid(long tiles, int per_sm) { return std::max(1L, std::min(tiles, (long)sm_count() * per_sm)); }
 
+cbct_status Engine::ensure_side(size_t n) {
+    while (side.size() < std::min<size_t>(n, 8)) {
+        cudaStream_t st = nullptr;
+        ECK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "side stream");
+        side.push_back(st);
+    }
+    while (side_events.size() < n + 1) {
+        cudaEvent_t e = nullptr;
+        ECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "side event");
+        side_events.push_back(e);
+    }
+    return CBCT_OK;
+}
+
+// One job's whole tick (every stage its own single-request launch) on stream s.
+static cbct_status launch_chain(const Engine::Chain &c, cudaStream_t s) {
+    const Job *j = c.job;
+    if (!c.power && j->P.clamp_mode == 1) {  // literal clamp mode: E1 of f_k needs its own pass
+        Level *L = j->Ls[j->level];
+        int nb = 0;
+        ECK(launch_tv_energy(tv_args(L, j->P), L->f, L->partial + project_partials(L->gd), s, &nb), "tv energy");
+    }
+    ECK(launch_project(c.proj.G, c.proj.vol, c.proj.y32, c.proj.y16, c.proj.out, c.proj.partial, c.proj.mode, s,
+                       nullptr),
+        "projection");
+    if (c.eq2)
+        ECK(launch_backproject_eq2(c.eq.G, c.eq.r, c.eq.fin, c.eq.out, c.eq.cscale, c.eq.mode, s), "eq2 backprojection");
+    else
+        ECK(launch_backproject(c.bp.G, c.bp.rs, c.bp.fin, c.bp.out, c.bp.c, c.bp.mode, s), "backprojection");
+    if (c.power) {  // the same partition and trees as the batched helpers
+        int nb = 0;
+        ECK(launch_dot2(c.vec.x, c.vec.y, (size_t)c.vec.n, c.vec.partial, s, &nb), "power dot");
+        ECK(launch_power_finalize(c.vec.partial, nb, c.vec.lam, c.vec.scale, s), "power finalize");
+        ECK(launch_scale(c.vec.y, c.vec.scale, (float *)c.vec.out, (size_t)c.vec.n, s), "power scale");
+    }
+    for (const TvItem &it : c.tv)
+        ECK(launch_tv_sweep(it.A, it.fin, it.g, it.fout, it.clamp != 0, it.e1 ? it.partial : nullptr, s, nullptr),
+            "tv sweep");
+    for (const auto &cp : c.copies) ECK(cudaMemcpyAsync(cp.dst, cp.src, cp.bytes, cudaMemcpyDeviceToDevice, s), "copy");
+    return CBCT_OK;
+}
+
 // The batched stages of one tick (no host synchronisation; capturable).
 cbct_status Engine::launch_stages() {
     cudaStream_t s = stream;
+    // jobs that fill the GPU by themselves: forked onto side streams
+    if (!chains.empty()) {
+        ECK(cudaEventRecord(side_events[0], s), "fork");
+        for (size_t q = 0; q < chains.size(); ++q) {
+            cudaStream_t ss = side[q % side.size()];
+            ECK(cudaStreamWaitEvent(ss, side_events[0], 0), "fork wait");
+            EST(launch_chain(chains[q], ss));
+        }
+    }
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr_done[dev]) {
@@ -771,6 +827,11 @@ cbct_status Engine::launch_stages() {
         ECK(cudaGetLastError(), "batched tv sweep");
     }
     for (const auto &c : copies) ECK(cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToDevice, s), "copy");
+    // join the side streams before the energies (which read every job's partials)
+    for (size_t q = 0; q < side.size() && q < chains.size(); ++q) {
+        ECK(cudaEventRecord(side_events[q + 1], side[q]), "join");
+        ECK(cudaStreamWaitEvent(s, side_events[q + 1], 0), "join wait");
+    }
     if (!hen.empty()) {
         k_energy_batch<<<(unsigned)hen.size(), 256, 0, s>>>(d_en);
         ECK(cudaGetLastError(), "batched energy");

@@ -7,12 +7,65 @@
 
 namespace cbct {
 
-struct ProjItem;
-struct BpItem;
-struct Eq2Item;
-struct TvItem;
-struct VecItem;
-struct EnItem;
+// Per-request items of the batched launches (device tables hold copies of these).
+struct ProjItem {
+    GeoDev G;
+    const float *vol;
+    const float *y32;
+    const __half *y16;
+    float *out;
+    double *partial;
+    int mode;
+};
+
+struct BpItem {
+    GeoDev G;
+    const float *rs;
+    const float *fin;
+    float *out;
+    float c;
+    int mode;
+};
+
+struct Eq2Item {  // Eq. 2 adjoint + gradient step of one request
+    GeoDev G;
+    const float *r;
+    const float *fin;
+    float *out;
+    float cscale;
+    int mode;
+};
+
+struct TvItem {
+    TvArgs A;
+    const float *fin;
+    const float *g;
+    float *fout;
+    double *partial;
+    int clamp;
+    int e1;
+};
+
+struct VecItem {  // power-iteration helpers on one volume
+    const float *x;
+    const float *y;
+    float *out;
+    double *partial;
+    double *lam;
+    float *scale;
+    long n;
+    int nblk;
+};
+
+struct EnItem {
+    const double *pe2;
+    const double *pe1;
+    double *trace;
+    int *counter;
+    double inv_nv, mu_over_nr;
+    int n2, n1;
+};
+
 
 enum JobPhase { PH_PREPARE = 0, PH_START_LEVEL, PH_POWER, PH_POWER_DONE, PH_FBS, PH_LEVEL_DONE, PH_DONE };
 
@@ -53,6 +106,19 @@ class Engine {
     void remove_finished();
     std::vector<Job *> jobs;
     cudaStream_t stream;
+    // jobs whose every stage fills the GPU by itself: each runs its whole tick on a
+    // side stream (forked from and joined back to the engine's stream), so that the
+    // tails of one job's kernels overlap the next job's
+    struct Chain {
+        Job *job = nullptr;
+        bool power = false, eq2 = false;
+        ProjItem proj;
+        BpItem bp;
+        Eq2Item eq;
+        VecItem vec;
+        std::vector<TvItem> tv;
+        std::vector<CopyOp> copies;
+    };
 
   private:
     cbct_status prepare(Job *j);
@@ -79,6 +145,10 @@ class Engine {
     std::vector<BpItem> solo_bp;
     std::vector<Eq2Item> solo_eq;
     std::vector<std::vector<TvItem>> solo_tv;
+    std::vector<Chain> chains;
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> side_events;
+    cbct_status ensure_side(size_t n);
     std::vector<BpItem> hbp[4];
     std::vector<Eq2Item> heq;
     std::vector<VecItem> hdot;
