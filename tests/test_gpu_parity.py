@@ -103,6 +103,24 @@ def test_project_large_sampled_rays(lib):
     assert (y[:, 150:234, 200:312] > 0).all()
 
 
+def tall_geometry():
+    # 600 imager rows: more than one 512-thread projector tile per detector column, and
+    # thick voxels (several rows per voxel) against thin rows
+    return dict(nx=24, ny=20, nz=40, hx=3.0, hy=3.0, hz=6.0, nu=30, nv=600, du=4.0, dv=0.6,
+                dso=500.0, dsd=800.0, angles=2 * math.pi * np.arange(6) / 6 + 0.37)
+
+
+def test_tall_imager_project_and_backproject(lib):
+    g = tall_geometry()
+    rng = np.random.default_rng(27)
+    check_projection(lib, g, rng.uniform(size=(40, 20, 24)))
+    G = lib.cbct_geometry_create(g)
+    y = rng.normal(size=(6, 600, 30))
+    bt = host(lib.cbct_backproject(G, dev(y)))
+    ref = oracle.backproject(g, f32(y))
+    assert rel(bt, ref) <= P_TOL, rel(bt, ref)
+
+
 # ---------------------------------------------------------------------------------
 # adjoint
 # ---------------------------------------------------------------------------------
