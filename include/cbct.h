@@ -127,6 +127,10 @@ typedef struct {
     int mg_pre, mg_post;  /* smoothing iterations per level; 0 -> 2 each             */
     int mg_coarse;        /* iterations on the coarsest level; 0 -> 10               */
     int *mg_accepted;     /* optional host out [levels]: coarse corrections kept     */
+    double *step_trace;   /* optional host out [levels][iters]: |f_k+1 - f_k|_2 of each
+                             iteration (float64 sum of float32 squares), coarsest
+                             level first, like energy_trace; with mg_cycle 1,
+                             [iters]: the change of the finest iterate over each cycle */
 } cbct_options;
 
 /* Kernel classes reported through cbct_options.kernel_ms. */
@@ -188,11 +192,12 @@ cbct_status cbct_tv_prox(cbct_geometry *geom, const float *g_dev, float *f_inout
  *   g = f - (gamma/beta) P^T (P f - Y),  gamma = 2 mu Nv / (n_angles nu nv)
  *   f = step 2 and 3 as in cbct_tv_prox (clamp_mode, tv_mode as in cbct_options)
  * beta must be > 0 (no automatic choice here).  Y_dev: measured sinogram.
- * energy_trace: optional host [iters][3] (E, E1, mu*E2 of each entering iterate;
- * synchronises the stream once at the end). */
+ * energy_trace: optional host [iters][3] (E, E1, mu*E2 of each entering iterate);
+ * step_trace: optional host [iters], |f_k+1 - f_k|_2 of each iteration.  Either one
+ * synchronises the stream once at the end. */
 cbct_status cbct_fbs(cbct_geometry *geom, const float *Y_dev, double mu, double beta, double eps,
                      int inner_iters, int clamp_mode, int tv_mode, int iters, float *f_inout_dev,
-                     double *energy_trace, cudaStream_t stream);
+                     double *energy_trace, double *step_trace, cudaStream_t stream);
 
 /* Largest eigenvalue of P^T P by `iters` power iterations from the all-ones volume;
  * the estimate is the Rayleigh quotient of the last normalised iterate.  Writes

@@ -259,16 +259,18 @@ def auto_beta(geom, mu, K=30):
 
 
 def fbs(geom, Y, mu, beta, eps, M, iters, f0=None, clamp_mode=0, tv_weight=1.0, tv_mode=0, adjoint_mode=0,
-        v=None):
-    """Algorithm A1; v (optional volume) adds the linear term -<v, f> to the energy."""
+        v=None, steps=False):
+    """Algorithm A1; v (optional volume) adds the linear term -<v, f> to the energy.
+    Returns (f, trace [iters][3]), or (f, trace, |f_k+1 - f_k| [iters]) with steps=True."""
     Y = _f64(Y)
     f = _f64(f0).copy() if f0 is not None else np.zeros(vol_shape(geom))
     trace = np.empty((iters, 3))
+    st = np.empty(max(iters, 1)) if steps else None
     vv = _f64(v) if v is not None else None
     h = _g(geom, tv_mode, adjoint_mode)
     _load().or_fbs(C.byref(h.s), _ptr(Y), mu, beta, eps, M, clamp_mode, tv_weight, iters, _ptr(f), _ptr(trace),
-                   _ptr(vv))
-    return f, trace
+                   _ptr(vv), _ptr(st))
+    return (f, trace, st[:iters]) if steps else (f, trace)
 
 
 def restrict_sino(y):

@@ -612,9 +612,11 @@ double or_auto_beta(const or_geom *g, double mu, int K)
  * Step 1 uses the exact transpose, or B of Eq. 2 when g->adjoint_mode is 1.
  * lin (optional, one value per voxel) adds the linear term -<lin, f> to the energy
  * (the coarse-level model of a multigrid cycle); the trace reports E without it.
+ * step (optional, iters): |f_{k+1} - f_k|_2 of each iteration.
  */
 void or_fbs(const or_geom *g, const double *Y, double mu, double beta, double eps, int M,
-            int clamp_mode, double tv_weight, int iters, double *f, double *trace, const double *lin)
+            int clamp_mode, double tv_weight, int iters, double *f, double *trace, const double *lin,
+            double *step)
 {
     const long nvox = (long)g->nx * g->ny * g->nz;
     const long nr = (long)g->na * g->nv * g->nu;
@@ -623,7 +625,9 @@ void or_fbs(const or_geom *g, const double *Y, double mu, double beta, double ep
     double *r = (double *)malloc(sizeof(double) * nr);
     double *bp = (double *)malloc(sizeof(double) * nvox);
     double *gv = (double *)malloc(sizeof(double) * nvox);
+    double *fprev = step ? (double *)malloc(sizeof(double) * nvox) : NULL;
     for (int it = 0; it < iters; ++it) {
+        if (step) memcpy(fprev, f, sizeof(double) * nvox);
         /* step 1: g = f - (gamma/beta) P^T (P f - Y) */
         or_project(g, f, r);
         double q = 0.0;
@@ -648,10 +652,16 @@ void or_fbs(const or_geom *g, const double *Y, double mu, double beta, double ep
             for (long j = 0; j < nvox; ++j) gv[j] += (double)nvox / beta * lin[j];
         /* steps 2 and 3 */
         or_prox(&v, gv, f, beta, eps, M, clamp_mode, tv_weight, NULL);
+        if (step) {
+            double d = 0.0;
+            for (long j = 0; j < nvox; ++j) d += (f[j] - fprev[j]) * (f[j] - fprev[j]);
+            step[it] = sqrt(d);
+        }
     }
     free(r);
     free(bp);
     free(gv);
+    free(fprev);
 }
 
 /* ------------------------------------------------------------------------------ */
@@ -772,7 +782,7 @@ void or_reconstruct(const or_geom *g, const double *Y, double mu, int iters, int
         double beta = betas ? betas[l] : or_auto_beta(&lg[l], mu, K_pi);
         double e = eps > 0 ? eps : or_default_eps(&lg[l]);
         double *tr = trace ? trace + 3 * iters * (levels - 1 - l) : NULL;
-        or_fbs(&lg[l], Ys[l], mu, beta, e, M, clamp_mode, 1.0, iters, f, tr, NULL);
+        or_fbs(&lg[l], Ys[l], mu, beta, e, M, clamp_mode, 1.0, iters, f, tr, NULL, NULL);
     }
     memcpy(f_out, f, sizeof(double) * (size_t)g->nx * g->ny * g->nz);
     free(f);
@@ -889,10 +899,10 @@ static void vcycle(const vc_ctx *C, int l, double *f, const double *v)
 {
     const or_geom *g = &C->lg[l];
     if (l == C->levels - 1) {
-        or_fbs(g, C->Ys[l], C->mu, C->betas[l], C->epss[l], C->M, 0, 1.0, C->coarse, f, NULL, v);
+        or_fbs(g, C->Ys[l], C->mu, C->betas[l], C->epss[l], C->M, 0, 1.0, C->coarse, f, NULL, v, NULL);
         return;
     }
-    or_fbs(g, C->Ys[l], C->mu, C->betas[l], C->epss[l], C->M, 0, 1.0, C->pre, f, NULL, v);
+    or_fbs(g, C->Ys[l], C->mu, C->betas[l], C->epss[l], C->M, 0, 1.0, C->pre, f, NULL, v, NULL);
     const or_geom *gc = &C->lg[l + 1];
     const long n = (long)g->nx * g->ny * g->nz, nc = (long)gc->nx * gc->ny * gc->nz;
     double *gr = (double *)malloc(sizeof(double) * n);
@@ -923,7 +933,7 @@ static void vcycle(const vc_ctx *C, int l, double *f, const double *v)
         memcpy(f, ftry, sizeof(double) * n);
         if (C->accepted) C->accepted[l] += 1;
     }
-    or_fbs(g, C->Ys[l], C->mu, C->betas[l], C->epss[l], C->M, 0, 1.0, C->post, f, NULL, v);
+    or_fbs(g, C->Ys[l], C->mu, C->betas[l], C->epss[l], C->M, 0, 1.0, C->post, f, NULL, v, NULL);
     free(gr);
     free(x0);
     free(x);

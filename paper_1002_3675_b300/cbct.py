@@ -46,7 +46,8 @@ class Options(C.Structure):
                 ("kernel_launches", C.POINTER(C.c_int)), ("kernel_mask", C.c_uint), ("reuse_lambda", C.c_int),
                 ("tv_mode", C.c_int),
                 ("adjoint_mode", C.c_int), ("mg_cycle", C.c_int), ("mg_pre", C.c_int), ("mg_post", C.c_int),
-                ("mg_coarse", C.c_int), ("mg_accepted", C.POINTER(C.c_int))]
+                ("mg_coarse", C.c_int), ("mg_accepted", C.POINTER(C.c_int)),
+                ("step_trace", C.POINTER(C.c_double))]
 
 
 class Request(C.Structure):
@@ -90,7 +91,7 @@ _SIGS = {
     "cbct_backproject": [_P, _P, _P, _V],
     "cbct_backproject_eq2": [_P, _P, _P, _V],
     "cbct_tv_prox": [_P, _P, _P, _D, _D, _I, _I, _V],
-    "cbct_fbs": [_P, _P, _D, _D, _D, _I, _I, _I, _I, _P, C.POINTER(C.c_double), _V],
+    "cbct_fbs": [_P, _P, _D, _D, _D, _I, _I, _I, _I, _P, C.POINTER(C.c_double), C.POINTER(C.c_double), _V],
     "cbct_power_iteration": [_P, _I, C.POINTER(C.c_double), _V],
     "cbct_energy": [_P, _P, _P, _D, _D, _I, C.POINTER(C.c_double), _V],
     "cbct_reconstruct": [_P, _P, C.POINTER(C.c_double), _I, _D, _I, _I, C.POINTER(Options), _P, _V],
@@ -228,11 +229,17 @@ def cbct_tv_prox(g: Geometry, gvol, f, beta: float, eps: float, inner_iters: int
     return f
 
 
-def cbct_fbs(g: Geometry, Y, mu, beta, eps, inner_iters, clamp_mode, iters, f, trace=False, tv_mode=0):
+def cbct_fbs(g: Geometry, Y, mu, beta, eps, inner_iters, clamp_mode, iters, f, trace=False, tv_mode=0,
+             step_trace=False):
+    """Returns f, or (f, trace [iters][3]) with trace=True, or (f, trace, steps [iters])
+    with step_trace=True as well (steps alone: (f, steps))."""
     tr = np.zeros((max(iters, 1), 3)) if trace else None
+    st = np.zeros(max(iters, 1)) if step_trace else None
     _check(lib.cbct_fbs(g.handle, _ptr(Y, "Y"), mu, beta, eps, inner_iters, clamp_mode, tv_mode, iters,
-                        _ptr(f, "f"), tr.ctypes.data_as(C.POINTER(C.c_double)) if trace else None, _stream()))
-    return (f, tr[:iters]) if trace else f
+                        _ptr(f, "f"), tr.ctypes.data_as(C.POINTER(C.c_double)) if trace else None,
+                        st.ctypes.data_as(C.POINTER(C.c_double)) if step_trace else None, _stream()))
+    out = (f,) + ((tr[:iters],) if trace else ()) + ((st[:iters],) if step_trace else ())
+    return out if len(out) > 1 else f
 
 
 def cbct_power_iteration(g: Geometry, iters: int = 30) -> float:
@@ -280,6 +287,7 @@ def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=N
                      kernel_mask=0):
     """Returns f_out, or (f_out, info) when trace/kernel_times is requested; info holds
     'trace' [levels][iters][3] ([iters][3] after each V-cycle when mg_cycle=1),
+    'step_trace' [levels][iters] |f_k+1 - f_k| ([iters], the change over each V-cycle),
     'betas' [levels], 'accepted' [levels] (V-cycles), 'kernel_ms'/'kernel_launches'."""
     f_out = _empty(g.vol_shape) if f_out is None else f_out
     o = Options()
@@ -304,6 +312,8 @@ def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=N
     tr = np.full((levels, max(iters, 1), 3), np.nan) if trace else None
     if trace:
         o.energy_trace = tr.ctypes.data_as(C.POINTER(C.c_double))
+        sp = np.full((levels, max(iters, 1)), np.nan)
+        o.step_trace = sp.ctypes.data_as(C.POINTER(C.c_double))
     bo = np.zeros(levels)
     o.beta_out = bo.ctypes.data_as(C.POINTER(C.c_double))
     km = (C.c_float * NUM_KERNEL_CLASSES)() if kernel_times else None
@@ -321,6 +331,7 @@ def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=N
         info["accepted"] = np.array(acc[:levels])
     if trace:
         info["trace"] = tr.reshape(-1, 3)[:iters] if mg_cycle else tr[:, :iters]
+        info["step_trace"] = sp.reshape(-1)[:iters] if mg_cycle else sp[:, :iters]
     if kernel_times:
         info["kernel_ms"] = dict(zip(KERNEL_CLASSES, list(km)))
         info["kernel_launches"] = dict(zip(KERNEL_CLASSES, list(kl)))
@@ -344,6 +355,8 @@ def cbct_reconstruct_batch(requests, use_graphs=False):
         if r.get("trace"):
             info["trace"] = np.full((levels, max(r["iters"], 1), 3), np.nan)
             o.energy_trace = info["trace"].ctypes.data_as(C.POINTER(C.c_double))
+            info["step_trace"] = np.full((levels, max(r["iters"], 1)), np.nan)
+            o.step_trace = info["step_trace"].ctypes.data_as(C.POINTER(C.c_double))
         keep.append(o)
         f = r.get("f_out")
         f = _empty(g.vol_shape) if f is None else f
@@ -355,6 +368,7 @@ def cbct_reconstruct_batch(requests, use_graphs=False):
     for info, r in zip(infos, requests):
         if "trace" in info:
             info["trace"] = info["trace"][:, :r["iters"]]
+            info["step_trace"] = info["step_trace"][:, :r["iters"]]
     return outs, infos
 
 

@@ -147,16 +147,17 @@ struct Launch {  // wraps one kernel launch with optional timing
     ~Launch() { p.end(); }
 };
 
-// Steps 2 and 3: M sweeps from src0 into L->f (ping-pong through A and B).
+// Steps 2 and 3: M sweeps from src0 (ping-pong through A and B), then the result moves
+// into L->f while the partials of |f_k+1 - f_k|^2 (f_k still in L->f) are formed.
 // partial_e1 (optional) receives the E1 partials of the first sweep's input.
 cbct_status enqueue_prox(Level *L, const SolveParams &P, const float *src0, double *partial_e1, int *ne1,
-                         Prof &prof, cudaStream_t s) {
+                         double *partial_step, Prof &prof, cudaStream_t s) {
     const TvArgs ta = tv_args(L, P);
     const float *src = src0;
     for (int m = 0; m < P.M; ++m) {
         const bool last = m == P.M - 1;
-        float *dst = last ? L->f : (m % 2 == 0 ? L->A : L->B);
-        if (dst == src) dst = L->A;  // M == 1 in place: go through A
+        float *dst = (m % 2 == 0) ? L->A : L->B;
+        if (dst == src) dst = (dst == L->A) ? L->B : L->A;
         const bool clamp = P.clamp_mode == 0 || last;
         {
             Launch l(prof, CBCT_K_TV);
@@ -165,7 +166,8 @@ cbct_status enqueue_prox(Level *L, const SolveParams &P, const float *src0, doub
         }
         src = dst;
     }
-    if (src != L->f) CK(cudaMemcpyAsync(L->f, src, vol_elems(L->gd) * 4, cudaMemcpyDeviceToDevice, s), "copy");
+    Launch l(prof, CBCT_K_REDUCE);
+    CK(launch_step_copy(src, L->f, vol_elems(L->gd), partial_step, s), "step");
     return CBCT_OK;
 }
 
@@ -200,17 +202,19 @@ cbct_status enqueue_iteration(cbct_geometry *G, Level *L, const SolveParams &P, 
         Launch l(prof, CBCT_K_REDUCE);
         CK(launch_axpy(L->g, P.lin, P.lin_scale, vol_elems(gd), s), "linear term");
     }
+    double *pstep = step_region(L);
     ST(enqueue_prox(L, P, P.clamp_mode == 0 ? L->f : L->g, P.clamp_mode == 0 ? pt : nullptr,
-                    P.clamp_mode == 0 ? &nb_t : nullptr, prof, s));
+                    P.clamp_mode == 0 ? &nb_t : nullptr, pstep, prof, s));
     {
         Launch l(prof, CBCT_K_REDUCE);
-        CK(launch_energy_finalize(pp, nb_p, pt, nb_t, P.inv_nv, P.mu_over_nr, dtrace, G->dcounter, s),
+        CK(launch_energy_finalize(pp, nb_p, pt, nb_t, P.inv_nv, P.mu_over_nr, dtrace, G->dcounter, s, pstep,
+                                  (int)step_partials(vol_elems(gd))),
            "energy reduction");
     }
     return CBCT_OK;
 }
 
-// `iters` iterations of A1 on level L; trace values land in dtrace[0 .. 3*iters).
+// `iters` iterations of A1 on level L; trace values land in dtrace[0 .. TRACE_W*iters).
 cbct_status run_level(cbct_geometry *G, Level *L, const SolveParams &P, int iters, double *dtrace, bool graphs,
                       Prof &prof, cudaStream_t s) {
     CK(cudaMemsetAsync(G->dcounter, 0, sizeof(int), s), "counter reset");
@@ -369,10 +373,26 @@ struct VCycle {
         CK(launch_energy_finalize(L->partial, nb_p, L->partial + np, nb_t, Q.inv_nv, Q.mu_over_nr, scratch,
                                   G->dcounter + 1, s),
            "energy");
-        if (lv) CK(launch_dot(lv, f, vol_elems(g), L->mg_partial, scratch + 3, s), "linear term");
-        else CK(cudaMemsetAsync(scratch + 3, 0, sizeof(double), s), "linear term");
-        CK(cudaMemcpyAsync(out, scratch, 4 * sizeof(double), cudaMemcpyDeviceToHost, s), "energy copy");
+        if (lv) CK(launch_dot(lv, f, vol_elems(g), L->mg_partial, scratch + TRACE_W, s), "linear term");
+        else CK(cudaMemsetAsync(scratch + TRACE_W, 0, sizeof(double), s), "linear term");
+        CK(cudaMemcpyAsync(out, scratch, 3 * sizeof(double), cudaMemcpyDeviceToHost, s), "energy copy");
+        CK(cudaMemcpyAsync(out + 3, scratch + TRACE_W, sizeof(double), cudaMemcpyDeviceToHost, s), "energy copy");
         CK(cudaStreamSynchronize(s), "energy sync");
+        return CBCT_OK;
+    }
+
+    // *out (host) = |f_l - prev|_2, the change of level l's iterate since prev
+    cbct_status change(int l, const float *prev, double *out) {
+        Level *L = Ls[l];
+        const size_t n = vol_elems(L->gd);
+        double *scratch = G->dscalars + 8;
+        Launch lz(*prof, CBCT_K_REDUCE);
+        CK(launch_sub(L->f, prev, t1(l), n, s), "change");
+        CK(launch_dot(t1(l), t1(l), n, L->mg_partial, scratch, s), "change norm");
+        double d = 0.0;
+        CK(cudaMemcpyAsync(&d, scratch, sizeof(double), cudaMemcpyDeviceToHost, s), "change copy");
+        CK(cudaStreamSynchronize(s), "change sync");
+        *out = std::sqrt(d);
         return CBCT_OK;
     }
 
@@ -437,6 +457,21 @@ cbct_status cbct::get_trace(cbct_geometry *G, size_t n, double **out) {
         G->dtrace_len = n;
     }
     *out = G->dtrace;
+    return CBCT_OK;
+}
+
+// Host copies of `iters` device trace entries: {E, E1, mu E2} into energy (3 per
+// iteration) and |f_k+1 - f_k| into step (1 per iteration); either may be null.
+cbct_status cbct::copy_trace(const double *dtrace, int iters, double *energy, double *step, cudaStream_t s) {
+    if (iters <= 0) return CBCT_OK;
+    const size_t w = TRACE_W * sizeof(double);
+    if (energy)
+        CK(cudaMemcpy2DAsync(energy, 3 * sizeof(double), dtrace, w, 3 * sizeof(double), iters,
+                             cudaMemcpyDeviceToHost, s),
+           "trace");
+    if (step)
+        CK(cudaMemcpy2DAsync(step, sizeof(double), dtrace + 3, w, sizeof(double), iters, cudaMemcpyDeviceToHost, s),
+           "step trace");
     return CBCT_OK;
 }
 
@@ -689,14 +724,14 @@ cbct_status cbct_tv_prox(cbct_geometry *G, const float *g_dev, float *f_inout_de
     CK(launch_vol_to_internal(g_dev, L->g, g.nx, g.ny, g.nz, s), "volume layout");
     CK(launch_vol_to_internal(f_inout_dev, L->f, g.nx, g.ny, g.nz, s), "volume layout");
     Prof prof;
-    ST(enqueue_prox(L, P, L->f, nullptr, nullptr, prof, s));
+    ST(enqueue_prox(L, P, L->f, nullptr, nullptr, nullptr, prof, s));
     CK(launch_vol_to_api(L->f, f_inout_dev, g.nx, g.ny, g.nz, s), "volume layout");
     return CBCT_OK;
 }
 
 cbct_status cbct_fbs(cbct_geometry *G, const float *Y_dev, double mu, double beta, double eps, int inner_iters,
                      int clamp_mode, int tv_mode, int iters, float *f_inout_dev, double *energy_trace,
-                     cudaStream_t s) {
+                     double *step_trace, cudaStream_t s) {
     if (!G) {
         set_error("geometry is null");
         return CBCT_ERR_INVALID_ARG;
@@ -713,15 +748,15 @@ cbct_status cbct_fbs(cbct_geometry *G, const float *Y_dev, double mu, double bet
     SolveParams P;
     ST(solve_params(L, mu, beta, eps, inner_iters, clamp_mode, false, &P, tv_mode));
     double *dtrace;
-    ST(get_trace(G, 3 * (size_t)std::max(iters, 1), &dtrace));
+    ST(get_trace(G, TRACE_W * (size_t)std::max(iters, 1), &dtrace));
     const GeoDev &g = L->gd;
     CK(launch_sino_to_internal(Y_dev, L->Y, nullptr, nullptr, g.na, g.nu, g.nv, s), "sinogram layout");
     CK(launch_vol_to_internal(f_inout_dev, L->f, g.nx, g.ny, g.nz, s), "volume layout");
     Prof prof;
     ST(run_level(G, L, P, iters, dtrace, false, prof, s));
     CK(launch_vol_to_api(L->f, f_inout_dev, g.nx, g.ny, g.nz, s), "volume layout");
-    if (energy_trace && iters > 0) {
-        CK(cudaMemcpyAsync(energy_trace, dtrace, 3 * sizeof(double) * iters, cudaMemcpyDeviceToHost, s), "trace");
+    if ((energy_trace || step_trace) && iters > 0) {
+        ST(copy_trace(dtrace, iters, energy_trace, step_trace, s));
         CK(cudaStreamSynchronize(s), "fbs");
     }
     return CBCT_OK;
@@ -753,7 +788,7 @@ cbct_status cbct_energy(cbct_geometry *G, const float *Y_dev, const float *f_dev
     SolveParams P;
     ST(solve_params(L, mu, 1.0, eps, 1, 0, false, &P, tv_mode));
     double *dtrace;
-    ST(get_trace(G, 3, &dtrace));
+    ST(get_trace(G, TRACE_W, &dtrace));
     const GeoDev &g = L->gd;
     CK(launch_sino_to_internal(Y_dev, L->Y, nullptr, nullptr, g.na, g.nu, g.nv, s), "sinogram layout");
     CK(launch_vol_to_internal(f_dev, L->A, g.nx, g.ny, g.nz, s), "volume layout");
@@ -836,7 +871,7 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
         ST(ensure_workspace(Ls[l], fp16));
     }
     double *dtrace;
-    ST(get_trace(G, 3 * (size_t)std::max(iters, 1), &dtrace));
+    ST(get_trace(G, TRACE_W * (size_t)std::max(iters, 1), &dtrace));
     Prof prof;
     prof.G = G;
     prof.s = s;
@@ -891,7 +926,7 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
         V.mu = mu;
         V.prof = &prof;
         V.s = s;
-        ST(get_trace(G, 3 * (size_t)std::max({V.pre, V.post, V.coarse, 1}), &V.dtrace));
+        ST(get_trace(G, TRACE_W * (size_t)std::max({V.pre, V.post, V.coarse, 1}), &V.dtrace));
         V.P.resize(levels);
         for (int l = 0; l < levels; ++l) {
             ST(ensure_mg_workspace(Ls[l]));
@@ -907,7 +942,13 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
             CK(cudaMemsetAsync(Ls[0]->f, 0, vol_elems(Ls[0]->gd) * 4, s), "zero start");
         }
         for (int c = 0; c < iters; ++c) {
+            if (o.step_trace) {
+                Launch lz(prof, CBCT_K_REDUCE);
+                CK(cudaMemcpyAsync(V.x0(0), Ls[0]->f, vol_elems(Ls[0]->gd) * 4, cudaMemcpyDeviceToDevice, s),
+                   "copy");
+            }
             ST(V.cycle(0, nullptr));
+            if (o.step_trace) ST(V.change(0, V.x0(0), &o.step_trace[c]));
             if (o.energy_trace) {
                 double e[4];
                 ST(V.energy(0, Ls[0]->f, nullptr, e));
@@ -944,9 +985,10 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
         SolveParams P;
         ST(solve_params(L, mu, beta, eps, M, o.clamp_mode, fp16, &P, o.tv_mode, o.adjoint_mode));
         ST(run_level(G, L, P, iters, dtrace, o.use_graphs != 0, prof, s));
-        if (o.energy_trace && iters > 0) {
-            double *dst = o.energy_trace + 3 * (size_t)iters * (levels - 1 - l);
-            CK(cudaMemcpyAsync(dst, dtrace, 3 * sizeof(double) * iters, cudaMemcpyDeviceToHost, s), "trace");
+        if ((o.energy_trace || o.step_trace) && iters > 0) {
+            const size_t lv = (size_t)iters * (levels - 1 - l);
+            ST(copy_trace(dtrace, iters, o.energy_trace ? o.energy_trace + 3 * lv : nullptr,
+                          o.step_trace ? o.step_trace + lv : nullptr, s));
             CK(cudaStreamSynchronize(s), "trace sync");
         }
     }

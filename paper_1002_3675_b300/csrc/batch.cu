@@ -21,6 +21,7 @@
 #include "bp_eq2_tile.cuh"
 #include "bp_tile.cuh"
 #include "project_tile.cuh"
+#include "step_tile.cuh"
 #include "tv_tile.cuh"
 
 namespace cbct {
@@ -217,17 +218,30 @@ __device__ double block_sum_fixed_b(const double *p, int n) {
     return r;
 }
 
+// The same sums and trace entries as the single-request energy finalisation.
 __global__ void k_energy_batch(const EnItem *__restrict__ items) {
     const EnItem it = items[blockIdx.x];
     const double q = block_sum_fixed_b(it.pe2, it.n2);
     const double t = block_sum_fixed_b(it.pe1, it.n1);
+    const double d = block_sum_fixed_b(it.pstep, it.nstep);
     if (threadIdx.x == 0) {
         const int k = *it.counter;
         const double e1 = t * it.inv_nv, e2 = q * it.mu_over_nr;
-        it.trace[3 * k + 0] = e1 + e2;
-        it.trace[3 * k + 1] = e1;
-        it.trace[3 * k + 2] = e2;
+        it.trace[TRACE_W * k + 0] = e1 + e2;
+        it.trace[TRACE_W * k + 1] = e1;
+        it.trace[TRACE_W * k + 2] = e2;
+        it.trace[TRACE_W * k + 3] = sqrt(d);
         *it.counter = k + 1;
+    }
+}
+
+// Step-norm copies of many requests: one 256-voxel block per tile.
+__global__ void __launch_bounds__(STEP_THREADS)
+k_step_batch(const StepItem *__restrict__ items, const long *__restrict__ start, int n, long total) {
+    for (long t = blockIdx.x; t < total; t += gridDim.x) {
+        const int r = find_item(start, n, t);
+        const StepItem it = items[r];
+        step_block(it.v, it.f, (size_t)it.n, it.partial, (size_t)(t - start[r]));
     }
 }
 
@@ -307,7 +321,7 @@ cbct_status Engine::prepare(Job *j) {
     }
     EST(ensure_trace(G, 0));
     double *dtrace;
-    EST(get_trace(G, 3 * (size_t)std::max(j->iters, 1), &dtrace));
+    EST(get_trace(G, TRACE_W * (size_t)std::max(j->iters, 1), &dtrace));
     const GeoDev &g0 = j->Ls[0]->gd;
     ECK(launch_sino_to_internal(j->Y, j->Ls[0]->Y, j->fp16 ? j->Ls[0]->Yh : nullptr, nullptr, g0.na, g0.nu, g0.nv,
                                 stream),
@@ -362,9 +376,11 @@ cbct_status Engine::begin_fbs(Job *j, double beta) {
 
 cbct_status Engine::finish_level(Job *j) {
     Level *L = j->Ls[j->level];
-    if (j->o.energy_trace && j->iters > 0) {
-        double *dst = j->o.energy_trace + 3 * (size_t)j->iters * (j->levels - 1 - j->level);
-        ECK(cudaMemcpy(dst, j->G->dtrace, 3 * sizeof(double) * j->iters, cudaMemcpyDeviceToHost), "trace");
+    if ((j->o.energy_trace || j->o.step_trace) && j->iters > 0) {
+        const size_t lv = (size_t)j->iters * (j->levels - 1 - j->level);
+        EST(copy_trace(j->G->dtrace, j->iters, j->o.energy_trace ? j->o.energy_trace + 3 * lv : nullptr,
+                       j->o.step_trace ? j->o.step_trace + lv : nullptr, stream));
+        ECK(cudaStreamSynchronize(stream), "trace");
     }
     if (j->level == 0) {
         const GeoDev &g = L->gd;
@@ -401,7 +417,9 @@ cbct_status Engine::build_tables() {
     chains.clear();
     const long sms = sm_count();
     max_m = 0;
-    copies.clear();
+    hstep.clear();
+    std::vector<long> sstart;
+    long stot = 0;
     tv_energy_jobs.clear();
     for (Job *j : jobs) {
         if (j->phase != PH_POWER && j->phase != PH_FBS) continue;
@@ -466,6 +484,8 @@ cbct_status Engine::build_tables() {
                 ei.pe1 = L->partial + np;
                 ei.n1 = (int)(j->P.clamp_mode == 1 ? tv_energy_partials(g.nx, g.ny, g.nz)
                                                    : tv_partials(g.nx, g.ny, g.nz));
+                ei.pstep = step_region(L);
+                ei.nstep = (int)step_partials(vol_elems(g));
                 ei.inv_nv = j->P.inv_nv;
                 ei.mu_over_nr = j->P.mu_over_nr;
                 ei.trace = j->G->dtrace;
@@ -535,6 +555,8 @@ cbct_status Engine::build_tables() {
             ei.n2 = (int)np;
             ei.pe1 = L->partial + np;
             ei.n1 = (int)(j->P.clamp_mode == 1 ? tv_energy_partials(g.nx, g.ny, g.nz) : tv_partials(g.nx, g.ny, g.nz));
+            ei.pstep = step_region(L);
+            ei.nstep = (int)step_partials(vol_elems(g));
             ei.inv_nv = j->P.inv_nv;
             ei.mu_over_nr = j->P.mu_over_nr;
             ei.trace = j->G->dtrace;
@@ -586,8 +608,8 @@ cbct_status Engine::build_tables() {
         const size_t np = project_partials(L->gd);
         for (int m = 0; m < j->P.M; ++m) {
             const bool last = m == j->P.M - 1;
-            float *dst = last ? L->f : (m % 2 == 0 ? L->A : L->B);
-            if (dst == src) dst = L->A;
+            float *dst = (m % 2 == 0) ? L->A : L->B;
+            if (dst == src) dst = (dst == L->A) ? L->B : L->A;
             TvItem ti;
             ti.A = ta;
             ti.fin = src;
@@ -607,8 +629,20 @@ cbct_status Engine::build_tables() {
             }
             src = dst;
         }
-        if (src != L->f) (chain ? chain->copies : copies).push_back({L->f, src, vol_elems(L->gd) * 4});
+        StepItem si;
+        si.v = src;
+        si.f = L->f;
+        si.partial = step_region(L);
+        si.n = (long)vol_elems(L->gd);
+        if (chain) {
+            chain->step = si;
+        } else {
+            hstep.push_back(si);
+            sstart.push_back(stot);
+            stot += (long)step_partials((size_t)si.n);
+        }
     }
+    steptotal = stot;
     dtotal = dtot;
     for (int v = 0; v < 4; ++v) bptotal[v] = bptot[v];
     eqtotal = eqtot;
@@ -634,6 +668,7 @@ cbct_status Engine::build_tables() {
         o_tst[m] = place(tvstart[m].size() * sizeof(long));
     }
     const size_t o_en = place(hen.size() * sizeof(EnItem));
+    const size_t o_step = place(hstep.size() * sizeof(StepItem)), o_sst = place(sstart.size() * sizeof(long));
     std::vector<char> blob(std::max<size_t>(off, 16));
     auto put = [&](size_t o, const void *src, size_t bytes) {
         if (bytes) memcpy(blob.data() + o, src, bytes);
@@ -653,6 +688,8 @@ cbct_status Engine::build_tables() {
         put(o_tst[m], tvstart[m].data(), tvstart[m].size() * sizeof(long));
     }
     put(o_en, hen.data(), hen.size() * sizeof(EnItem));
+    put(o_step, hstep.data(), hstep.size() * sizeof(StepItem));
+    put(o_sst, sstart.data(), sstart.size() * sizeof(long));
     if (blob.size() > dblob_len) {
         ECK(cudaStreamSynchronize(stream), "engine sync");
         cudaFree(dblob);
@@ -682,6 +719,8 @@ cbct_status Engine::build_tables() {
         d_tstart[m] = (long *)(b + o_tst[m]);
     }
     d_en = (EnItem *)(b + o_en);
+    d_step = (StepItem *)(b + o_step);
+    d_sstart = (long *)(b + o_sst);
     if (!chains.empty()) EST(ensure_side(chains.size()));
     return CBCT_OK;
 }
@@ -740,7 +779,7 @@ static cbct_status launch_chain(const Engine::Chain &c, cudaStream_t s) {
     for (const TvItem &it : c.tv)
         ECK(launch_tv_sweep(it.A, it.fin, it.g, it.fout, it.clamp != 0, it.e1 ? it.partial : nullptr, s, nullptr),
             "tv sweep");
-    for (const auto &cp : c.copies) ECK(cudaMemcpyAsync(cp.dst, cp.src, cp.bytes, cudaMemcpyDeviceToDevice, s), "copy");
+    if (!c.power) ECK(launch_step_copy(c.step.v, c.step.f, (size_t)c.step.n, c.step.partial, s), "step");
     return CBCT_OK;
 }
 
@@ -826,7 +865,11 @@ cbct_status Engine::launch_stages() {
                                                                                          (int)htv[m].size(), tvtot[m]);
         ECK(cudaGetLastError(), "batched tv sweep");
     }
-    for (const auto &c : copies) ECK(cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToDevice, s), "copy");
+    if (!hstep.empty()) {
+        const long nb = persistent_grid(steptotal, resident_blocks(k_step_batch, STEP_THREADS, 0));
+        k_step_batch<<<(unsigned)nb, STEP_THREADS, 0, s>>>(d_step, d_sstart, (int)hstep.size(), steptotal);
+        ECK(cudaGetLastError(), "batched step");
+    }
     // join the side streams before the energies (which read every job's partials)
     for (size_t q = 0; q < side.size() && q < chains.size(); ++q) {
         ECK(cudaEventRecord(side_events[q + 1], side[q]), "join");

@@ -57,9 +57,18 @@ struct VecItem {  // power-iteration helpers on one volume
     int nblk;
 };
 
+struct StepItem {  // prox result v moved into the iterate f, with the step-norm partials
+    const float *v;
+    float *f;
+    double *partial;
+    long n;
+};
+
 struct EnItem {
     const double *pe2;
     const double *pe1;
+    const double *pstep;
+    int nstep;
     double *trace;
     int *counter;
     double inv_nv, mu_over_nr;
@@ -87,12 +96,6 @@ struct Job {
     bool done_event_pending = false;
 };
 
-struct CopyOp {
-    float *dst;
-    const float *src;
-    size_t bytes;
-};
-
 // Advances every job by one power-iteration step or one Algorithm A1 iteration per
 // tick, all stages of all jobs in one batched launch per stage.
 class Engine {
@@ -117,7 +120,7 @@ class Engine {
         Eq2Item eq;
         VecItem vec;
         std::vector<TvItem> tv;
-        std::vector<CopyOp> copies;
+        StepItem step{};
     };
 
   private:
@@ -155,8 +158,11 @@ class Engine {
     std::vector<std::vector<TvItem>> htv;
     std::vector<EnItem> hen;
     std::vector<long> tvtot;
-    std::vector<CopyOp> copies;
+    std::vector<StepItem> hstep;
     std::vector<Job *> tv_energy_jobs;
+    long steptotal = 0;
+    StepItem *d_step = nullptr;
+    long *d_sstart = nullptr;
     long dtotal = 0, bptotal[4] = {0, 0, 0, 0}, eqtotal = 0;
     int max_m = 0;
     void *dblob = nullptr;

@@ -178,8 +178,17 @@ cudaError_t launch_prolong(const float *fc, int c0, int c1, int c2, float *f, in
                            cudaStream_t s);
 
 // reductions and small kernels
+// device energy trace: TRACE_W doubles per iteration: E, E1, mu E2 of the entering
+// iterate and |f_k+1 - f_k|_2 of the iteration
+constexpr int TRACE_W = 4;
 cudaError_t launch_energy_finalize(const double *pe2, int n2, const double *pe1, int n1, double inv_nv,
-                                   double mu_over_nr, double *trace, int *counter, cudaStream_t s);
+                                   double mu_over_nr, double *trace, int *counter, cudaStream_t s,
+                                   const double *pstep = nullptr, int nstep = 0);
+size_t step_partials(size_t n);
+// the step-norm partials inside a level's partials buffer (after the projector's and
+// the TV sweep's)
+double *step_region(Level *L);
+cudaError_t launch_step_copy(const float *v, float *f, size_t n, double *partial, cudaStream_t s);
 cudaError_t launch_dot2(const float *x, const float *y, size_t n, double *partial, cudaStream_t s,
                         int *nblocks_out);
 cudaError_t launch_power_finalize(const double *partial, int nblk, double *lam, float *scale,
@@ -227,5 +236,6 @@ TvArgs tv_args(const Level *L, const SolveParams &P);
 cbct_status solve_params(const Level *L, double mu, double beta, double eps, int M, int clamp_mode, bool fp16,
                          SolveParams *P, int tv_mode = 0, int adjoint_mode = 0);
 cbct_status get_trace(cbct_geometry *G, size_t n, double **out);
+cbct_status copy_trace(const double *dtrace, int iters, double *energy, double *step, cudaStream_t s);
 
 }  // namespace cbct

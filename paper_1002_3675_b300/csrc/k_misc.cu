@@ -1,7 +1,7 @@
 // Layout changes at the ABI boundary, multigrid transfers (the multigrid of Jia et
 // al. 2010, cited method [20], read as a coarse-to-fine cascade) and deterministic
 // float64 reductions for the energies of Eq. 1 and the step-size estimate.
-#include "cbct_internal.h"
+#include "step_tile.cuh"
 
 namespace cbct {
 
@@ -212,25 +212,43 @@ __device__ double block_sum_fixed(const double *p, int n) {
     return r;
 }
 
-// E = E1 + mu E2 with E1 = sum|grad f|_eps / Nv and mu E2 = mu |r|^2 / Nr; written to
-// trace[3 * (*counter)] and the counter advanced (so a captured graph can be replayed).
-__global__ void k_energy_finalize(const double *pe2, int n2, const double *pe1, int n1, double inv_nv,
-                                  double mu_over_nr, double *trace, int *counter) {
+// E = E1 + mu E2 with E1 = sum|grad f|_eps / Nv and mu E2 = mu |r|^2 / Nr, and (when
+// pstep is given) |f_k+1 - f_k|_2 from its partials; written to trace[TRACE_W * (*counter)]
+// and the counter advanced (so a captured graph can be replayed).
+__global__ void k_energy_finalize(const double *pe2, int n2, const double *pe1, int n1, const double *pstep,
+                                  int nstep, double inv_nv, double mu_over_nr, double *trace, int *counter) {
     const double q = block_sum_fixed(pe2, n2);
     const double t = block_sum_fixed(pe1, n1);
+    const double d = pstep ? block_sum_fixed(pstep, nstep) : 0.0;
     if (threadIdx.x == 0) {
         const int it = *counter;
         const double e1 = t * inv_nv, e2 = q * mu_over_nr;
-        trace[3 * it + 0] = e1 + e2;
-        trace[3 * it + 1] = e1;
-        trace[3 * it + 2] = e2;
+        trace[TRACE_W * it + 0] = e1 + e2;
+        trace[TRACE_W * it + 1] = e1;
+        trace[TRACE_W * it + 2] = e2;
+        trace[TRACE_W * it + 3] = pstep ? sqrt(d) : 0.0;
         *counter = it + 1;
     }
 }
 
 cudaError_t launch_energy_finalize(const double *pe2, int n2, const double *pe1, int n1, double inv_nv,
-                                   double mu_over_nr, double *trace, int *counter, cudaStream_t s) {
-    k_energy_finalize<<<1, 256, 0, s>>>(pe2, n2, pe1, n1, inv_nv, mu_over_nr, trace, counter);
+                                   double mu_over_nr, double *trace, int *counter, cudaStream_t s,
+                                   const double *pstep, int nstep) {
+    k_energy_finalize<<<1, 256, 0, s>>>(pe2, n2, pe1, n1, pstep, nstep, inv_nv, mu_over_nr, trace, counter);
+    return cudaGetLastError();
+}
+
+// f = v and per-block float64 partials of |v - f_old|^2: the step norm of Algorithm A1
+// while the prox result is moved into the iterate.
+__global__ void k_step_copy(const float *__restrict__ v, float *__restrict__ f, size_t n, double *__restrict__ partial) {
+    step_block(v, f, n, partial, blockIdx.x);
+}
+
+size_t step_partials(size_t n) { return (n + STEP_THREADS - 1) / STEP_THREADS; }
+
+cudaError_t launch_step_copy(const float *v, float *f, size_t n, double *partial, cudaStream_t s) {
+    if (!partial) return cudaMemcpyAsync(f, v, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    k_step_copy<<<(unsigned)step_partials(n), STEP_THREADS, 0, s>>>(v, f, n, partial);
     return cudaGetLastError();
 }
 

@@ -66,7 +66,7 @@ size_t tv_energy_partials(int nx, int ny, int nz) { return ((size_t)nx * ny * nz
 cudaError_t launch_tv_sweep(const TvArgs &a, const float *fin, const float *g, float *fout, bool clamp,
                             double *partial_e1, cudaStream_t s, int *nblocks_out) {
     if (nblocks_out) *nblocks_out = (int)tv_partials(a.nx, a.ny, a.nz);
-    dim3 grid((unsigned)tv_blocks(a.nx, a.ny, a.nz)), block(TV_THREADS);
+    dim3 grid((unsigned)tv_blocks(a.nx, a.ny, a.nz));
     if (clamp) {
         if (partial_e1) launch_sweep<true, true>(a, grid, fin, g, fout, partial_e1, s);
         else launch_sweep<true, false>(a, grid, fin, g, fout, nullptr, s);

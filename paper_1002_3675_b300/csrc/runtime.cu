@@ -256,8 +256,11 @@ cbct_status ensure_workspace(Level *L, bool need_half) {
         return st;
     if (!L->Y && (st = dmalloc((void **)&L->Y, nr * 4, "data")) != CBCT_OK) return st;
     if (need_half && !L->Yh && (st = dmalloc((void **)&L->Yh, nr * 2, "half data")) != CBCT_OK) return st;
+    // [projector partials][TV partials][step-norm partials]; the power iteration
+    // reuses the front of the same buffer
     size_t need = project_partials(L->gd) +
-                  std::max(tv_partials(L->nx, L->ny, L->nz), tv_energy_partials(L->nx, L->ny, L->nz));
+                  std::max(tv_partials(L->nx, L->ny, L->nz), tv_energy_partials(L->nx, L->ny, L->nz)) +
+                  step_partials(nvox);
     size_t dp = 2 * ((nvox + 255) / 256) + 16;
     if (dp > need) need = dp;
     need += 64;
@@ -268,6 +271,11 @@ cbct_status ensure_workspace(Level *L, bool need_half) {
         L->partial_len = need;
     }
     return CBCT_OK;
+}
+
+double *step_region(Level *L) {
+    return L->partial + project_partials(L->gd) +
+           std::max(tv_partials(L->nx, L->ny, L->nz), tv_energy_partials(L->nx, L->ny, L->nz));
 }
 
 cbct_status ensure_mg_workspace(Level *L) {

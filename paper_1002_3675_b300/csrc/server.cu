@@ -222,6 +222,7 @@ void cbct_server::run() {
             j.o.betas = p->betas.empty() ? nullptr : p->betas.data();
             j.o.beta_out = p->result.betas;
             j.o.energy_trace = nullptr;
+            j.o.step_trace = nullptr;
             j.o.kernel_ms = nullptr;
             j.o.kernel_launches = nullptr;
             j.f_out = p->req.f_out_dev;

@@ -72,6 +72,7 @@ def test_batch_equals_single_requests(lib, cuda):
         for (fa, ia), fb, ib in zip(alone, outs, infos):
             assert np.array_equal(fa, host(fb))
             assert np.array_equal(ia["trace"], ib["trace"])
+            assert np.array_equal(ia["step_trace"], ib["step_trace"])
             assert np.array_equal(ia["betas"], ib["betas"])
 
 
@@ -90,6 +91,8 @@ def test_batch_mixes_single_request_and_persistent_launches(lib, cuda):
     for (fa, ia), fb, ib in zip(alone, outs, infos):
         assert np.array_equal(fa, host(fb))
         assert np.array_equal(ia["trace"], ib["trace"])
+        assert np.array_equal(ia["step_trace"], ib["step_trace"])
+        assert np.all(ib["step_trace"] > 0)
 
 
 def test_batch_rejects_shared_geometry(lib):

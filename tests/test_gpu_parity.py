@@ -219,15 +219,18 @@ def test_fbs_small_20_iterations(lib):
     mu, eps = case["mu"], oracle.default_eps(g)
     beta = 1.05 * oracle.gamma(g, mu) * oracle.power_iteration(g, 30)
     Y = f32(case["Y"])
-    f_ref, tr_ref = oracle.fbs(g, Y, mu, beta, eps, 10, 20)
+    f_ref, tr_ref, st_ref = oracle.fbs(g, Y, mu, beta, eps, 10, 20, steps=True)
     G = lib.cbct_geometry_create(g)
     ft = dev(np.zeros((64, 64, 64)))
-    ft, tr = lib.cbct_fbs(G, dev(Y), mu, beta, eps, 10, 0, 20, ft, trace=True)
+    ft, tr, st = lib.cbct_fbs(G, dev(Y), mu, beta, eps, 10, 0, 20, ft, trace=True, step_trace=True)
     f = host(ft)
     assert rel(f, f_ref) <= VOL_TOL, rel(f, f_ref)
     assert (f >= 0).all() and not np.signbit(f).any()
     assert np.all(np.abs(tr - tr_ref) <= 1e-4 * np.abs(tr_ref))
     assert np.all(np.diff(tr[:, 0]) <= 1e-6 * tr[:-1, 0])
+    # |f_k+1 - f_k|: both iterates carry the volume tolerance, so the difference of two
+    # steps is within 2 VOL_TOL |f| on top of the float32 rounding of the step itself
+    assert np.all(np.abs(st - st_ref) <= 1e-4 * st_ref + 2 * VOL_TOL * np.linalg.norm(f_ref)), (st, st_ref)
 
 
 def test_fbs_paper_literal_clamp_mode(lib):
@@ -236,13 +239,15 @@ def test_fbs_paper_literal_clamp_mode(lib):
     mu, eps = case["mu"], oracle.default_eps(g)
     beta = 1.05 * oracle.gamma(g, mu) * oracle.power_iteration(g, 30)
     Y = f32(case["Y"])
-    f_ref, tr_ref = oracle.fbs(g, Y, mu, beta, eps, 10, 10, clamp_mode=1)
+    f_ref, tr_ref, st_ref = oracle.fbs(g, Y, mu, beta, eps, 10, 10, clamp_mode=1, steps=True)
     G = lib.cbct_geometry_create(g)
-    ft, tr = lib.cbct_fbs(G, dev(Y), mu, beta, eps, 10, 1, 10, dev(np.zeros((64, 64, 64))), trace=True)
+    ft, tr, st = lib.cbct_fbs(G, dev(Y), mu, beta, eps, 10, 1, 10, dev(np.zeros((64, 64, 64))), trace=True,
+                              step_trace=True)
     f = host(ft)
     assert rel(f, f_ref) <= VOL_TOL, rel(f, f_ref)
     assert (f >= 0).all()
     assert np.all(np.abs(tr - tr_ref) <= 1e-4 * np.abs(tr_ref))
+    assert np.all(np.abs(st - st_ref) <= 1e-4 * st_ref + 2 * VOL_TOL * np.linalg.norm(f_ref)), (st, st_ref)
 
 
 def test_reconstruct_two_levels_small(lib):
@@ -291,11 +296,15 @@ def test_medium_one_iteration_full_size(lib):
         assert np.all(np.diff(E) <= 1e-5 * E[:-1])
     beta = float(info["betas"][0])
     eps = oracle.default_eps(g)
-    f1 = host(lib.cbct_fbs(G, dev(Y), mu, beta, eps, 10, 0, 1, dev(f_k)))
-    f1_ref, _ = oracle.fbs(g, Y, mu, beta, eps, 10, 1, f0=f_k)
+    f1t, st = lib.cbct_fbs(G, dev(Y), mu, beta, eps, 10, 0, 1, dev(f_k), step_trace=True)
+    f1 = host(f1t)
+    f1_ref, _, st_ref = oracle.fbs(g, Y, mu, beta, eps, 10, 1, f0=f_k, steps=True)
     step_ref = f1_ref - f_k
     assert np.linalg.norm((f1 - f_k) - step_ref) <= 1e-3 * np.linalg.norm(step_ref)
     assert rel(f1, f1_ref) <= 1e-5
+    # the reported step norm is that of the GPU's own two iterates, and the oracle's
+    assert abs(st[0] - np.linalg.norm(f1.astype(np.float64) - f_k)) <= 1e-5 * st[0]
+    assert abs(st[0] - st_ref[0]) <= 1e-3 * st_ref[0]
 
 
 def test_multigrid_transfers(lib):

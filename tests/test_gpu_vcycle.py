@@ -65,6 +65,11 @@ def test_vcycle_energy_falls_every_cycle(lib, small):
     G = lib.cbct_geometry_create(g)
     _, iv = lib.cbct_reconstruct(G, dev(small["Y"]), small["mu"], 5, 2, trace=True, mg_cycle=1)
     assert np.all(np.diff(iv["trace"][:, 0]) < 0) and iv["accepted"][0] >= 1
+    # step_trace: the change of the iterate over each cycle; the first is |f_1| (f_0 = 0)
+    f1 = host(lib.cbct_reconstruct(lib.cbct_geometry_create(g), dev(small["Y"]), small["mu"], 1, 2, mg_cycle=1))
+    st = iv["step_trace"]
+    assert st.shape == (5,) and np.all(st > 0)
+    assert abs(st[0] - np.linalg.norm(f1.astype(np.float64))) <= 1e-5 * st[0]
 
 
 def test_vcycle_is_rejected_where_unsupported(lib, small):

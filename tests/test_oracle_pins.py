@@ -448,24 +448,30 @@ def test_fbs_fixed_point():
     eps = 1e-3
     E = oracle.energy(g, Y, fstar, 2.0, eps)
     assert abs(E[1] - eps) <= 1e-15 and E[2] == 0.0
-    f, _ = oracle.fbs(g, Y, 2.0, 50.0, eps, 5, 3, f0=fstar)
+    f, _, st = oracle.fbs(g, Y, 2.0, 50.0, eps, 5, 3, f0=fstar, steps=True)
     assert np.abs(f - fstar).max() <= 1e-15
+    assert st.shape == (3,) and st.max() <= 1e-14   # |f_k+1 - f_k| at the fixed point
 
 
 def test_fbs_without_tv_is_projected_landweber():
     """Removing the TV term (weight 0, one inner step of length 1/beta) reduces
-    Algorithm A1 to f <- max(0, f - (gamma/beta) A^T (A f - Y)) on the dense matrix."""
+    Algorithm A1 to f <- max(0, f - (gamma/beta) A^T (A f - Y)) on the dense matrix;
+    the step norms |f_k+1 - f_k| are those of that iteration."""
     g = tiny_geometry()
     A = system_matrix(g)
     rng = np.random.default_rng(10)
     Y = rng.uniform(0, 3, size=(6, 8, 8))
     mu, beta = 1.5, 4000.0
-    f, _ = oracle.fbs(g, Y, mu, beta, 1e-3, 1, 15, tv_weight=0.0)
+    f, _, st = oracle.fbs(g, Y, mu, beta, 1e-3, 1, 15, tv_weight=0.0, steps=True)
     gam = 2 * mu * 512 / (6 * 64)
     x = np.zeros(512)
+    dx = []
     for _ in range(15):
-        x = np.maximum(0.0, x - gam / beta * (A.T @ (A @ x - Y.ravel())))
+        xn = np.maximum(0.0, x - gam / beta * (A.T @ (A @ x - Y.ravel())))
+        dx.append(np.linalg.norm(xn - x))
+        x = xn
     assert np.abs(f.ravel() - x).max() <= 1e-12 * max(1.0, np.abs(x).max())
+    assert np.allclose(st, dx, rtol=1e-10, atol=1e-14)
 
 
 @pytest.mark.slow
