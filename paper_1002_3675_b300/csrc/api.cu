@@ -147,27 +147,33 @@ struct Launch {  // wraps one kernel launch with optional timing
     ~Launch() { p.end(); }
 };
 
-// Steps 2 and 3: M sweeps from src0 (ping-pong through A and B), then the result moves
-// into L->f while the partials of |f_k+1 - f_k|^2 (f_k still in L->f) are formed.
+// Steps 2 and 3: M sweeps from src0 (ping-pong through A and B) into L->f, with the
+// partials of |f_k+1 - f_k|^2 (f_k in L->f on entry) in partial_step (*nstep values).
 // partial_e1 (optional) receives the E1 partials of the first sweep's input.
 cbct_status enqueue_prox(Level *L, const SolveParams &P, const float *src0, double *partial_e1, int *ne1,
-                         double *partial_step, Prof &prof, cudaStream_t s) {
+                         double *partial_step, int *nstep, Prof &prof, cudaStream_t s) {
     const TvArgs ta = tv_args(L, P);
+    const bool fused = prox_step_fused(P.M, src0, L->f);
     const float *src = src0;
     for (int m = 0; m < P.M; ++m) {
         const bool last = m == P.M - 1;
-        float *dst = (m % 2 == 0) ? L->A : L->B;
+        float *dst = (last && fused) ? L->f : (m % 2 == 0) ? L->A : L->B;
         if (dst == src) dst = (dst == L->A) ? L->B : L->A;
         const bool clamp = P.clamp_mode == 0 || last;
         {
             Launch l(prof, CBCT_K_TV);
-            CK(launch_tv_sweep(ta, src, L->g, dst, clamp, m == 0 ? partial_e1 : nullptr, s, m == 0 ? ne1 : nullptr),
+            CK(launch_tv_sweep(ta, src, L->g, dst, clamp, m == 0 ? partial_e1 : nullptr, s, m == 0 ? ne1 : nullptr,
+                               (last && fused) ? partial_step : nullptr),
                "tv sweep");
         }
         src = dst;
     }
-    Launch l(prof, CBCT_K_REDUCE);
-    CK(launch_step_copy(src, L->f, vol_elems(L->gd), partial_step, s), "step");
+    if (nstep) *nstep = (int)(fused ? tv_partials(L->nx, L->ny, L->nz) : step_partials(vol_elems(L->gd)));
+    if (!fused || !partial_step) {
+        if (src == L->f) return CBCT_OK;
+        Launch l(prof, CBCT_K_REDUCE);
+        CK(launch_step_copy(src, L->f, vol_elems(L->gd), partial_step, s), "step");
+    }
     return CBCT_OK;
 }
 
@@ -203,12 +209,12 @@ cbct_status enqueue_iteration(cbct_geometry *G, Level *L, const SolveParams &P, 
         CK(launch_axpy(L->g, P.lin, P.lin_scale, vol_elems(gd), s), "linear term");
     }
     double *pstep = step_region(L);
+    int nb_s = 0;
     ST(enqueue_prox(L, P, P.clamp_mode == 0 ? L->f : L->g, P.clamp_mode == 0 ? pt : nullptr,
-                    P.clamp_mode == 0 ? &nb_t : nullptr, pstep, prof, s));
+                    P.clamp_mode == 0 ? &nb_t : nullptr, pstep, &nb_s, prof, s));
     {
         Launch l(prof, CBCT_K_REDUCE);
-        CK(launch_energy_finalize(pp, nb_p, pt, nb_t, P.inv_nv, P.mu_over_nr, dtrace, G->dcounter, s, pstep,
-                                  (int)step_partials(vol_elems(gd))),
+        CK(launch_energy_finalize(pp, nb_p, pt, nb_t, P.inv_nv, P.mu_over_nr, dtrace, G->dcounter, s, pstep, nb_s),
            "energy reduction");
     }
     return CBCT_OK;
@@ -724,7 +730,7 @@ cbct_status cbct_tv_prox(cbct_geometry *G, const float *g_dev, float *f_inout_de
     CK(launch_vol_to_internal(g_dev, L->g, g.nx, g.ny, g.nz, s), "volume layout");
     CK(launch_vol_to_internal(f_inout_dev, L->f, g.nx, g.ny, g.nz, s), "volume layout");
     Prof prof;
-    ST(enqueue_prox(L, P, L->f, nullptr, nullptr, nullptr, prof, s));
+    ST(enqueue_prox(L, P, L->f, nullptr, nullptr, nullptr, nullptr, prof, s));
     CK(launch_vol_to_api(L->f, f_inout_dev, g.nx, g.ny, g.nz, s), "volume layout");
     return CBCT_OK;
 }

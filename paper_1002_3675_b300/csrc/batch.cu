@@ -122,12 +122,14 @@ k_tv_batch(const TvItem *__restrict__ items, const long *__restrict__ start, int
             __syncthreads();
         }
         const long blk = t - first;
+        // (a step-norm sweep is the last of its prox, which always clamps)
         if (it.clamp) {
-            if (it.e1) tv_block<true, true>(it.A, it.fin, it.g, it.fout, it.partial, blk);
-            else tv_block<true, false>(it.A, it.fin, it.g, it.fout, it.partial, blk);
+            if (it.acc == TV_ACC_E1) tv_block<true, TV_ACC_E1>(it.A, it.fin, it.g, it.fout, it.partial, blk);
+            else if (it.acc == TV_ACC_STEP) tv_block<true, TV_ACC_STEP>(it.A, it.fin, it.g, it.fout, it.partial, blk);
+            else tv_block<true, TV_ACC_NONE>(it.A, it.fin, it.g, it.fout, it.partial, blk);
         } else {
-            if (it.e1) tv_block<false, true>(it.A, it.fin, it.g, it.fout, it.partial, blk);
-            else tv_block<false, false>(it.A, it.fin, it.g, it.fout, it.partial, blk);
+            if (it.acc == TV_ACC_E1) tv_block<false, TV_ACC_E1>(it.A, it.fin, it.g, it.fout, it.partial, blk);
+            else tv_block<false, TV_ACC_NONE>(it.A, it.fin, it.g, it.fout, it.partial, blk);
         }
         __syncthreads();
     }
@@ -248,6 +250,15 @@ k_step_batch(const StepItem *__restrict__ items, const long *__restrict__ start,
 // ---------------------------------------------------------------------------------
 // engine
 // ---------------------------------------------------------------------------------
+
+// Step-norm partials of one Algorithm A1 iteration of job j on level L (the rule of
+// the single-request path: fused into the last sweep unless M == 1 from f_k).
+static bool job_step_fused(const Job *j, const Level *L) {
+    return prox_step_fused(j->P.M, j->P.clamp_mode == 0 ? L->f : L->g, L->f);
+}
+static int job_nstep(const Job *j, const Level *L) {
+    return (int)(job_step_fused(j, L) ? tv_partials(L->nx, L->ny, L->nz) : step_partials(vol_elems(L->gd)));
+}
 
 static int sm_count() {
     static int n = 0;
@@ -394,6 +405,14 @@ cbct_status Engine::finish_level(Job *j) {
     return CBCT_OK;
 }
 
+// One TV item as a single-request sweep launch.
+static cbct_status launch_tv_item(const TvItem &it, cudaStream_t s) {
+    ECK(launch_tv_sweep(it.A, it.fin, it.g, it.fout, it.clamp != 0, it.acc == TV_ACC_E1 ? it.partial : nullptr, s,
+                        nullptr, it.acc == TV_ACC_STEP ? it.partial : nullptr),
+        "tv sweep");
+    return CBCT_OK;
+}
+
 // Rebuild the item tables for the current set of (job, phase) pairs.
 cbct_status Engine::build_tables() {
     const size_t ALIGN = 256;
@@ -485,7 +504,7 @@ cbct_status Engine::build_tables() {
                 ei.n1 = (int)(j->P.clamp_mode == 1 ? tv_energy_partials(g.nx, g.ny, g.nz)
                                                    : tv_partials(g.nx, g.ny, g.nz));
                 ei.pstep = step_region(L);
-                ei.nstep = (int)step_partials(vol_elems(g));
+                ei.nstep = job_nstep(j, L);
                 ei.inv_nv = j->P.inv_nv;
                 ei.mu_over_nr = j->P.mu_over_nr;
                 ei.trace = j->G->dtrace;
@@ -556,7 +575,7 @@ cbct_status Engine::build_tables() {
             ei.pe1 = L->partial + np;
             ei.n1 = (int)(j->P.clamp_mode == 1 ? tv_energy_partials(g.nx, g.ny, g.nz) : tv_partials(g.nx, g.ny, g.nz));
             ei.pstep = step_region(L);
-            ei.nstep = (int)step_partials(vol_elems(g));
+            ei.nstep = job_nstep(j, L);
             ei.inv_nv = j->P.inv_nv;
             ei.mu_over_nr = j->P.mu_over_nr;
             ei.trace = j->G->dtrace;
@@ -606,18 +625,19 @@ cbct_status Engine::build_tables() {
         const float *src = j->P.clamp_mode == 0 ? L->f : L->g;
         const long nb = (long)tv_blocks(L->nx, L->ny, L->nz);
         const size_t np = project_partials(L->gd);
+        const bool fused = job_step_fused(j, L);
         for (int m = 0; m < j->P.M; ++m) {
             const bool last = m == j->P.M - 1;
-            float *dst = (m % 2 == 0) ? L->A : L->B;
+            float *dst = (last && fused) ? L->f : (m % 2 == 0) ? L->A : L->B;
             if (dst == src) dst = (dst == L->A) ? L->B : L->A;
             TvItem ti;
             ti.A = ta;
             ti.fin = src;
             ti.g = L->g;
             ti.fout = dst;
-            ti.partial = L->partial + np;
             ti.clamp = (j->P.clamp_mode == 0 || last) ? 1 : 0;
-            ti.e1 = (m == 0 && j->P.clamp_mode == 0) ? 1 : 0;
+            ti.acc = (m == 0 && j->P.clamp_mode == 0) ? TV_ACC_E1 : (last && fused) ? TV_ACC_STEP : TV_ACC_NONE;
+            ti.partial = ti.acc == TV_ACC_STEP ? step_region(L) : L->partial + np;
             if (chain) {
                 chain->tv.push_back(ti);
             } else if (nb >= 16 * sms) {
@@ -629,6 +649,8 @@ cbct_status Engine::build_tables() {
             }
             src = dst;
         }
+        if (chain) chain->step = StepItem{};
+        if (fused) continue;
         StepItem si;
         si.v = src;
         si.f = L->f;
@@ -776,10 +798,8 @@ static cbct_status launch_chain(const Engine::Chain &c, cudaStream_t s) {
         ECK(launch_power_finalize(c.vec.partial, nb, c.vec.lam, c.vec.scale, s), "power finalize");
         ECK(launch_scale(c.vec.y, c.vec.scale, (float *)c.vec.out, (size_t)c.vec.n, s), "power scale");
     }
-    for (const TvItem &it : c.tv)
-        ECK(launch_tv_sweep(it.A, it.fin, it.g, it.fout, it.clamp != 0, it.e1 ? it.partial : nullptr, s, nullptr),
-            "tv sweep");
-    if (!c.power) ECK(launch_step_copy(c.step.v, c.step.f, (size_t)c.step.n, c.step.partial, s), "step");
+    for (const TvItem &it : c.tv) EST(launch_tv_item(it, s));
+    if (c.step.f) ECK(launch_step_copy(c.step.v, c.step.f, (size_t)c.step.n, c.step.partial, s), "step");
     return CBCT_OK;
 }
 
@@ -857,9 +877,7 @@ cbct_status Engine::launch_stages() {
     // TV prox sweeps
     const int tv_per_sm = resident_blocks(k_tv_batch, TV_THREADS, 0);
     for (int m = 0; m < max_m; ++m) {
-        for (const TvItem &it : solo_tv[m])
-            ECK(launch_tv_sweep(it.A, it.fin, it.g, it.fout, it.clamp != 0, it.e1 ? it.partial : nullptr, s, nullptr),
-                "tv sweep");
+        for (const TvItem &it : solo_tv[m]) EST(launch_tv_item(it, s));
         if (htv[m].empty()) continue;
         k_tv_batch<<<(unsigned)persistent_grid(tvtot[m], tv_per_sm), TV_THREADS, 0, s>>>(d_tv[m], d_tstart[m],
                                                                                          (int)htv[m].size(), tvtot[m]);

@@ -43,7 +43,7 @@ struct TvItem {
     float *fout;
     double *partial;
     int clamp;
-    int e1;
+    int acc;  // TV_ACC_NONE, TV_ACC_E1 or TV_ACC_STEP
 };
 
 struct VecItem {  // power-iteration helpers on one volume

@@ -157,9 +157,12 @@ struct TvArgs {
 __host__ __device__ __forceinline__ int tv_rows_per_tile(int nx, int ny, int nz) {
     return (long)nx * ((ny + 15) / 16) * ((nz + 31) / 32) >= 8192 ? 16 : 0;
 }
+// One prox sweep fin -> fout.  partial_e1: the E1 partials of fin; partial_step (fout
+// then holds f_k and is overwritten in place): the partials of (fout_new - f_k)^2.  At
+// most one of the two; tv_partials values either way.
 cudaError_t launch_tv_sweep(const TvArgs &a, const float *fin, const float *g, float *fout, bool clamp,
-                            double *partial_e1, cudaStream_t s, int *nblocks_out);
-size_t tv_partials(int nx, int ny, int nz);         // E1 partials written by a sweep
+                            double *partial_e1, cudaStream_t s, int *nblocks_out, double *partial_step = nullptr);
+size_t tv_partials(int nx, int ny, int nz);         // E1 (or step) partials written by a sweep
 size_t tv_blocks(int nx, int ny, int nz);           // blocks of one sweep launch
 size_t tv_energy_partials(int nx, int ny, int nz);  // partials written by launch_tv_energy
 
@@ -188,6 +191,10 @@ size_t step_partials(size_t n);
 // the step-norm partials inside a level's partials buffer (after the projector's and
 // the TV sweep's)
 double *step_region(Level *L);
+// The last of M prox sweeps from src0 writes f_k+1 over f_k in place and forms the
+// step-norm partials itself unless its input is f_k (M == 1 from f_k); then it goes
+// through a buffer and launch_step_copy.  Number of step partials either way:
+inline bool prox_step_fused(int M, const float *src0, const float *f) { return M >= 2 || src0 != f; }
 cudaError_t launch_step_copy(const float *v, float *f, size_t n, double *partial, cudaStream_t s);
 cudaError_t launch_dot2(const float *x, const float *y, size_t n, double *partial, cudaStream_t s,
                         int *nblocks_out);

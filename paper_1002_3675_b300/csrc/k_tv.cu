@@ -3,22 +3,22 @@
 
 namespace cbct {
 
-template <bool CLAMP, bool E1, bool ANISO, bool WARP>
+template <bool CLAMP, int ACC, bool ANISO, bool WARP>
 __global__ void __launch_bounds__(TV_THREADS)
 k_tv_sweep(TvArgs A, const float *__restrict__ fin, const float *__restrict__ g, float *__restrict__ fout,
            double *__restrict__ partial) {
-    tv_block_t<CLAMP, E1, ANISO, WARP>(A, fin, g, fout, partial, blockIdx.x);
+    tv_block_t<CLAMP, ACC, ANISO, WARP>(A, fin, g, fout, partial, blockIdx.x);
 }
 
-template <bool CLAMP, bool E1>
+template <bool CLAMP, int ACC>
 static void launch_sweep(const TvArgs &a, dim3 grid, const float *fin, const float *g, float *fout, double *p,
                          cudaStream_t s) {
     if (a.aniso) {
-        if (a.jc) k_tv_sweep<CLAMP, E1, true, true><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p);
-        else k_tv_sweep<CLAMP, E1, true, false><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p);
+        if (a.jc) k_tv_sweep<CLAMP, ACC, true, true><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p);
+        else k_tv_sweep<CLAMP, ACC, true, false><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p);
     } else {
-        if (a.jc) k_tv_sweep<CLAMP, E1, false, true><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p);
-        else k_tv_sweep<CLAMP, E1, false, false><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p);
+        if (a.jc) k_tv_sweep<CLAMP, ACC, false, true><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p);
+        else k_tv_sweep<CLAMP, ACC, false, false><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p);
     }
 }
 
@@ -64,15 +64,18 @@ size_t tv_blocks(int nx, int ny, int nz) { return (size_t)((tv_warp_tiles(nx, ny
 size_t tv_energy_partials(int nx, int ny, int nz) { return ((size_t)nx * ny * nz + TV_THREADS - 1) / TV_THREADS; }
 
 cudaError_t launch_tv_sweep(const TvArgs &a, const float *fin, const float *g, float *fout, bool clamp,
-                            double *partial_e1, cudaStream_t s, int *nblocks_out) {
+                            double *partial_e1, cudaStream_t s, int *nblocks_out, double *partial_step) {
     if (nblocks_out) *nblocks_out = (int)tv_partials(a.nx, a.ny, a.nz);
+    if (partial_e1 && partial_step) return cudaErrorInvalidValue;  // one accumulator per sweep
     dim3 grid((unsigned)tv_blocks(a.nx, a.ny, a.nz));
     if (clamp) {
-        if (partial_e1) launch_sweep<true, true>(a, grid, fin, g, fout, partial_e1, s);
-        else launch_sweep<true, false>(a, grid, fin, g, fout, nullptr, s);
+        if (partial_e1) launch_sweep<true, TV_ACC_E1>(a, grid, fin, g, fout, partial_e1, s);
+        else if (partial_step) launch_sweep<true, TV_ACC_STEP>(a, grid, fin, g, fout, partial_step, s);
+        else launch_sweep<true, TV_ACC_NONE>(a, grid, fin, g, fout, nullptr, s);
     } else {
-        if (partial_e1) launch_sweep<false, true>(a, grid, fin, g, fout, partial_e1, s);
-        else launch_sweep<false, false>(a, grid, fin, g, fout, nullptr, s);
+        if (partial_e1) launch_sweep<false, TV_ACC_E1>(a, grid, fin, g, fout, partial_e1, s);
+        else if (partial_step) launch_sweep<false, TV_ACC_STEP>(a, grid, fin, g, fout, partial_step, s);
+        else launch_sweep<false, TV_ACC_NONE>(a, grid, fin, g, fout, nullptr, s);
     }
     return cudaGetLastError();
 }

@@ -260,7 +260,7 @@ cbct_status ensure_workspace(Level *L, bool need_half) {
     // reuses the front of the same buffer
     size_t need = project_partials(L->gd) +
                   std::max(tv_partials(L->nx, L->ny, L->nz), tv_energy_partials(L->nx, L->ny, L->nz)) +
-                  step_partials(nvox);
+                  std::max(step_partials(nvox), tv_partials(L->nx, L->ny, L->nz));
     size_t dp = 2 * ((nvox + 255) / 256) + 16;
     if (dp > need) need = dp;
     need += 64;

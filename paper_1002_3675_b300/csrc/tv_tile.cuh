@@ -10,8 +10,10 @@
 // Anisotropic (A.aniso == 1): sum_j sum_d sqrt((D_d f)_j^2 + eps^2), gradient
 // sum_d D_d^T (D_d f / sqrt((D_d f)^2 + eps^2)), a 7-point stencil.  In both,
 //   (D_d^T p)_i = (p_{i-1} [i > 0] - p_i [i < n-1]) / h_d.
-// The sweep also emits the partial sums of |grad f|_eps of its input (the
-// E1 energy of the entering iterate when the input is f_k).
+// A sweep also emits one of two partial sums (ACC): those of |grad f|_eps of its
+// input (TV_ACC_E1: the E1 energy of the entering iterate when the input is f_k), or,
+// on the last sweep of an Algorithm A1 iteration, which overwrites f_k in place with
+// f_k+1, those of (f_k+1 - f_k)^2 (TV_ACC_STEP: the step norm).
 //
 // Layout [nx][ny][nz] (z fastest); one thread per voxel, consecutive lanes along z.
 #include "cbct_internal.h"
@@ -19,6 +21,7 @@
 namespace cbct {
 
 constexpr int TV_THREADS = 256;
+constexpr int TV_ACC_NONE = 0, TV_ACC_E1 = 1, TV_ACC_STEP = 2;
 
 // grad TV_eps at voxel idx (internal layout) and, if E1, the voxel's term of TV_eps
 // itself (|grad f|_eps, or the sum over the axes in the anisotropic reading).  Shared
@@ -100,8 +103,8 @@ __device__ __forceinline__ float tv_div(const TvArgs &A, const float *__restrict
 // recomputed: the p_y term at (i, j-1) is the previous row's own term, the p_z term
 // at (i, j, k-1) is the lower lane's own term (lane 0 of a tile that does not start
 // at k = 0 computes it), and f(i, j, k), f(i-1, j, k) come from the previous row's
-// loads.  Each tile writes one float64 partial of the E1 terms of its voxels
-// (float32 along the rows, then over the lanes).
+// loads.  Each tile writes one float64 partial of the E1 (or step) terms of its
+// voxels (float32 along the rows, then over the lanes).
 constexpr int TV_WARPS = TV_THREADS / 32;
 
 // Warp tiles of a sweep (row walks), or, for the per-voxel form, 8 per block of
@@ -153,9 +156,10 @@ __device__ __forceinline__ float tv_px_minus(const TvArgs &A, float c, float m, 
     return __fmul_rn(ax, rsqrtf(__fmaf_rn(ax, ax, __fmaf_rn(ay, ay, __fmaf_rn(az, az, A.eps2)))));
 }
 
-template <bool CLAMP, bool E1, bool ANISO>
+template <bool CLAMP, int ACC, bool ANISO>
 __device__ __forceinline__ void tv_warp(const TvArgs &A, const float *__restrict__ fin, const float *__restrict__ g,
                                         float *__restrict__ fout, double *__restrict__ partial, const long wtile) {
+    constexpr bool E1 = ACC == TV_ACC_E1;
     const int lane = threadIdx.x & 31;
     const int nkb = (A.nz + 31) >> 5, njc = (A.ny + A.jc - 1) / A.jc;
     const int kb = (int)(wtile % nkb);
@@ -204,7 +208,12 @@ __device__ __forceinline__ void tv_warp(const TvArgs &A, const float *__restrict
         if (zm) div = __fmaf_rn(pz_lo, A.ihz, div);
         if (kin) {
             const float x = __fmaf_rn(-A.s, __fmaf_rn(A.beta, __fsub_rn(c, __ldg(g + o)), div), c);
-            fout[o] = CLAMP ? fmaxf(x, 0.f) : x;
+            const float y = CLAMP ? fmaxf(x, 0.f) : x;
+            if (ACC == TV_ACC_STEP) {  // fout holds f_k here (read before it is overwritten)
+                const float d = __fsub_rn(y, fout[o]);
+                e1 = __fmaf_rn(d, d, e1);
+            }
+            fout[o] = y;
             if (E1) e1 = __fadd_rn(e1, own.e1);
         }
         py_prev = own.py;
@@ -212,7 +221,7 @@ __device__ __forceinline__ void tv_warp(const TvArgs &A, const float *__restrict
         m = myp;
         o += sy;
     }
-    if (E1) {
+    if (ACC != TV_ACC_NONE) {
         // float32 along the rows, a pairwise tree over the lanes, one float64 per tile
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) e1 += __shfl_down_sync(0xffffffffu, e1, off);
@@ -222,9 +231,10 @@ __device__ __forceinline__ void tv_warp(const TvArgs &A, const float *__restrict
 
 // One thread per voxel (small or oddly sized volumes): the same arithmetic, one E1
 // partial per block (float32 within a warp, float64 across the warps).
-template <bool CLAMP, bool E1, bool ANISO>
+template <bool CLAMP, int ACC, bool ANISO>
 __device__ __forceinline__ void tv_voxels(const TvArgs &A, const float *__restrict__ fin, const float *__restrict__ g,
                                           float *__restrict__ fout, double *__restrict__ partial, const long blk) {
+    constexpr bool E1 = ACC == TV_ACC_E1;
     const size_t n = (size_t)A.nx * A.ny * A.nz;
     const size_t idx = (size_t)blk * TV_THREADS + threadIdx.x;
     float e1 = 0.f;
@@ -232,9 +242,14 @@ __device__ __forceinline__ void tv_voxels(const TvArgs &A, const float *__restri
         const float f0 = __ldg(fin + idx);
         const float div = tv_div<E1, ANISO>(A, fin, idx, e1);
         const float x = __fmaf_rn(-A.s, __fmaf_rn(A.beta, __fsub_rn(f0, __ldg(g + idx)), div), f0);
-        fout[idx] = CLAMP ? fmaxf(x, 0.f) : x;
+        const float y = CLAMP ? fmaxf(x, 0.f) : x;
+        if (ACC == TV_ACC_STEP) {
+            const float d = __fsub_rn(y, fout[idx]);
+            e1 = __fmul_rn(d, d);
+        }
+        fout[idx] = y;
     }
-    if (E1) {
+    if (ACC != TV_ACC_NONE) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) e1 += __shfl_down_sync(0xffffffffu, e1, off);
         __shared__ double red[TV_WARPS];
@@ -250,28 +265,28 @@ __device__ __forceinline__ void tv_voxels(const TvArgs &A, const float *__restri
 }
 
 // One block of the sweep (block index blk): TV_WARPS row-walking warp tiles (WARP), or
-// TV_THREADS voxels in the per-voxel form.
-template <bool CLAMP, bool E1, bool ANISO, bool WARP>
+// TV_THREADS voxels in the per-voxel form.  With TV_ACC_STEP, fout holds f_k on entry.
+template <bool CLAMP, int ACC, bool ANISO, bool WARP>
 __device__ __forceinline__ void tv_block_t(const TvArgs &A, const float *__restrict__ fin, const float *__restrict__ g,
                                            float *__restrict__ fout, double *__restrict__ partial, const long blk) {
     if (!WARP) {
-        tv_voxels<CLAMP, E1, ANISO>(A, fin, g, fout, partial, blk);
+        tv_voxels<CLAMP, ACC, ANISO>(A, fin, g, fout, partial, blk);
         return;
     }
     const long wt = blk * TV_WARPS + (threadIdx.x >> 5);
-    if (wt < tv_warp_tiles(A.nx, A.ny, A.nz)) tv_warp<CLAMP, E1, ANISO>(A, fin, g, fout, partial, wt);
+    if (wt < tv_warp_tiles(A.nx, A.ny, A.nz)) tv_warp<CLAMP, ACC, ANISO>(A, fin, g, fout, partial, wt);
 }
 
 // The same with the reading and the form chosen at run time (batched kernels).
-template <bool CLAMP, bool E1>
+template <bool CLAMP, int ACC>
 __device__ __forceinline__ void tv_block(const TvArgs &A, const float *__restrict__ fin, const float *__restrict__ g,
                                          float *__restrict__ fout, double *__restrict__ partial, const long blk) {
     if (A.aniso) {
-        if (A.jc) tv_block_t<CLAMP, E1, true, true>(A, fin, g, fout, partial, blk);
-        else tv_block_t<CLAMP, E1, true, false>(A, fin, g, fout, partial, blk);
+        if (A.jc) tv_block_t<CLAMP, ACC, true, true>(A, fin, g, fout, partial, blk);
+        else tv_block_t<CLAMP, ACC, true, false>(A, fin, g, fout, partial, blk);
     } else {
-        if (A.jc) tv_block_t<CLAMP, E1, false, true>(A, fin, g, fout, partial, blk);
-        else tv_block_t<CLAMP, E1, false, false>(A, fin, g, fout, partial, blk);
+        if (A.jc) tv_block_t<CLAMP, ACC, false, true>(A, fin, g, fout, partial, blk);
+        else tv_block_t<CLAMP, ACC, false, false>(A, fin, g, fout, partial, blk);
     }
 }
 
