@@ -75,6 +75,7 @@ template <int VPL>
 __global__ void __launch_bounds__(BP_THREADS, 8)
 k_bp_batch(const BpItem *__restrict__ items, const long *__restrict__ start, int n, long total) {
     __shared__ BpItem it[BP_THREADS / 32];
+    __shared__ float4 rec[(BP_THREADS / 32) * BP_REC_PER_WARP];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long stride = (long)gridDim.x * (BP_THREADS / 32);
     int cur = -1;
@@ -89,7 +90,8 @@ k_bp_batch(const BpItem *__restrict__ items, const long *__restrict__ start, int
             first = __ldg(start + r);
             next = r + 1 < n ? __ldg(start + r + 1) : total;
         }
-        bp_warp<VPL>(it[w].G, it[w].mode, it[w].rs, it[w].fin, it[w].out, it[w].c, t - first);
+        bp_warp<VPL>(it[w].G, it[w].mode, it[w].rs, it[w].fin, it[w].out, it[w].c, t - first,
+                     rec + w * BP_REC_PER_WARP);
     }
 }
 

@@ -10,10 +10,10 @@
 // g = f - c P^T r with c = gamma / beta.
 //
 // Work decomposition.  One warp owns 32*VPL voxels of one z-column (i, j); lane l
-// holds the consecutive voxels k = base + VPL l + v, v < VPL.  Per view, the detector
-// columns whose ray plane meets the xy-cell come from a precomputed table; for each,
-// the part of the rays' horizontal parameter t inside the cell, [tlo, thi], is the
-// same for the whole z-column.
+// holds the consecutive voxels k = base + VPL l + v, v < VPL.  The (view, detector
+// column) pairs whose ray plane meets the xy-cell come from a precomputed per-cell
+// table; for each, the part of the rays' horizontal parameter t inside the cell,
+// [tlo, thi], is the same for the whole z-column.
 //
 // Plane sweep.  In detector-row units, a ray b sits at row b and the plane z at
 // rho_z(t) = z D / ((tS + t) dv) + cv, monotone in t.  Ray b is inside voxel k at t iff
@@ -70,10 +70,19 @@ __host__ __device__ __forceinline__ long bp_warp_tiles(const GeoDev &G) {
 // 31).  mode: BP_PLAIN writes P^T rs, BP_STEP writes fin - c P^T rs.  Shared by the
 // single-request and batched kernels, so a request's result does not depend on what
 // else is in the launch.
+//
+// The cell's candidate (view, column) pairs are taken 32 at a time: each lane first
+// sets up one pair (its t-interval inside the cell, the row slopes at both ends and
+// the chunk's top plane) into the warp's record buffer rec (2 float4 per lane, shared
+// memory), then the warp walks the valid pairs in table order, reading each record as
+// a broadcast.  The sums are taken in the same order as a pair-by-pair walk.
+constexpr int BP_REC_PER_WARP = 64;  // float4 records of one warp
+
 template <int VPL>
 __device__ __forceinline__ void bp_warp(const GeoDev &G, const int mode, const float *__restrict__ rs,
                                          const float *__restrict__ fin, float *__restrict__ out, const float c,
-                                         const long wtile) {
+                                         const long wtile, float4 *__restrict__ rec) {
+    constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int nkc = (G.nz + 32 * VPL - 1) / (32 * VPL);
     const int kc = (int)(wtile % nkc);
@@ -81,67 +90,84 @@ __device__ __forceinline__ void bp_warp(const GeoDev &G, const int mode, const f
     const int j = (int)(colid % G.ny);
     const int i = (int)(colid / G.ny);
     const int base = kc * 32 * VPL + lane * VPL;     // first voxel of this lane
-    float zb[VPL], acc[VPL];
+    float acc[VPL];
 #pragma unroll
-    for (int v = 0; v < VPL; ++v) {
-        zb[v] = plane_at(base + v, G.hz, G.z0);
-        acc[v] = 0.f;
-    }
-    const float ztop = plane_at(kc * 32 * VPL + 32 * VPL, G.hz, G.z0);
-    const float xl = plane_at(i, G.hx, G.x0), xh = plane_at(i + 1, G.hx, G.x0);
-    const float yl = plane_at(j, G.hy, G.y0), yh = plane_at(j + 1, G.hy, G.y0);
+    for (int v = 0; v < VPL; ++v) acc[v] = 0.f;
+    const unsigned p0 = __ldg(G.cell_start + colid), p1 = __ldg(G.cell_start + colid + 1);
 #pragma unroll 1
-    for (int ia = 0; ia < G.na; ++ia) {
-        const short2 ar = G.arange[((size_t)ia * G.nx + i) * G.ny + j];
-        const float *rsv = rs + (size_t)ia * G.nu * G.nv;
-#pragma unroll 1
-        for (int a = ar.x; a <= ar.y; ++a) {
-            const float4 rxy = G.ray_xy[(size_t)ia * G.nu + a];
+    for (unsigned pb = p0; pb < p1; pb += 32) {
+        // setup of pair pb + lane
+        bool ok = false;
+        if (pb + lane < p1) {
+            const float xl = plane_at(i, G.hx, G.x0), xh = plane_at(i + 1, G.hx, G.x0);
+            const float yl = plane_at(j, G.hy, G.y0), yh = plane_at(j + 1, G.hy, G.y0);
+            const unsigned pr = __ldg(G.pairs + pb + lane);
+            const int a = (int)(pr & 0x7fffu);
+            const int col = (int)(pr >> 15) * G.nu + a;
+            const float4 rxy = __ldg(G.ray_xy + col);
             float tlo = -INFINITY, thi = INFINITY;
+            ok = true;
             if (rxy.z != 0.f) {
                 const float t1 = t_cross(xl, rxy.x, rxy.z), t2 = t_cross(xh, rxy.x, rxy.z);
                 tlo = fminf(t1, t2);
                 thi = fmaxf(t1, t2);
             } else if (!(rxy.x >= xl && rxy.x < xh)) {
-                continue;
+                ok = false;
             }
             if (rxy.w != 0.f) {
                 const float t1 = t_cross(yl, rxy.y, rxy.w), t2 = t_cross(yh, rxy.y, rxy.w);
                 tlo = fmaxf(tlo, fminf(t1, t2));
                 thi = fminf(thi, fmaxf(t1, t2));
             } else if (!(rxy.y >= yl && rxy.y < yh)) {
-                continue;
+                ok = false;
             }
-            if (!(thi > tlo)) continue;
-            const float2 Dt = G.col[a];
-            const float q1 = __fdividef(Dt.x, Dt.y + tlo) * G.inv_dv;
-            const float q2 = __fdividef(Dt.x, Dt.y + thi) * G.inv_dv;
+            ok = ok && thi > tlo;
+            if (ok) {
+                const float2 Dt = __ldg(G.col + a);
+                const float q1 = __fdividef(Dt.x, Dt.y + tlo) * G.inv_dv;
+                const float q2 = __fdividef(Dt.x, Dt.y + thi) * G.inv_dv;
+                int nt;
+                float pt;
+                eval_plane(plane_at(kc * 32 * VPL + 32 * VPL, G.hz, G.z0), q1, q2, G.cv, G.nv, tlo, thi,
+                           G.ray_zc + (size_t)a * G.nv, rs + (size_t)col * G.nv, nt, pt);
+                rec[2 * lane] = make_float4(tlo, thi, q1, q2);
+                rec[2 * lane + 1] = make_float4(__int_as_float(col), __int_as_float(a), __int_as_float(nt), pt);
+            }
+        }
+        unsigned valid = __ballot_sync(FULL, ok);
+        __syncwarp();
+#pragma unroll 1
+        while (valid) {
+            const int src = __ffs(valid) - 1;
+            valid &= valid - 1;
+            const float4 r0 = rec[2 * src], r1 = rec[2 * src + 1];
+            const float tlo = r0.x, thi = r0.y, q1 = r0.z, q2 = r0.w;
+            const int col = __float_as_int(r1.x), a = __float_as_int(r1.y);
             const float w = thi - tlo;
             const float2 *rzp = G.ray_zc + (size_t)a * G.nv;
-            const float *rsp = rsv + (size_t)a * G.nv;
-            const float2 *cum = G.rowsum + ((size_t)ia * G.nu + a) * (G.nv + 1);
+            const float *rsp = rs + (size_t)col * G.nv;
+            const float2 *cum = G.rowsum + (size_t)col * (G.nv + 1);
             int nb[VPL + 1];
-            float pb[VPL + 1];
+            float pbv[VPL + 1];
 #pragma unroll
-            for (int v = 0; v < VPL; ++v) eval_plane(zb[v], q1, q2, G.cv, G.nv, tlo, thi, rzp, rsp, nb[v], pb[v]);
-            int nt;
-            float pt;
-            eval_plane(ztop, q1, q2, G.cv, G.nv, tlo, thi, rzp, rsp, nt, pt);
-            nb[VPL] = __shfl_down_sync(0xffffffffu, nb[0], 1);
-            pb[VPL] = __shfl_down_sync(0xffffffffu, pb[0], 1);
+            for (int v = 0; v < VPL; ++v)
+                eval_plane(plane_at(base + v, G.hz, G.z0), q1, q2, G.cv, G.nv, tlo, thi, rzp, rsp, nb[v], pbv[v]);
+            nb[VPL] = __shfl_down_sync(FULL, nb[0], 1);
+            pbv[VPL] = __shfl_down_sync(FULL, pbv[0], 1);
             if (lane == 31) {
-                nb[VPL] = nt;
-                pb[VPL] = pt;
+                nb[VPL] = __float_as_int(r1.z);
+                pbv[VPL] = r1.w;
             }
             float2 c0 = __ldg(cum + nb[0]);
 #pragma unroll
             for (int v = 0; v < VPL; ++v) {
                 const float2 c1 = __ldg(cum + nb[v + 1]);
                 const float full = __fadd_rn(__fsub_rn(c1.x, c0.x), __fsub_rn(c1.y, c0.y));
-                acc[v] += __fmaf_rn(w, full, pb[v + 1] - pb[v]);
+                acc[v] += __fmaf_rn(w, full, pbv[v + 1] - pbv[v]);
                 c0 = c1;
             }
         }
+        __syncwarp();  // the next chunk's setup overwrites the records
     }
 #pragma unroll
     for (int v = 0; v < VPL; ++v) {

@@ -42,7 +42,9 @@ struct GeoDev {
     const float4 *ray_z;         // [nu][nv]  zO, cot(phi), sec(phi), tan(phi)  (cot = 0: v = 0)
     const float2 *ray_zc;        // [nu][nv]  zO, cot(phi) (same values; the adjoint's table)
     const float2 *col;           // [nu]      D = |d_xy|, t_S (source-to-O distance)
-    const short2 *arange;        // [na][nx][ny] first/last detector column meeting each xy-cell
+    const unsigned *cell_start;  // [nx*ny+1] first entry of each xy-cell (i ny + j) in pairs
+    const unsigned *pairs;       // (view << 15 | column) of every detector column whose ray plane
+                                 // meets the cell, per cell in view then column order
     const float2 *view;          // [na]      cos, sin
     float2 *rowsum;              // [na][nu][nv+1] running sums of the scaled residual along each
                                  // detector column, float64 split as (hi, lo) float32 (workspace)

@@ -3,14 +3,16 @@
 
 namespace cbct {
 
-// at most 51 registers per thread (48 used): 10 blocks of 128 threads per SM
+// at most 51 registers per thread (48 used): 10 blocks of 128 threads per SM (64
+// registers for 4 voxels per lane); dynamic shared memory: the warps' setup records
 template <int MODE, int VPL>
-__global__ void __launch_bounds__(256, 5)
+__global__ void __launch_bounds__(256, VPL == 4 ? 4 : 5)
 k_backproject(GeoDev G, const float *__restrict__ rs, const float *__restrict__ fin,
               float *__restrict__ out, float c) {
+    extern __shared__ float4 rec[];
     const long gwarp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gwarp >= bp_warp_tiles<VPL>(G)) return;
-    bp_warp<VPL>(G, MODE, rs, fin, out, c, gwarp);
+    bp_warp<VPL>(G, MODE, rs, fin, out, c, gwarp, rec + (threadIdx.x >> 5) * BP_REC_PER_WARP);
 }
 
 template <int VPL>
@@ -18,10 +20,11 @@ static void launch_vpl(const GeoDev &g, const float *rs, const float *fin, float
                        cudaStream_t s) {
     const int T = (g.bp_threads == 64 || g.bp_threads == 256) ? g.bp_threads : BP_THREADS;
     const long nb = (bp_warp_tiles<VPL>(g) * 32 + T - 1) / T;
+    const size_t smem = (size_t)(T / 32) * BP_REC_PER_WARP * sizeof(float4);
     if (mode == BP_PLAIN)
-        k_backproject<BP_PLAIN, VPL><<<(unsigned)nb, T, 0, s>>>(g, rs, fin, out, c);
+        k_backproject<BP_PLAIN, VPL><<<(unsigned)nb, T, smem, s>>>(g, rs, fin, out, c);
     else
-        k_backproject<BP_STEP, VPL><<<(unsigned)nb, T, 0, s>>>(g, rs, fin, out, c);
+        k_backproject<BP_STEP, VPL><<<(unsigned)nb, T, smem, s>>>(g, rs, fin, out, c);
 }
 
 // Running sums of rs along every detector column (one thread per column, float64, in
