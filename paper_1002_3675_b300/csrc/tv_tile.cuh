@@ -183,42 +183,55 @@ __device__ __forceinline__ void tv_warp(const TvArgs &A, const float *__restrict
         const float bzp = zp ? __ldg(fin + o - sy + 1) : b;
         py_prev = tv_own<false, ANISO>(A, b, bxp, c, bzp).py;
     }
+    // the loads of row j (fy: +y, fx: +x, fz: +z, my/mz: the +y/+z neighbours of
+    // f(i-1, j, k), gv: g, d*: the halo voxel (i, j, k-1) and its +x/+y neighbours),
+    // issued one row ahead so that they are in flight during the previous row's
+    // arithmetic
+    float fy, fx, fz, my, mz, gv, d, dx, dy;
+    auto load_row = [&](int jr, size_t orow, float cr, float mr, float &ly, float &lx, float &lz, float &lmy,
+                        float &lmz, float &lg, float &ld, float &ldx, float &ldy) {
+        const bool ypr = jr < A.ny - 1;
+        ly = ypr ? __ldg(fin + orow + sy) : cr;
+        lx = xp ? __ldg(fin + orow + sx) : cr;
+        lz = zp ? __ldg(fin + orow + 1) : cr;
+        lmy = (xm && ypr) ? __ldg(fin + orow - sx + sy) : mr;
+        lmz = (xm && zp) ? __ldg(fin + orow - sx + 1) : mr;
+        lg = __ldg(g + orow);
+        if (halo) {
+            ld = __ldg(fin + orow - 1);
+            ldx = xp ? __ldg(fin + orow - 1 + sx) : ld;
+            ldy = ypr ? __ldg(fin + orow - 1 + sy) : ld;
+        } else {
+            ld = ldx = ldy = 0.f;
+        }
+    };
+    load_row(j0, o, c, m, fy, fx, fz, my, mz, gv, d, dx, dy);
 #pragma unroll 1
     for (int j = j0; j < j1; ++j) {
-        const bool yp = j < A.ny - 1;
-        const float fyp = yp ? __ldg(fin + o + sy) : c;
-        const float fxp = xp ? __ldg(fin + o + sx) : c;
-        const float fzp = zp ? __ldg(fin + o + 1) : c;
-        const TvOwn own = tv_own<E1, ANISO>(A, c, fxp, fyp, fzp);
+        // next row: its own value is fy, its (i-1) value my
+        float nfy = 0.f, nfx = 0.f, nfz = 0.f, nmy = 0.f, nmz = 0.f, ngv = 0.f, nd = 0.f, ndx = 0.f, ndy = 0.f;
+        if (j + 1 < j1) load_row(j + 1, o + sy, fy, my, nfy, nfx, nfz, nmy, nmz, ngv, nd, ndx, ndy);
+        const TvOwn own = tv_own<E1, ANISO>(A, c, fx, fy, fz);
         float div = own.div;
-        float myp = 0.f;
-        if (xm) {
-            myp = yp ? __ldg(fin + o - sx + sy) : m;
-            const float mzp = zp ? __ldg(fin + o - sx + 1) : m;
-            div = __fmaf_rn(tv_px_minus<ANISO>(A, c, m, myp, mzp), A.ihx, div);
-        }
+        if (xm) div = __fmaf_rn(tv_px_minus<ANISO>(A, c, m, my, mz), A.ihx, div);
         if (j > 0) div = __fmaf_rn(py_prev, A.ihy, div);
         float pz_lo = __shfl_up_sync(0xffffffffu, own.pz, 1);
-        if (halo) {  // own term of (i, j, k-1)
-            const float d = __ldg(fin + o - 1);
-            const float dxp = xp ? __ldg(fin + o - 1 + sx) : d;
-            const float dyp = yp ? __ldg(fin + o - 1 + sy) : d;
-            pz_lo = tv_own<false, ANISO>(A, d, dxp, dyp, c).pz;
-        }
+        if (halo) pz_lo = tv_own<false, ANISO>(A, d, dx, dy, c).pz;  // own term of (i, j, k-1)
         if (zm) div = __fmaf_rn(pz_lo, A.ihz, div);
         if (kin) {
-            const float x = __fmaf_rn(-A.s, __fmaf_rn(A.beta, __fsub_rn(c, __ldg(g + o)), div), c);
+            const float x = __fmaf_rn(-A.s, __fmaf_rn(A.beta, __fsub_rn(c, gv), div), c);
             const float y = CLAMP ? fmaxf(x, 0.f) : x;
             if (ACC == TV_ACC_STEP) {  // fout holds f_k here (read before it is overwritten)
-                const float d = __fsub_rn(y, fout[o]);
-                e1 = __fmaf_rn(d, d, e1);
+                const float dd = __fsub_rn(y, fout[o]);
+                e1 = __fmaf_rn(dd, dd, e1);
             }
             fout[o] = y;
             if (E1) e1 = __fadd_rn(e1, own.e1);
         }
         py_prev = own.py;
-        c = fyp;
-        m = myp;
+        c = fy;
+        m = my;
+        fy = nfy; fx = nfx; fz = nfz; my = nmy; mz = nmz; gv = ngv; d = nd; dx = ndx; dy = ndy;
         o += sy;
     }
     if (ACC != TV_ACC_NONE) {
