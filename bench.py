@@ -635,6 +635,37 @@ def run_vcycle(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_kernels(args, world, rank, local):
+    """Profiler target: `--steps` Algorithm A1 iterations on the finest level of the
+    workload at its full size, with a fixed beta (no power iteration), so that the
+    k-th launch of each kernel is the k-th iteration's.  Prints the ms per iteration."""
+    import torch
+
+    from paper_1002_3675_b300 import cbct
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = synth.CONFIGS[args.workload]
+    case = synth.make_case(args.workload)
+    G = cbct.cbct_geometry_create(case["geom"])
+    mu = cfg["mu"]
+    Y = torch.tensor(np.asarray(case["Y"], dtype=np.float32), device=dev)
+    f = torch.zeros((cfg["vol"][2], cfg["vol"][1], cfg["vol"][0]), dtype=torch.float32, device=dev)
+    g = case["geom"]
+    eps = 2e-5 / min(g["hx"], g["hy"], g["hz"])
+    beta = 10.0 * mu * 1e3  # fixed: the step size does not change the work of an iteration
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cbct.cbct_fbs(G, Y, mu, beta, eps, 10, 0, args.steps, f, tv_mode=args.tv_mode)
+    e1.record(stream)
+    e1.synchronize()
+    if rank == 0:
+        ms = e0.elapsed_time(e1)
+        print(json.dumps({"mode": "kernels", "workload": args.workload, "iterations": args.steps,
+                          "ms_per_iteration": ms / max(args.steps, 1)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -643,7 +674,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="medium", choices=sorted(WORKLOAD_TEXT))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "vcycle"])
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "vcycle", "kernels"],
+                    help="kernels: --steps single-level iterations at full size (a profiler target)")
     ap.add_argument("--cycles", type=int, default=10, help="vcycle: V-cycles per step")
     ap.add_argument("--tv-mode", type=int, default=0, choices=[0, 1], help="E1: 0 isotropic, 1 anisotropic")
     ap.add_argument("--sino-fp16", action="store_true", help="keep the projection data in half precision")
@@ -668,6 +700,8 @@ def main():
         run_serve(args, world, rank, local)
     elif args.mode == "vcycle":
         run_vcycle(args, world, rank, local)
+    elif args.mode == "kernels":
+        run_kernels(args, world, rank, local)
     else:
         run_gpu(args, world, rank, local)
     if world > 1:

@@ -46,17 +46,24 @@ __device__ __forceinline__ float y_crossing(const GeoDev &G, const ColumnRay &c,
     return t_cross(plane_at(c.j0 + (c.sj > 0 ? m : 1 - m), G.hy, G.y0), c.Oy, c.iy);
 }
 
-// number of m in [1, mmax] with crossing(m) < v (strict) or <= v (inclusive)
+// number of m in [1, mmax] with crossing(m) < v (strict) or <= v (inclusive).  The
+// crossings are evenly spaced in exact arithmetic and monotone in float32, so the
+// count is a linear estimate corrected by a walk over the float32 values themselves
+// (the same count as a search of the sequence).
 template <bool X, bool INCL>
 __device__ __forceinline__ int count_before(const GeoDev &G, const ColumnRay &c, int mmax, float v) {
-    int lo = 0, hi = mmax;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        const float t = X ? x_crossing(G, c, mid) : y_crossing(G, c, mid);
-        if (INCL ? (t <= v) : (t < v)) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
+    if (mmax <= 0) return 0;
+    const float t1 = X ? x_crossing(G, c, 1) : y_crossing(G, c, 1);
+    const float rate = X ? fabsf(c.ex) * G.inv_hx : fabsf(c.ey) * G.inv_hy;  // crossings per unit t
+    const float est = (v - t1) * rate;
+    int m = est >= 0.f ? min((int)fminf(est, (float)mmax) + 1, mmax) : 0;
+    auto before = [&](int q) {
+        const float t = X ? x_crossing(G, c, q) : y_crossing(G, c, q);
+        return INCL ? (t <= v) : (t < v);
+    };
+    while (m < mmax && before(m + 1)) ++m;
+    while (m > 0 && !before(m)) --m;
+    return m;
 }
 
 __device__ __forceinline__ ColumnRay column_setup(const GeoDev &G, int ia, int a) {
@@ -242,7 +249,8 @@ __device__ __forceinline__ void project_tile(const GeoDev &G, const int mode, co
 
     // ---- 2./3. bands of z-levels: running slice integrals, then the rays ---------------
     const int c_cap = proj_smem_of(G) / 4 - 2 * slots;
-    const int kband = S > 0 ? max(1, min(G.nz, c_cap / (S + max_chunks))) : G.nz;
+    int kband = S > 0 ? max(1, min(G.nz, c_cap / (S + max_chunks))) : G.nz;
+    if (kband >= 32 && kband < G.nz) kband &= ~31;  // whole 32-level groups: full warps, aligned loads
     for (int kb = 0; kb < G.nz && S > 0; kb += kband) {
         const int nk = min(kband, G.nz - kb);
         float *C = coff + max_chunks * nk;        // [s][kk], chunk-local running sums
