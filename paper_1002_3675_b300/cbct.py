@@ -77,7 +77,9 @@ class ServerStats(C.Structure):
 
 
 def _load() -> C.CDLL:
-    path = _build.build()          # compiles in-tree if missing or stale; raises on failure
+    # CBCT_LIBRARY: an explicitly chosen build of the library (e.g. one with other
+    # launch shapes); otherwise the in-tree build, compiled if missing or stale
+    path = os.environ.get("CBCT_LIBRARY") or _build.build()
     return C.CDLL(path)
 
 

@@ -142,12 +142,13 @@ constexpr int CHUNK = 1 << CHUNK_LOG;
 constexpr int PROJ_BATCH = 8;           // voxel loads in flight per thread
 
 // Projector block size (rows per tile): G.proj_threads if valid, else the default: one
-// thread per row up to 256 rows, 512 threads above (timed on B300 for 96 to 384 rows;
-// more threads shorten the segment and running-sum phases that every row waits for).
+// thread per row up to 128 rows, 256 threads up to 256 rows, 512 above (timed on B300
+// for 96 to 384 rows; more threads shorten the segment and running-sum phases that
+// every row waits for).
 __host__ __device__ __forceinline__ int proj_threads_of(const GeoDev &g) {
     const int need = min(PROJ_MAX_THREADS, 32 * ((g.nv + 31) / 32));
     if (g.proj_threads >= need && g.proj_threads <= PROJ_MAX_THREADS && g.proj_threads % 32 == 0) return g.proj_threads;
-    return need <= 256 ? need : PROJ_MAX_THREADS;
+    return need <= 128 ? need : need <= 256 ? 256 : PROJ_MAX_THREADS;
 }
 
 // Bytes of shared memory the projector tile may use: G.proj_smem if valid, else as much
@@ -162,22 +163,6 @@ __host__ __device__ __forceinline__ int proj_smem_of(const GeoDev &g) {
     return max(least, min(PROJ_SMEM, fit));
 }
 
-// Level-kk running integral at t, seg_t[s-1] < t <= seg_t[s].  C holds chunk-local
-// running sums; coff[chunk][kk] adds the totals of the preceding chunks.  C is
-// piecewise linear in t between segment ends.
-__device__ __forceinline__ float eval_c(const float *seg_t, const float *C, const float *coff, int nk, int kk,
-                                        float tin, float t, int s) {
-    const int ch = s >> CHUNK_LOG;
-    const float base = coff[ch * nk + kk];
-    const bool first = (s & (CHUNK - 1)) == 0;   // previous value is the chunk's base
-    const float tp = s > 0 ? seg_t[s - 1] : tin;
-    const float cp = first ? base : base + C[(s - 1) * nk + kk];
-    const float cs = base + C[s * nk + kk];
-    const float dt = seg_t[s] - tp;
-    const float frac = dt > 0.f ? __fdividef(t - tp, dt) : 0.f;
-    return __fmaf_rn(frac, cs - cp, cp);
-}
-
 // first s in [0, S) with seg_t[s] >= t (tin <= t <= seg_t[S-1]), from a linear
 // estimate corrected by a local walk (segment ends are nearly evenly spaced)
 __device__ __forceinline__ int seg_find(const float *seg_t, int S, float tin, float scale, float t) {
@@ -185,6 +170,34 @@ __device__ __forceinline__ int seg_find(const float *seg_t, int S, float tin, fl
     while (s < S - 1 && seg_t[s] < t) ++s;
     while (s > 0 && seg_t[s - 1] >= t) --s;
     return s;
+}
+
+// Position of t in the segment list: its segment s (seg_t[s-1] < t <= seg_t[s]) and the
+// fraction of that segment before t.  The same for every level, so a z-plane crossing
+// shared by two consecutive levels is located once.
+struct SegPos {
+    int s;
+    float frac;
+};
+__device__ __forceinline__ SegPos seg_pos(const float *seg_t, int S, float tin, float scale, float t) {
+    SegPos p;
+    p.s = seg_find(seg_t, S, tin, scale, t);
+    const float tp = p.s > 0 ? seg_t[p.s - 1] : tin;
+    const float dt = seg_t[p.s] - tp;
+    p.frac = dt > 0.f ? __fdividef(t - tp, dt) : 0.f;
+    return p;
+}
+
+// Level-kk running integral at position p.  C holds chunk-local running sums;
+// coff[chunk][kk] adds the totals of the preceding chunks.  C is piecewise linear in t
+// between segment ends.
+__device__ __forceinline__ float eval_c(const float *C, const float *coff, int nk, int kk, const SegPos p) {
+    const int ch = p.s >> CHUNK_LOG;
+    const float base = coff[ch * nk + kk];
+    const bool first = (p.s & (CHUNK - 1)) == 0;   // previous value is the chunk's base
+    const float cp = first ? base : base + C[(p.s - 1) * nk + kk];
+    const float cs = base + C[p.s * nk + kk];
+    return __fmaf_rn(p.frac, cs - cp, cp);
 }
 
 // One tile: detector column a of view ia, rows [zc T, zc T + T) with T = blockDim.x.
@@ -299,7 +312,7 @@ __device__ __forceinline__ void project_tile(const GeoDev &G, const int mode, co
         if (k0 <= k1) {
             const bool up = cotp >= 0.f;  // rising ray: level k + 1 starts where k ends
             float last_t = -INFINITY;
-            int last_s = 0;
+            SegPos last_p{0, 0.f};
             for (int k = k0; k <= k1; ++k) {
                 float ta = c.tin, tb = c.tout;
                 if (cotp != 0.f) {
@@ -309,13 +322,12 @@ __device__ __forceinline__ void project_tile(const GeoDev &G, const int mode, co
                     tb = fminf(tb, fmaxf(z1, z2));
                 }
                 if (tb > ta) {
-                    const int sa = ta == last_t ? last_s : seg_find(seg_t, S, c.tin, scale, ta);
-                    const int sb = tb == last_t ? last_s : seg_find(seg_t, S, c.tin, scale, tb);
+                    const SegPos pa = ta == last_t ? last_p : seg_pos(seg_t, S, c.tin, scale, ta);
+                    const SegPos pb = tb == last_t ? last_p : seg_pos(seg_t, S, c.tin, scale, tb);
                     const int kq = k - kb;
-                    acc += eval_c(seg_t, C, coff, nk, kq, c.tin, tb, sb) -
-                           eval_c(seg_t, C, coff, nk, kq, c.tin, ta, sa);
+                    acc += eval_c(C, coff, nk, kq, pb) - eval_c(C, coff, nk, kq, pa);
                     last_t = up ? tb : ta;
-                    last_s = up ? sb : sa;
+                    last_p = up ? pb : pa;
                 }
             }
         }
