@@ -96,7 +96,8 @@ typedef struct {
     float *kernel_ms;     /* optional host out [CBCT_NUM_KERNEL_CLASSES]: summed
                              device time per kernel class, measured with CUDA events
                              on `stream` (synchronises at the end of the call)    */
-    int *kernel_launches; /* optional host out [CBCT_NUM_KERNEL_CLASSES]          */
+    int *kernel_launches; /* optional host out [CBCT_NUM_KERNEL_CLASSES]: kernels
+                             launched per class                                    */
     unsigned kernel_mask; /* kernel classes (bit c: class c) that kernel_ms times with
                              events around each launch; 0 -> all.  Launches of every
                              class are counted.  Timing fewer classes keeps the event
@@ -259,6 +260,9 @@ typedef struct {
     float bp_ms;       /* autotune: measured time of one adjoint with the choice       */
     int proj_smem;     /* projector shared memory per block in bytes (multiple of 16, at
                           most 110 KB); sets how many z-levels one pass holds          */
+    int proj_levels;   /* z-levels per projector launch, 1..nz: a projection of a volume
+                          larger than the L2 cache runs as consecutive launches over
+                          slabs of levels, each ray's sum carried between them        */
 } cbct_tuning;
 /* Time the candidate launch shapes of level `level` with CUDA events on `stream`
  * (synchronises), keep the fastest in the geometry and report it in *out. */
@@ -345,6 +349,10 @@ const char *cbct_last_error(void);
 
 /* Library version string. */
 const char *cbct_version(void);
+
+/* Kernels launched through the library by this process so far (every launch site
+ * counts itself; a captured graph replay adds nothing).  Never fails. */
+unsigned long long cbct_kernel_launch_count(void);
 
 #ifdef __cplusplus
 }

@@ -57,7 +57,7 @@ class Request(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("proj_threads", C.c_int), ("bp_vpl", C.c_int), ("bp_threads", C.c_int),
-                ("proj_ms", C.c_float), ("bp_ms", C.c_float), ("proj_smem", C.c_int)]
+                ("proj_ms", C.c_float), ("bp_ms", C.c_float), ("proj_smem", C.c_int), ("proj_levels", C.c_int)]
 
 
 class ServerRequest(C.Structure):
@@ -112,13 +112,14 @@ _SIGS = {
     "cbct_debug_fail_next_allocations": [_I],
     "cbct_last_error": [],
     "cbct_version": [],
+    "cbct_kernel_launch_count": [],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(lib, _name)
     _fn.argtypes = _args
     _fn.restype = C.c_char_p if _name in ("cbct_last_error", "cbct_version") else (
         None if _name in ("cbct_geometry_destroy", "cbct_server_destroy", "cbct_debug_fail_next_allocations")
-        else C.c_int)
+        else C.c_ulonglong if _name == "cbct_kernel_launch_count" else C.c_int)
 
 
 def header_functions(path: str = HEADER):
@@ -134,6 +135,11 @@ def cbct_last_error() -> str:
 
 def cbct_version() -> str:
     return lib.cbct_version().decode()
+
+
+def cbct_kernel_launch_count() -> int:
+    """Kernels launched through the library by this process so far."""
+    return int(lib.cbct_kernel_launch_count())
 
 
 def _check(status: int):
@@ -378,12 +384,12 @@ def cbct_autotune(g: Geometry, level: int = 0) -> dict:
     t = Tuning()
     _check(lib.cbct_autotune(g.handle, level, C.byref(t), _stream()))
     return dict(proj_threads=t.proj_threads, proj_smem=t.proj_smem, bp_vpl=t.bp_vpl, bp_threads=t.bp_threads,
-                proj_ms=t.proj_ms, bp_ms=t.bp_ms)
+                proj_ms=t.proj_ms, bp_ms=t.bp_ms, proj_levels=t.proj_levels)
 
 
 def cbct_set_tuning(g: Geometry, level: int, tuning: dict):
     t = Tuning(int(tuning.get("proj_threads", 0)), int(tuning.get("bp_vpl", 0)), int(tuning.get("bp_threads", 0)),
-               0.0, 0.0, int(tuning.get("proj_smem", 0)))
+               0.0, 0.0, int(tuning.get("proj_smem", 0)), int(tuning.get("proj_levels", 0)))
     _check(lib.cbct_set_tuning(g.handle, level, C.byref(t)))
 
 

@@ -102,11 +102,15 @@ struct Prof {
     bool on = false;
     unsigned mask = ~0u;     // kernel classes timed with events (all launches are counted)
     bool timing = false;     // the current launch is timed
-    std::vector<int> cls, all;
+    int cur = 0;             // class of the current operation
+    unsigned long long k0 = 0;
+    std::vector<int> cls;
     std::vector<cudaEvent_t> a, b;
+    int count[CBCT_NUM_KERNEL_CLASSES] = {};
     void begin(int c) {
         if (!on) return;
-        all.push_back(c);
+        cur = c;
+        k0 = g_kernel_launches.load(std::memory_order_relaxed);
         timing = (mask >> c) & 1u;
         if (!timing) return;
         cudaEvent_t e0 = G->events.get();
@@ -115,7 +119,9 @@ struct Prof {
         cls.push_back(c);
     }
     void end() {
-        if (!on || !timing) return;
+        if (!on) return;
+        count[cur] += (int)(g_kernel_launches.load(std::memory_order_relaxed) - k0);  // kernels it launched
+        if (!timing) return;
         cudaEvent_t e1 = G->events.get();
         cudaEventRecord(e1, s);
         b.push_back(e1);
@@ -133,8 +139,8 @@ struct Prof {
             cudaEventElapsedTime(&t, a[q], b[q]);
             if (ms) ms[cls[q]] += t;
         }
-        for (int c : all)
-            if (cnt) cnt[c] += 1;
+        for (int c = 0; c < CBCT_NUM_KERNEL_CLASSES; ++c)
+            if (cnt) cnt[c] = count[c];
         G->events.release_all();
         return CBCT_OK;
     }
@@ -712,6 +718,8 @@ cbct_status cbct_backproject_eq2(cbct_geometry *G, const float *y_dev, float *f_
     return CBCT_OK;
 }
 
+
+unsigned long long cbct_kernel_launch_count(void) { return g_kernel_launches.load(std::memory_order_relaxed); }
 
 cbct_status cbct_tv_prox(cbct_geometry *G, const float *g_dev, float *f_inout_dev, double beta, double eps,
                          int inner_iters, int tv_mode, cudaStream_t s) {

@@ -835,6 +835,7 @@ cbct_status Engine::launch_stages() {
         const int per_sm = resident_blocks(k_project_batch, pg.threads, pg.smem);
         k_project_batch<<<(unsigned)persistent_grid(pg.tiles, per_sm), pg.threads, pg.smem, s>>>(
             d_proj + pg.first, d_pstart + pg.first, pg.count, pg.tiles);
+        count_launch();
         ECK(cudaGetLastError(), "batched projection");
     }
     // adjoint (+ gradient step)
@@ -852,28 +853,36 @@ cbct_status Engine::launch_stages() {
         if (v == 0) {
             const long nb = persistent_grid((warps + wpb - 1) / wpb, resident_blocks(k_bp_batch<1>, BP_THREADS, 0));
             k_bp_batch<1><<<(unsigned)nb, BP_THREADS, 0, s>>>(d_bp[0], d_bstart[0], n, warps);
+            count_launch();
         } else if (v == 1) {
             const long nb = persistent_grid((warps + wpb - 1) / wpb, resident_blocks(k_bp_batch<2>, BP_THREADS, 0));
             k_bp_batch<2><<<(unsigned)nb, BP_THREADS, 0, s>>>(d_bp[1], d_bstart[1], n, warps);
+            count_launch();
         } else if (v == 2) {
             const long nb = persistent_grid((warps + wpb - 1) / wpb, resident_blocks(k_bp_batch<3>, BP_THREADS, 0));
             k_bp_batch<3><<<(unsigned)nb, BP_THREADS, 0, s>>>(d_bp[2], d_bstart[2], n, warps);
+            count_launch();
         } else {
             const long nb = persistent_grid((warps + wpb - 1) / wpb, resident_blocks(k_bp_batch<4>, BP_THREADS, 0));
             k_bp_batch<4><<<(unsigned)nb, BP_THREADS, 0, s>>>(d_bp[3], d_bstart[3], n, warps);
+            count_launch();
         }
         ECK(cudaGetLastError(), "batched backprojection");
     }
     if (!heq.empty()) {
         const long nb = persistent_grid(eqtotal, resident_blocks(k_eq2_batch, EQ2_THREADS, 0));
         k_eq2_batch<<<(unsigned)nb, EQ2_THREADS, 0, s>>>(d_eq, d_eqstart, (int)heq.size(), eqtotal);
+        count_launch();
         ECK(cudaGetLastError(), "batched eq2 backprojection");
     }
     if (!hdot.empty()) {
         const int n = (int)hdot.size();
         k_dot_batch<<<(unsigned)persistent_grid(dtotal, 8), 256, 0, s>>>(d_dot, d_dstart, n, dtotal);
+        count_launch();
         k_pfin_batch<<<(unsigned)n, 256, 0, s>>>(d_dot);
+        count_launch();
         k_scale_batch<<<(unsigned)persistent_grid(dtotal, 8), 256, 0, s>>>(d_dot, d_dstart, n, dtotal);
+        count_launch();
         ECK(cudaGetLastError(), "batched power iteration");
     }
     // TV prox sweeps
@@ -883,11 +892,13 @@ cbct_status Engine::launch_stages() {
         if (htv[m].empty()) continue;
         k_tv_batch<<<(unsigned)persistent_grid(tvtot[m], tv_per_sm), TV_THREADS, 0, s>>>(d_tv[m], d_tstart[m],
                                                                                          (int)htv[m].size(), tvtot[m]);
+        count_launch();
         ECK(cudaGetLastError(), "batched tv sweep");
     }
     if (!hstep.empty()) {
         const long nb = persistent_grid(steptotal, resident_blocks(k_step_batch, STEP_THREADS, 0));
         k_step_batch<<<(unsigned)nb, STEP_THREADS, 0, s>>>(d_step, d_sstart, (int)hstep.size(), steptotal);
+        count_launch();
         ECK(cudaGetLastError(), "batched step");
     }
     // join the side streams before the energies (which read every job's partials)
@@ -897,6 +908,7 @@ cbct_status Engine::launch_stages() {
     }
     if (!hen.empty()) {
         k_energy_batch<<<(unsigned)hen.size(), 256, 0, s>>>(d_en);
+        count_launch();
         ECK(cudaGetLastError(), "batched energy");
     }
     return CBCT_OK;
@@ -1100,6 +1112,7 @@ extern "C" cbct_status cbct_autotune(cbct_geometry *G, int level, cbct_tuning *o
     L->gd.bp_threads = best_b;
     out->proj_threads = best_t;
     out->proj_smem = best_m;
+    out->proj_levels = L->gd.proj_levels;
     out->bp_vpl = best_v;
     out->bp_threads = best_b;
     out->proj_ms = best_p;
@@ -1117,7 +1130,8 @@ extern "C" cbct_status cbct_set_tuning(cbct_geometry *G, int level, const cbct_t
     const int need = std::min(PROJ_MAX_THREADS, 32 * ((L->gd.nv + 31) / 32));
     if ((t->proj_threads && (t->proj_threads < need || t->proj_threads > PROJ_MAX_THREADS || t->proj_threads % 32)) ||
         t->bp_vpl < 0 || t->bp_vpl > 4 ||
-        (t->bp_threads && t->bp_threads != 64 && t->bp_threads != 128 && t->bp_threads != 256)) {
+        (t->bp_threads && t->bp_threads != 64 && t->bp_threads != 128 && t->bp_threads != 256) ||
+        t->proj_levels < 0 || t->proj_levels > L->gd.nz) {
         set_error("tuning values out of range");
         return CBCT_ERR_INVALID_ARG;
     }
@@ -1131,6 +1145,7 @@ extern "C" cbct_status cbct_set_tuning(cbct_geometry *G, int level, const cbct_t
     }
     L->gd.proj_threads = t->proj_threads;
     L->gd.proj_smem = t->proj_smem;
+    L->gd.proj_levels = t->proj_levels;
     L->gd.bp_vpl = t->bp_vpl;
     L->gd.bp_threads = t->bp_threads;
     return CBCT_OK;

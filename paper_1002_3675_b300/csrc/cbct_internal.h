@@ -8,6 +8,7 @@
 // warp (32 consecutive voxels of one z-column) write contiguous outputs and read
 // contiguous residual rows.
 #pragma once
+#include <atomic>
 
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
@@ -19,6 +20,12 @@
 #include "../../include/cbct.h"
 
 namespace cbct {
+
+// Kernels this process has launched through the library (every launch site counts
+// itself); read with cbct_kernel_launch_count.
+extern std::atomic<unsigned long long> g_kernel_launches;
+inline void count_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+
 
 // Ray parameterisation shared by the projector and the adjoint.
 //
@@ -51,6 +58,7 @@ struct GeoDev {
     // launch shapes (0 = default); none of them changes any result bit
     int proj_threads;            // projector block size (>= 32 ceil(nv/32) up to 512, multiple of 32)
     int proj_smem;               // projector dynamic shared memory, bytes (0 = default; see proj_smem_of)
+    int proj_levels;             // z-levels per projector launch (0 = default; see project_levels_per_launch)
     int bp_vpl;                  // adjoint voxels per lane (1..4)
     int bp_threads;              // adjoint block size (64, 128 or 256)
 };

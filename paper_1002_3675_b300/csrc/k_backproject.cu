@@ -25,6 +25,7 @@ static void launch_vpl(const GeoDev &g, const float *rs, const float *fin, float
         k_backproject<BP_PLAIN, VPL><<<(unsigned)nb, T, smem, s>>>(g, rs, fin, out, c);
     else
         k_backproject<BP_STEP, VPL><<<(unsigned)nb, T, smem, s>>>(g, rs, fin, out, c);
+    count_launch();
 }
 
 // Running sums of rs along every detector column (one thread per column, float64, in
@@ -48,6 +49,7 @@ cudaError_t launch_row_prefix(const GeoDev &g, const float *rs, cudaStream_t s) 
     long nb = (ncol + 127) / 128;
     if (nb > 148 * 16) nb = 148 * 16;
     k_row_prefix<<<(unsigned)nb, 128, 0, s>>>(rs, g.rowsum, ncol, g.nv);
+    count_launch();
     return cudaGetLastError();
 }
 

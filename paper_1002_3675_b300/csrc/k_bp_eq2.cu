@@ -13,6 +13,7 @@ cudaError_t launch_backproject_eq2(const GeoDev &g, const float *r, const float 
                                    int mode, cudaStream_t s) {
     const size_t nb = (vol_elems(g) + EQ2_THREADS - 1) / EQ2_THREADS;
     k_bp_eq2<<<(unsigned)nb, EQ2_THREADS, 0, s>>>(g, r, fin, out, cscale, mode);
+    count_launch();
     return cudaGetLastError();
 }
 

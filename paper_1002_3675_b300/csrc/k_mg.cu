@@ -154,33 +154,39 @@ __global__ void k_sum_partials(const double *__restrict__ p, int n, double *__re
 cudaError_t launch_restrict_vol(const float *f, int n0, int n1, int n2, float *fc, cudaStream_t s) {
     const int c0 = (n0 + 1) / 2, c1 = (n1 + 1) / 2, c2 = (n2 + 1) / 2;
     k_restrict_vol<<<blocks_for((size_t)c0 * c1 * c2), 256, 0, s>>>(f, n0, n1, n2, fc, c0, c1, c2);
+    count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_prolong_adjoint(const float *x, int n0, int n1, int n2, float *out, int c0, int c1, int c2,
                                    cudaStream_t s) {
     k_prolong_adjoint<<<blocks_for((size_t)c0 * c1 * c2), 256, 0, s>>>(x, n0, n1, n2, out, c0, c1, c2);
+    count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_energy_grad(const TvArgs &a, const float *f, const float *bp, float gamma, float inv_nv,
                                const float *lin, float *out, cudaStream_t s) {
     k_energy_grad<<<blocks_for((size_t)a.nx * a.ny * a.nz), 256, 0, s>>>(a, f, bp, gamma, inv_nv, lin, out);
+    count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_axpy(float *y, const float *x, float a, size_t n, cudaStream_t s) {
     k_axpy<<<blocks_for(n), 256, 0, s>>>(y, x, a, n);
+    count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_sub(const float *a, const float *b, float *out, size_t n, cudaStream_t s) {
     k_sub<<<blocks_for(n), 256, 0, s>>>(a, b, out, n);
+    count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_add_clamp(const float *f, const float *c, float *out, size_t n, cudaStream_t s) {
     k_add_clamp<<<blocks_for(n), 256, 0, s>>>(f, c, out, n);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -189,7 +195,9 @@ size_t dot_partials(size_t n) { return (n + 255) / 256; }
 cudaError_t launch_dot(const float *x, const float *y, size_t n, double *partial, double *out, cudaStream_t s) {
     const size_t nb = dot_partials(n);
     k_dot<<<(unsigned)nb, 256, 0, s>>>(x, y, n, partial);
+    count_launch();
     k_sum_partials<<<1, 256, 0, s>>>(partial, (int)nb, out);
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -38,12 +38,14 @@ __global__ void k_vol_transpose(const float *__restrict__ src, float *__restrict
 cudaError_t launch_vol_to_internal(const float *api, float *in, int nx, int ny, int nz, cudaStream_t s) {
     dim3 grid((nx + 31) / 32, (nz + 31) / 32, ny), block(32, 8);
     k_vol_transpose<true><<<grid, block, 0, s>>>(api, in, nx, ny, nz);
+    count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_vol_to_api(const float *in, float *api, int nx, int ny, int nz, cudaStream_t s) {
     dim3 grid((nz + 31) / 32, (nx + 31) / 32, ny), block(32, 8);
     k_vol_transpose<false><<<grid, block, 0, s>>>(in, api, nx, ny, nz);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -75,6 +77,7 @@ cudaError_t launch_sino_to_internal(const float *api, float *out32, __half *out1
                                     int na, int nu, int nv, cudaStream_t s) {
     dim3 grid((nu + 31) / 32, (nv + 31) / 32, na), block(32, 8);
     k_sino_to_internal<<<grid, block, 0, s>>>(api, out32, out16, ray_z, nu, nv);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -97,6 +100,7 @@ __global__ void k_sino_to_api(const float *__restrict__ src, float *__restrict__
 cudaError_t launch_sino_to_api(const float *in, float *api, int na, int nu, int nv, cudaStream_t s) {
     dim3 grid((nv + 31) / 32, (nu + 31) / 32, na), block(32, 8);
     k_sino_to_api<<<grid, block, 0, s>>>(in, api, nu, nv);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -132,6 +136,7 @@ cudaError_t launch_restrict(const float *y, float *yc, int na, int n1, int n2, c
     unsigned nb = (unsigned)((n + 255) / 256);
     if (nb > 148u * 32u) nb = 148u * 32u;
     k_restrict<<<nb > 0 ? nb : 1, 256, 0, s>>>(y, yc, na, n1, n2);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -144,6 +149,7 @@ cudaError_t launch_to_half(const float *x, __half *y, size_t n, cudaStream_t s) 
     unsigned nb = (unsigned)((n + 255) / 256);
     if (nb > 148u * 32u) nb = 148u * 32u;
     k_to_half<<<nb > 0 ? nb : 1, 256, 0, s>>>(x, y, n);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -189,6 +195,7 @@ cudaError_t launch_prolong(const float *fc, int c0, int c1, int c2, float *f, in
     unsigned nb = (unsigned)((n + 255) / 256);
     if (nb > 148u * 32u) nb = 148u * 32u;
     k_prolong<<<nb > 0 ? nb : 1, 256, 0, s>>>(fc, c0, c1, c2, f, n0, n1, n2);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -235,6 +242,7 @@ cudaError_t launch_energy_finalize(const double *pe2, int n2, const double *pe1,
                                    double mu_over_nr, double *trace, int *counter, cudaStream_t s,
                                    const double *pstep, int nstep) {
     k_energy_finalize<<<1, 256, 0, s>>>(pe2, n2, pe1, n1, pstep, nstep, inv_nv, mu_over_nr, trace, counter);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -249,6 +257,7 @@ size_t step_partials(size_t n) { return (n + STEP_THREADS - 1) / STEP_THREADS; }
 cudaError_t launch_step_copy(const float *v, float *f, size_t n, double *partial, cudaStream_t s) {
     if (!partial) return cudaMemcpyAsync(f, v, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
     k_step_copy<<<(unsigned)step_partials(n), STEP_THREADS, 0, s>>>(v, f, n, partial);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -288,6 +297,7 @@ cudaError_t launch_dot2(const float *x, const float *y, size_t n, double *partia
     const unsigned nb = (unsigned)((n + 255) / 256);
     if (nblocks_out) *nblocks_out = (int)nb;
     k_dot2<<<nb, 256, 0, s>>>(x, y, n, partial);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -317,6 +327,7 @@ __global__ void k_power_finalize(const double *partial, int nblk, double *lam, f
 
 cudaError_t launch_power_finalize(const double *partial, int nblk, double *lam, float *scale, cudaStream_t s) {
     k_power_finalize<<<1, 256, 0, s>>>(partial, nblk, lam, scale);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -331,6 +342,7 @@ cudaError_t launch_scale(const float *y, const float *scale, float *x, size_t n,
     unsigned nb = (unsigned)((n + 255) / 256);
     if (nb > 148u * 32u) nb = 148u * 32u;
     k_scale<<<nb > 0 ? nb : 1, 256, 0, s>>>(y, scale, x, n);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -343,6 +355,7 @@ cudaError_t launch_fill(float *x, float v, size_t n, cudaStream_t s) {
     unsigned nb = (unsigned)((n + 255) / 256);
     if (nb > 148u * 32u) nb = 148u * 32u;
     k_fill<<<nb > 0 ? nb : 1, 256, 0, s>>>(x, v, n);
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -1,5 +1,7 @@
 // Forward projection launchers (single request).  The arithmetic is in
 // project_tile.cuh.
+#include <algorithm>
+
 #include "project_tile.cuh"
 
 namespace cbct {
@@ -7,9 +9,24 @@ namespace cbct {
 template <int MODE>
 __global__ void __launch_bounds__(PROJ_MAX_THREADS, 2)
 k_project(GeoDev G, const float *__restrict__ vol, const float *__restrict__ y32,
-          const __half *__restrict__ y16, float *__restrict__ out, double *__restrict__ partial) {
+          const __half *__restrict__ y16, float *__restrict__ out, double *__restrict__ partial, int kr0, int kr1,
+          int carry) {
     extern __shared__ float smem[];
-    project_tile(G, MODE, vol, y32, y16, out, partial, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+    project_tile(G, MODE, vol, y32, y16, out, partial, blockIdx.x, blockIdx.y, blockIdx.z, smem, kr0, kr1,
+                 (carry & 1) != 0, (carry & 2) != 0);
+}
+
+// Levels per launch: G.proj_levels if set, else the whole volume in one launch while it fits comfortably in the
+// 126 MB L2 next to the projection data; otherwise slabs of whole 32-level groups of at
+// most 32 MB, so that the blocks of one launch (every view and column) find their slab
+// in L2 instead of re-reading the volume from HBM for every view.
+int project_levels_per_launch(const GeoDev &g) {
+    if (g.proj_levels >= 1 && g.proj_levels <= g.nz) return g.proj_levels;
+    const size_t level_bytes = (size_t)g.nx * g.ny * sizeof(float);
+    if (level_bytes * g.nz <= (size_t)48 << 20) return g.nz;
+    int r = (int)(((size_t)32 << 20) / level_bytes);
+    if (r >= 32) r &= ~31;
+    return std::max(1, std::min(r, g.nz));
 }
 
 int project_threads(const GeoDev &g) { return proj_threads_of(g); }
@@ -44,15 +61,26 @@ cudaError_t launch_project(const GeoDev &g, const float *vol, const float *y32, 
         attr_set[dev] = true;
     }
     const dim3 grid = project_grid(g), block((unsigned)project_threads(g));
-    switch (mode) {
-        case PROJ_PLAIN: k_project<PROJ_PLAIN><<<grid, block, smem, s>>>(g, vol, y32, y16, out, partial); break;
-        case PROJ_RESID32: k_project<PROJ_RESID32><<<grid, block, smem, s>>>(g, vol, y32, y16, out, partial); break;
-        case PROJ_RESID16: k_project<PROJ_RESID16><<<grid, block, smem, s>>>(g, vol, y32, y16, out, partial); break;
-        case PROJ_RAW32: k_project<PROJ_RAW32><<<grid, block, smem, s>>>(g, vol, y32, y16, out, partial); break;
-        case PROJ_RAW16: k_project<PROJ_RAW16><<<grid, block, smem, s>>>(g, vol, y32, y16, out, partial); break;
-        default: k_project<PROJ_SCALED><<<grid, block, smem, s>>>(g, vol, y32, y16, out, partial); break;
+    const int R = project_levels_per_launch(g);
+    for (int k0 = 0; k0 < g.nz; k0 += R) {
+        const int k1 = std::min(g.nz, k0 + R);
+        const int carry = (k0 > 0 ? 1 : 0) | (k1 < g.nz ? 2 : 0);
+#define CBCT_PROJ_LAUNCH(M) \
+    k_project<M><<<grid, block, smem, s>>>(g, vol, y32, y16, out, partial, k0, k1, carry)
+        switch (mode) {
+            case PROJ_PLAIN: CBCT_PROJ_LAUNCH(PROJ_PLAIN); break;
+            case PROJ_RESID32: CBCT_PROJ_LAUNCH(PROJ_RESID32); break;
+            case PROJ_RESID16: CBCT_PROJ_LAUNCH(PROJ_RESID16); break;
+            case PROJ_RAW32: CBCT_PROJ_LAUNCH(PROJ_RAW32); break;
+            case PROJ_RAW16: CBCT_PROJ_LAUNCH(PROJ_RAW16); break;
+            default: CBCT_PROJ_LAUNCH(PROJ_SCALED); break;
+        }
+#undef CBCT_PROJ_LAUNCH
+        count_launch();
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 }  // namespace cbct

@@ -20,6 +20,7 @@ static void launch_sweep(const TvArgs &a, dim3 grid, const float *fin, const flo
         if (a.jc) k_tv_sweep<CLAMP, ACC, false, true><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p);
         else k_tv_sweep<CLAMP, ACC, false, false><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p);
     }
+    count_launch();
 }
 
 // E1 alone: float64 partial sums of |grad f|_eps.
@@ -85,6 +86,7 @@ cudaError_t launch_tv_energy(const TvArgs &a, const float *f, double *partial, c
     const size_t nb = tv_energy_partials(a.nx, a.ny, a.nz);
     if (nblocks_out) *nblocks_out = (int)nb;
     k_tv_energy<<<(unsigned)nb, TV_THREADS, 0, s>>>(a, f, partial);
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -131,9 +131,11 @@ extern "C" cbct_status cbct_tv_energy_noalloc(int nx, int ny, int nz, double hx,
     // caller layout [nz][ny][nx]: axis 0 is z, axis 2 is x
     k_tv_energy_static<<<nb, kThreads, 0, stream>>>(nz, ny, nx, (float)(1.0 / hz), (float)(1.0 / hy),
                                                      (float)(1.0 / hx), (float)(eps * eps), f_dev, partials);
+    cbct::count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cbct::cuda_fail(e, "cbct_tv_energy_noalloc: launch");
     k_tv_energy_static_final<<<1, kThreads, 0, stream>>>(partials, nb, 1.0 / nvox, e1_dev);
+    cbct::count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return cbct::cuda_fail(e, "cbct_tv_energy_noalloc: launch");
     return CBCT_OK;

@@ -204,10 +204,19 @@ __device__ __forceinline__ float eval_c(const float *C, const float *coff, int n
 // mode selects the epilogue (uniform per tile).  smem: PROJ_SMEM bytes of dynamic
 // shared memory.  Called by the single-request and the batched kernels alike, so a
 // request's result does not depend on what else is in the launch.
+//
+// Only the z-levels [kr0, kr1) are added.  A projection split over several launches of
+// consecutive level ranges (so that each launch's slab of the volume stays in L2)
+// carries every ray's running sum in out: carry_in starts from out instead of 0,
+// carry_out stores the sum there and skips the epilogue.  The levels are added in the
+// same ascending order either way, so the split does not change a bit of the result.
 __device__ __forceinline__ void project_tile(const GeoDev &G, const int mode, const float *__restrict__ vol,
                                              const float *__restrict__ y32, const __half *__restrict__ y16,
                                              float *__restrict__ out, double *__restrict__ partial, const int a,
-                                             const int ia, const int zc, float *smem) {
+                                             const int ia, const int zc, float *smem, const int kr0 = 0,
+                                             int kr1 = -1, const bool carry_in = false,
+                                             const bool carry_out = false) {
+    if (kr1 < 0) kr1 = G.nz;
     const int slots = G.nx + G.ny + 1;
     const int max_chunks = (slots + CHUNK - 1) >> CHUNK_LOG;
     float *seg_t = smem;                          // exit t of each segment
@@ -257,15 +266,17 @@ __device__ __forceinline__ void project_tile(const GeoDev &G, const int mode, co
         }
     }
     const float scale = S > 0 && c.tout > c.tin ? (float)S / (c.tout - c.tin) : 0.f;
-    float acc = 0.f;
+    const size_t o = ((size_t)ia * G.nu + a) * G.nv + (valid ? b : 0);
+    float acc = (carry_in && valid) ? out[o] : 0.f;
     __syncthreads();
 
     // ---- 2./3. bands of z-levels: running slice integrals, then the rays ---------------
     const int c_cap = proj_smem_of(G) / 4 - 2 * slots;
-    int kband = S > 0 ? max(1, min(G.nz, c_cap / (S + max_chunks))) : G.nz;
-    if (kband >= 32 && kband < G.nz) kband &= ~31;  // whole 32-level groups: full warps, aligned loads
-    for (int kb = 0; kb < G.nz && S > 0; kb += kband) {
-        const int nk = min(kband, G.nz - kb);
+    const int nr = kr1 - kr0;
+    int kband = S > 0 ? max(1, min(nr, c_cap / (S + max_chunks))) : nr;
+    if (kband >= 32 && kband < nr) kband &= ~31;  // whole 32-level groups: full warps, aligned loads
+    for (int kb = kr0; kb < kr1 && S > 0; kb += kband) {
+        const int nk = min(kband, kr1 - kb);
         float *C = coff + max_chunks * nk;        // [s][kk], chunk-local running sums
         // 2. warps over (32-level group, 64-segment chunk) pairs; lanes over levels, so
         //    each load is a contiguous piece of a z-column
@@ -334,12 +345,16 @@ __device__ __forceinline__ void project_tile(const GeoDev &G, const int mode, co
         __syncthreads();
     }
 
+    if (carry_out) {  // uniform per launch: the next level range continues from here
+        if (valid) out[o] = acc;
+        return;
+    }
+
     // ---- epilogue ----------------------------------------------------------------------
     float r2 = 0.f;
     if (valid) {
         // every rounding spelled out, so no caller's inlining can fuse them differently
         const float p = __fmul_rn(acc, secp);  // horizontal length -> 3D length
-        const size_t o = ((size_t)ia * G.nu + a) * G.nv + b;
         if (mode == PROJ_PLAIN) {
             out[o] = p;
         } else if (mode == PROJ_SCALED) {

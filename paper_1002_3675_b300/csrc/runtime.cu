@@ -14,6 +14,9 @@
 
 namespace cbct {
 
+std::atomic<unsigned long long> g_kernel_launches{0};
+
+
 static thread_local char g_err[512] = "";
 
 void set_error(const char *fmt, ...) {

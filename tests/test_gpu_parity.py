@@ -103,6 +103,42 @@ def test_project_large_sampled_rays(lib):
     assert (y[:, 150:234, 200:312] > 0).all()
 
 
+def test_projection_split_over_level_launches_is_bitwise_identical(lib):
+    """A projection run as consecutive launches over slabs of z-levels (the default for
+    volumes larger than the L2 cache) equals the single launch bit for bit, in every
+    epilogue: plain projection, the power iteration's scaled one and the residual with
+    the E2 partials of an Algorithm A1 iteration."""
+    rng = np.random.default_rng(28)
+    small = synth.make_case("small")
+    for g, shape in ((ragged_geometry(), (37, 38, 45)), (small["geom"], (64, 64, 64))):
+        f = rng.uniform(size=shape) * 0.02
+        G = lib.cbct_geometry_create(g)
+        fd = dev(f)
+        n0 = lib.cbct_kernel_launch_count()
+        y0 = host(lib.cbct_project(G, fd))
+        single = lib.cbct_kernel_launch_count() - n0
+        for levels in (1, 5, 32):
+            lib.cbct_set_tuning(G, 0, {"proj_levels": levels})
+            n0 = lib.cbct_kernel_launch_count()
+            assert np.array_equal(host(lib.cbct_project(G, fd)), y0), levels
+            # the launch counter sees one projector launch per slab of levels
+            assert lib.cbct_kernel_launch_count() - n0 == single - 1 + -(-shape[0] // levels)
+        lib.cbct_set_tuning(G, 0, {})
+    g = small["geom"]
+    Y = f32(small["Y"])
+    runs = []
+    for levels in (0, 7):
+        G = lib.cbct_geometry_create(g)
+        lib.cbct_set_tuning(G, 0, {"proj_levels": levels})
+        lam = lib.cbct_power_iteration(G, 5)
+        f, tr, st = lib.cbct_fbs(G, dev(Y), small["mu"], 1.05 * oracle.gamma(g, small["mu"]) * lam, 1e-3, 10, 0, 3,
+                                 dev(np.zeros((64, 64, 64))), trace=True, step_trace=True)
+        runs.append((lam, host(f), tr, st))
+    assert runs[0][0] == runs[1][0]
+    for a, b in zip(runs[0][1:], runs[1][1:]):
+        assert np.array_equal(a, b)
+
+
 def tall_geometry():
     # 600 imager rows: more than one 512-thread projector tile per detector column, and
     # thick voxels (several rows per voxel) against thin rows
@@ -363,7 +399,9 @@ def test_kernel_timing_report(lib):
     G = lib.cbct_geometry_create(case["geom"])
     f, info = lib.cbct_reconstruct(G, dev(case["Y"]), case["mu"], 3, 2, kernel_times=True)
     ms, n = info["kernel_ms"], info["kernel_launches"]
-    assert n["project"] == 2 * (3 + 30) and n["backproject"] == 2 * (3 + 30)
+    # kernels per class: one projector launch per projection (the volume fits in L2), the
+    # column running sums and the gather per adjoint, one launch per prox sweep
+    assert n["project"] == 2 * (3 + 30) and n["backproject"] == 2 * 2 * (3 + 30)
     assert n["tv"] == 2 * 3 * 10
     assert all(ms[k] > 0 for k in ("project", "backproject", "tv"))
     # a class mask times only the chosen classes and still counts every launch
