@@ -66,6 +66,7 @@ TvArgs tv_args(const Level *L, const SolveParams &P) {
     a.eps2 = P.eps2;
     a.aniso = P.tv_mode;
     a.jc = tv_rows_per_tile(a.nx, a.ny, a.nz);
+    a.vz = tv_col_vz(a.nx, a.ny, a.nz);
     return a;
 }
 

@@ -262,6 +262,12 @@ static int job_nstep(const Job *j, const Level *L) {
     return (int)(job_step_fused(j, L) ? tv_partials(L->nx, L->ny, L->nz) : step_partials(vol_elems(L->gd)));
 }
 
+// A TV sweep that fills the GPU by itself, or uses full-column tiles (which the batched
+// kernel does not carry), runs as a single-request launch.
+static bool tv_sweep_solo(int nx, int ny, int nz, long sms) {
+    return (long)tv_blocks(nx, ny, nz) >= 16 * sms || tv_col_vz(nx, ny, nz) > 0;
+}
+
 static int sm_count() {
     static int n = 0;
     if (n == 0) {
@@ -465,7 +471,7 @@ cbct_status Engine::build_tables() {
                                                          : vpl0 == 3 ? bp_warp_tiles<3>(g) : bp_warp_tiles<4>(g);
         const long eblocks0 = (long)((vol_elems(g) + EQ2_THREADS - 1) / EQ2_THREADS);
         const bool indep = ptiles >= 8 * sms && (eq2 ? eblocks0 >= 16 * sms : wt0 >= 64 * sms) &&
-                           (power || (long)tv_blocks(g.nx, g.ny, g.nz) >= 16 * sms);
+                           (power || tv_sweep_solo(g.nx, g.ny, g.nz, sms));
         if (indep) {  // the whole tick of this job on a side stream
             Chain ch;
             ch.job = j;
@@ -642,7 +648,7 @@ cbct_status Engine::build_tables() {
             ti.partial = ti.acc == TV_ACC_STEP ? step_region(L) : L->partial + np;
             if (chain) {
                 chain->tv.push_back(ti);
-            } else if (nb >= 16 * sms) {
+            } else if (tv_sweep_solo(L->nx, L->ny, L->nz, sms)) {
                 solo_tv[m].push_back(ti);
             } else {
                 htv[m].push_back(ti);

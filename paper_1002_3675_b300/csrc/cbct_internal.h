@@ -159,12 +159,26 @@ struct TvArgs {
     float s, beta, eps2;
     int aniso;               // 0: isotropic E1, 1: anisotropic E1
     int jc;                  // rows per warp tile of the sweep (tv_rows_per_tile; 0: per voxel)
+    int vz;                  // full-column tiles: voxels per lane in z (tv_col_vz; 0: 32-voxel z-blocks)
 };
-// Rows per warp tile of the TV sweep: walks of 16 rows when that still gives at least
-// 8192 warp tiles (measured on B300: 1.3-1.5x faster than one thread per voxel from
-// 256x256x48 up); 0 selects the one-thread-per-voxel form, faster for smaller volumes.
-// A function of the sizes alone, so every launch of a level uses the same tiles.
+// Forms of the TV sweep, chosen from the sizes alone (so every launch of a level, alone
+// or batched, uses the same tiles):
+//  * full column (tv_col_vz > 0): a warp owns whole z-columns of at most 128 voxels (up
+//    to 4 per lane) and walks jc rows in y; z-neighbours come by shuffle, with no halo.
+//    Used when walks of 4 rows still give 8192 warp tiles.
+//  * row walk (jc > 0, vz = 0): a warp owns 32 consecutive z-voxels and walks 16 rows;
+//    for taller volumes (measured on B300: 1.3-1.5x faster than one thread per voxel
+//    from 256x256x48 up).
+//  * one thread per voxel (jc = 0): smaller volumes.
+__host__ __device__ __forceinline__ int tv_col_vz(int nx, int ny, int nz) {
+    return (nz <= 64 && (long)nx * ((ny + 3) / 4) >= 8192) ? (nz + 31) / 32 : 0;
+}
 __host__ __device__ __forceinline__ int tv_rows_per_tile(int nx, int ny, int nz) {
+    if (tv_col_vz(nx, ny, nz)) {
+        if ((long)nx * ((ny + 15) / 16) >= 8192) return 16;
+        if ((long)nx * ((ny + 7) / 8) >= 8192) return 8;
+        return 4;
+    }
     return (long)nx * ((ny + 15) / 16) * ((nz + 31) / 32) >= 8192 ? 16 : 0;
 }
 // One prox sweep fin -> fout.  partial_e1: the E1 partials of fin; partial_step (fout

@@ -3,24 +3,32 @@
 
 namespace cbct {
 
-template <bool CLAMP, int ACC, bool ANISO, bool WARP>
+template <bool CLAMP, int ACC, bool ANISO, int FORM>
 __global__ void __launch_bounds__(TV_THREADS)
 k_tv_sweep(TvArgs A, const float *__restrict__ fin, const float *__restrict__ g, float *__restrict__ fout,
            double *__restrict__ partial) {
-    tv_block_t<CLAMP, ACC, ANISO, WARP>(A, fin, g, fout, partial, blockIdx.x);
+    tv_block_t<CLAMP, ACC, ANISO, FORM>(A, fin, g, fout, partial, blockIdx.x);
+}
+
+template <bool CLAMP, int ACC, bool ANISO>
+static void launch_form(const TvArgs &a, dim3 grid, const float *fin, const float *g, float *fout, double *p,
+                        cudaStream_t s) {
+    switch (tv_form(a)) {
+        case 0: k_tv_sweep<CLAMP, ACC, ANISO, 0><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p); break;
+        case 1: k_tv_sweep<CLAMP, ACC, ANISO, 1><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p); break;
+        case 2: k_tv_sweep<CLAMP, ACC, ANISO, 2><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p); break;
+        case 3: k_tv_sweep<CLAMP, ACC, ANISO, 3><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p); break;
+        case 4: k_tv_sweep<CLAMP, ACC, ANISO, 4><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p); break;
+        default: k_tv_sweep<CLAMP, ACC, ANISO, 5><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p); break;
+    }
+    count_launch();
 }
 
 template <bool CLAMP, int ACC>
 static void launch_sweep(const TvArgs &a, dim3 grid, const float *fin, const float *g, float *fout, double *p,
                          cudaStream_t s) {
-    if (a.aniso) {
-        if (a.jc) k_tv_sweep<CLAMP, ACC, true, true><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p);
-        else k_tv_sweep<CLAMP, ACC, true, false><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p);
-    } else {
-        if (a.jc) k_tv_sweep<CLAMP, ACC, false, true><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p);
-        else k_tv_sweep<CLAMP, ACC, false, false><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p);
-    }
-    count_launch();
+    if (a.aniso) launch_form<CLAMP, ACC, true>(a, grid, fin, g, fout, p, s);
+    else launch_form<CLAMP, ACC, false>(a, grid, fin, g, fout, p, s);
 }
 
 // E1 alone: float64 partial sums of |grad f|_eps.

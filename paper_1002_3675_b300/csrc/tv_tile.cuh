@@ -107,11 +107,12 @@ __device__ __forceinline__ float tv_div(const TvArgs &A, const float *__restrict
 // voxels (float32 along the rows, then over the lanes).
 constexpr int TV_WARPS = TV_THREADS / 32;
 
-// Warp tiles of a sweep (row walks), or, for the per-voxel form, 8 per block of
-// TV_THREADS voxels; E1 partials: one per warp tile, or one per block.
+// Warp tiles of a sweep (full columns or row walks), or, for the per-voxel form, 8 per
+// block of TV_THREADS voxels; E1 partials: one per warp tile, or one per block.
 __host__ __device__ __forceinline__ long tv_warp_tiles(int nx, int ny, int nz) {
     const int jc = tv_rows_per_tile(nx, ny, nz);
     if (jc == 0) return TV_WARPS * (((long)nx * ny * nz + TV_THREADS - 1) / TV_THREADS);
+    if (tv_col_vz(nx, ny, nz)) return (long)nx * ((ny + jc - 1) / jc);
     return (long)nx * ((ny + jc - 1) / jc) * ((nz + 31) / 32);
 }
 
@@ -242,6 +243,110 @@ __device__ __forceinline__ void tv_warp(const TvArgs &A, const float *__restrict
     }
 }
 
+// Full-column warp tile: the warp owns the whole z-column of (i, j) for A.jc rows in y
+// from j0, lane l holding the voxels k = l + 32 v (v < VZ, interleaved so that every load
+// is coalesced).  The same arithmetic as the row walk (same expressions, same order);
+// the +z neighbours f(i, j, k+1), f(i-1, j, k+1) and the p_z term of (i, j, k-1) come from
+// the neighbouring lane (lane 31 / lane 0 of the next / previous slot), so nothing in z
+// is loaded twice and no lane computes a halo.  One float64 partial per tile.
+template <bool CLAMP, int ACC, bool ANISO, int VZ>
+__device__ __forceinline__ void tv_col(const TvArgs &A, const float *__restrict__ fin, const float *__restrict__ g,
+                                       float *__restrict__ fout, double *__restrict__ partial, const long wtile) {
+    constexpr bool E1 = ACC == TV_ACC_E1;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int njc = (A.ny + A.jc - 1) / A.jc;
+    const int jc = (int)(wtile % njc), i = (int)(wtile / njc);
+    const int j0 = jc * A.jc, j1 = min(j0 + A.jc, A.ny);
+    const size_t sx = (size_t)A.ny * A.nz, sy = A.nz;
+    const bool xp = i < A.nx - 1, xm = i > 0;
+    int kq[VZ];
+    bool kin[VZ];
+#pragma unroll
+    for (int v = 0; v < VZ; ++v) {
+        const int k = lane + 32 * v;
+        kin[v] = k < A.nz;
+        kq[v] = kin[v] ? k : A.nz - 1;  // idle lanes read a valid address
+    }
+    // value at k + 1 of a per-slot quantity q (q itself at the top of the column)
+    auto zup = [&](const float (&q)[VZ], int v) {
+        const float dn = __shfl_down_sync(FULL, q[v], 1);
+        const float nx0 = __shfl_sync(FULL, q[v + 1 < VZ ? v + 1 : v], 0);
+        const float r = lane == 31 ? nx0 : dn;
+        return lane + 32 * v < A.nz - 1 ? r : q[v];
+    };
+    size_t o = ((size_t)i * A.ny + j0) * A.nz;   // (i, j, 0)
+    float e1 = 0.f;
+    float c[VZ], m[VZ], py_prev[VZ];
+#pragma unroll
+    for (int v = 0; v < VZ; ++v) {
+        c[v] = __ldg(fin + o + kq[v]);
+        m[v] = xm ? __ldg(fin + o - sx + kq[v]) : 0.f;
+        py_prev[v] = 0.f;
+    }
+    if (j0 > 0) {  // p_y piece of (i, j0 - 1, k)
+        float b[VZ], bxp[VZ];
+#pragma unroll
+        for (int v = 0; v < VZ; ++v) {
+            b[v] = __ldg(fin + o - sy + kq[v]);
+            bxp[v] = xp ? __ldg(fin + o - sy + sx + kq[v]) : b[v];
+        }
+#pragma unroll
+        for (int v = 0; v < VZ; ++v) py_prev[v] = tv_own<false, ANISO>(A, b[v], bxp[v], c[v], zup(b, v)).py;
+    }
+#pragma unroll 1
+    for (int j = j0; j < j1; ++j) {
+        const bool yp = j < A.ny - 1;
+        float fy[VZ], fx[VZ], my[VZ], gv[VZ];
+#pragma unroll
+        for (int v = 0; v < VZ; ++v) {
+            fy[v] = yp ? __ldg(fin + o + sy + kq[v]) : c[v];
+            fx[v] = xp ? __ldg(fin + o + sx + kq[v]) : c[v];
+            my[v] = (xm && yp) ? __ldg(fin + o - sx + sy + kq[v]) : m[v];
+            gv[v] = __ldg(g + o + kq[v]);
+        }
+        float pz[VZ], div[VZ];
+#pragma unroll
+        for (int v = 0; v < VZ; ++v) {
+            const TvOwn own = tv_own<E1, ANISO>(A, c[v], fx[v], fy[v], zup(c, v));
+            pz[v] = own.pz;
+            float d = own.div;
+            if (xm) d = __fmaf_rn(tv_px_minus<ANISO>(A, c[v], m[v], my[v], zup(m, v)), A.ihx, d);
+            if (j > 0) d = __fmaf_rn(py_prev[v], A.ihy, d);
+            div[v] = d;
+            py_prev[v] = own.py;
+            if (E1 && kin[v]) e1 = __fadd_rn(e1, own.e1);
+        }
+#pragma unroll
+        for (int v = 0; v < VZ; ++v) {
+            // p_z piece of (i, j, k - 1): the lower lane's, lane 31 of the previous slot for lane 0
+            const float up1 = __shfl_up_sync(FULL, pz[v], 1);
+            const float prev = __shfl_sync(FULL, pz[v > 0 ? v - 1 : 0], 31);
+            const float pz_lo = lane == 0 ? prev : up1;
+            float d = div[v];
+            if (lane + 32 * v > 0) d = __fmaf_rn(pz_lo, A.ihz, d);
+            if (kin[v]) {
+                const size_t ov = o + kq[v];
+                const float x = __fmaf_rn(-A.s, __fmaf_rn(A.beta, __fsub_rn(c[v], gv[v]), d), c[v]);
+                const float y = CLAMP ? fmaxf(x, 0.f) : x;
+                if (ACC == TV_ACC_STEP) {  // fout holds f_k here (read before it is overwritten)
+                    const float dd = __fsub_rn(y, fout[ov]);
+                    e1 = __fmaf_rn(dd, dd, e1);
+                }
+                fout[ov] = y;
+            }
+            c[v] = fy[v];
+            m[v] = my[v];
+        }
+        o += sy;
+    }
+    if (ACC != TV_ACC_NONE) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) e1 += __shfl_down_sync(FULL, e1, off);
+        if (lane == 0) partial[wtile] = (double)e1;
+    }
+}
+
 // One thread per voxel (small or oddly sized volumes): the same arithmetic, one E1
 // partial per block (float32 within a warp, float64 across the warps).
 template <bool CLAMP, int ACC, bool ANISO>
@@ -277,31 +382,39 @@ __device__ __forceinline__ void tv_voxels(const TvArgs &A, const float *__restri
     }
 }
 
-// One block of the sweep (block index blk): TV_WARPS row-walking warp tiles (WARP), or
-// TV_THREADS voxels in the per-voxel form.  With TV_ACC_STEP, fout holds f_k on entry.
-template <bool CLAMP, int ACC, bool ANISO, bool WARP>
+// One block of the sweep (block index blk): TV_WARPS warp tiles (FORM 1: row walks;
+// FORM 2 + v: full columns with v + 1 voxels per lane), or TV_THREADS voxels in the
+// per-voxel form (FORM 0).  With TV_ACC_STEP, fout holds f_k on entry.
+template <bool CLAMP, int ACC, bool ANISO, int FORM>
 __device__ __forceinline__ void tv_block_t(const TvArgs &A, const float *__restrict__ fin, const float *__restrict__ g,
                                            float *__restrict__ fout, double *__restrict__ partial, const long blk) {
-    if (!WARP) {
+    if (FORM == 0) {
         tv_voxels<CLAMP, ACC, ANISO>(A, fin, g, fout, partial, blk);
         return;
     }
     const long wt = blk * TV_WARPS + (threadIdx.x >> 5);
-    if (wt < tv_warp_tiles(A.nx, A.ny, A.nz)) tv_warp<CLAMP, ACC, ANISO>(A, fin, g, fout, partial, wt);
+    if (wt >= tv_warp_tiles(A.nx, A.ny, A.nz)) return;
+    if (FORM == 1) tv_warp<CLAMP, ACC, ANISO>(A, fin, g, fout, partial, wt);
+    else tv_col<CLAMP, ACC, ANISO, (FORM >= 2 ? FORM - 1 : 1)>(A, fin, g, fout, partial, wt);
 }
 
-// The same with the reading and the form chosen at run time (batched kernels).
+// The form of a level's sweep (FORM of tv_block_t).
+__host__ __device__ __forceinline__ int tv_form(const TvArgs &A) { return A.jc == 0 ? 0 : A.vz ? 1 + A.vz : 1; }
+
+// The same with the reading and the form chosen at run time, for the batched kernels.
+// Only the per-voxel form and the row walk: a level big enough for full-column tiles
+// fills the GPU by itself, and the batch engine launches its sweeps as single-request
+// launches (so the batched kernel keeps the registers of the two small forms).
 template <bool CLAMP, int ACC>
 __device__ __forceinline__ void tv_block(const TvArgs &A, const float *__restrict__ fin, const float *__restrict__ g,
                                          float *__restrict__ fout, double *__restrict__ partial, const long blk) {
     if (A.aniso) {
-        if (A.jc) tv_block_t<CLAMP, ACC, true, true>(A, fin, g, fout, partial, blk);
-        else tv_block_t<CLAMP, ACC, true, false>(A, fin, g, fout, partial, blk);
+        if (A.jc) tv_block_t<CLAMP, ACC, true, 1>(A, fin, g, fout, partial, blk);
+        else tv_block_t<CLAMP, ACC, true, 0>(A, fin, g, fout, partial, blk);
     } else {
-        if (A.jc) tv_block_t<CLAMP, ACC, false, true>(A, fin, g, fout, partial, blk);
-        else tv_block_t<CLAMP, ACC, false, false>(A, fin, g, fout, partial, blk);
+        if (A.jc) tv_block_t<CLAMP, ACC, false, 1>(A, fin, g, fout, partial, blk);
+        else tv_block_t<CLAMP, ACC, false, 0>(A, fin, g, fout, partial, blk);
     }
 }
-
 
 }  // namespace cbct

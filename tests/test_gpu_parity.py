@@ -230,6 +230,30 @@ def test_tv_prox_matches_oracle(lib):
     assert np.linalg.norm((out - f32(f0)) - d_ref) <= 1e-4 * np.linalg.norm(d_ref)
 
 
+@pytest.mark.parametrize("dims,form", [((29, 206, 160), "full columns, 1 voxel per lane"),
+                                       ((45, 206, 160), "full columns, 2 voxels per lane"),
+                                       ((70, 256, 180), "32-voxel row walks")])
+@pytest.mark.parametrize("tv_mode", [0, 1])
+def test_tv_prox_sweep_forms_match_oracle(lib, dims, form, tv_mode):
+    """The warp-tile forms of the prox sweep on ragged sizes (a partly filled z-slot or
+    z-block, a last walk of fewer rows) against the oracle's prox."""
+    nz, ny, nx = dims
+    g = dict(nx=nx, ny=ny, nz=nz, hx=1.0, hy=1.25, hz=2.0, nu=16, nv=16, du=30.0, dv=30.0, dso=800.0,
+             dsd=1200.0, angles=np.array([0.0, 1.0]))
+    rng = np.random.default_rng(31)
+    f0 = np.clip(rng.normal(0.01, 0.006, size=dims), 0.0, None)
+    gv = f0 + rng.normal(scale=0.003, size=dims)
+    eps, beta = 1e-3, 5.0e3
+    G = lib.cbct_geometry_create(g)
+    ft = dev(f0)
+    lib.cbct_tv_prox(G, dev(gv), ft, beta, eps, 10, tv_mode=tv_mode)
+    out = host(ft)
+    ref = oracle.prox(f32(gv), f32(f0), (1.0, 1.25, 2.0), beta, eps, 10, tv_mode=tv_mode)
+    assert (out >= 0).all() and not np.signbit(out).any()
+    d_ref = ref - f32(f0)
+    assert np.linalg.norm((out - f32(f0)) - d_ref) <= 1e-4 * np.linalg.norm(d_ref), form
+
+
 def test_energy_and_power_iteration(lib):
     case = synth.make_case("small")
     g = case["geom"]
