@@ -179,6 +179,17 @@ def barrier(world):
         dist.barrier()
 
 
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def cpu_oracle_iterations(case, n_iter):
     """Time n_iter Algorithm A1 iterations of the oracle on the finest level."""
     import oracle
@@ -212,7 +223,7 @@ def run_reference(args, world, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded ellipsoid phantom, analytic line integrals, Poisson/log noise)",
             "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "host_cores": os.cpu_count()},
-            "cpu_baseline": {"value": value, "unit": "iter/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "iter/s", "cores": cores, "cpu_model": cpu_model(), "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -302,7 +313,8 @@ def run_gpu(args, world, rank, local):
     torch.cuda.synchronize()
 
     # ---- the same steps with lambda_max(P^T P) cached per geometry (reported beside) --
-    cbct.cbct_reconstruct(G, Y, mu, iters, levels, f_out=f, reuse_lambda=True)   # fills the cache
+    cbct.cbct_reconstruct(G, Y, mu, iters, levels, f_out=f, reuse_lambda=True, tv_mode=args.tv_mode,
+                          adjoint_mode=args.adjoint_mode, sino_fp16=args.sino_fp16)   # fills the cache
     torch.cuda.synchronize()
     cached_ms = []
     for _ in range(args.steps):
@@ -310,7 +322,7 @@ def run_gpu(args, world, rank, local):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         cbct.cbct_reconstruct(G, Y, mu, iters, levels, f_out=f, reuse_lambda=True, tv_mode=args.tv_mode,
-                              adjoint_mode=args.adjoint_mode)
+                              adjoint_mode=args.adjoint_mode, sino_fp16=args.sino_fp16)
         e1.record(stream)
         e1.synchronize()
         cached_ms.append(e0.elapsed_time(e1))
@@ -369,9 +381,66 @@ def run_gpu(args, world, rank, local):
     if world == 1 and not args.no_cpu_baseline:
         n_cpu = 2
         dt, cores = cpu_oracle_iterations(case, n_cpu)
-        cpu = {"value": n_cpu / dt, "unit": "iter/s", "cores": cores, "kind": "oracle",
+        cpu = {"value": n_cpu / dt, "unit": "iter/s", "cores": cores, "cpu_model": cpu_model(), "kind": "oracle",
                "sample": f"{n_cpu} Algorithm A1 iterations (P, P^T, 10 prox sweeps) of the finest level of the "
                          f"same workload, FP64 C oracle with OpenMP; fixed beta, no power iteration"}
+
+    # ---- per-iteration fractions (algorithmic HBM bytes and the composite floor) -------
+    s_bytes = 2 if args.sino_fp16 else 4
+    dims = [cbct.cbct_level_dims(G, l) for l in range(levels)]
+    nv_l = [d[0] * d[1] * d[2] for d in dims]
+    nr_l = [len(case["geom"]["angles"]) * d[3] * d[4] for d in dims]
+    b_fbs = sum(24 * v + (8 + s_bytes) * r for v, r in zip(nv_l, nr_l)) * iters       # per step
+    b_pow = sum(8 * v + 8 * r for v, r in zip(nv_l, nr_l)) * K_pi
+    bw = peaks["hbm_gbs"] * 1e9
+    t_step = tot_ms / args.steps / 1e3
+    floor_s = {"project": units["project"] * OPS_PER_NNZ["project"] / (alu_peak * 1e12),
+               "backproject": units["backproject"] * OPS_PER_NNZ["backproject"] / (alu_peak * 1e12),
+               "tv": sum(12.0 * v * 10 for v in nv_l) * iters / bw}
+    per_iter = {"hbm_bytes_per_fbs_iteration_finest": 24 * nv_l[0] + (8 + s_bytes) * nr_l[0],
+                "literal_hbm_frac": (b_fbs + b_pow) / (t_step * bw),
+                "composite_frac": sum(floor_s.values()) / t_step,
+                "floor_ms_per_step": {k: v * 1e3 for k, v in floor_s.items()},
+                "basis": "literal: (24 Nv + (8+s) Nr) bytes per FBS iteration and (8 Nv + 8 Nr) per power "
+                         "iteration over the step time at the measured HBM bandwidth; composite: the sum of "
+                         "the per-class floors (P and P^T: nonzeros x lane-ops / FP32 issue peak; TV: 12 B "
+                         "per voxel per sweep / HBM) over the step time"}
+
+    # ---- quality context: the last reconstruction against the ground truth ------------
+    quality = None
+    if not args.no_quality:
+        gm = case["geom"]
+        ss = 1 if gm["nx"] * gm["ny"] * gm["nz"] > 8e6 else 2
+        truth = synth.voxelize(case["ellipsoids"], gm, ss)
+        rec = f.detach().cpu().numpy().astype(np.float64)
+        z = (np.arange(gm["nz"]) - (gm["nz"] - 1) / 2) * gm["hz"]
+        y = (np.arange(gm["ny"]) - (gm["ny"] - 1) / 2) * gm["hy"]
+        x = (np.arange(gm["nx"]) - (gm["nx"] - 1) / 2) * gm["hx"]
+        r_xy = np.sqrt(y[:, None] ** 2 + x[None, :] ** 2)
+        r_fov = gm["dso"] * np.sin(np.arctan(gm["nu"] * gm["du"] / 2 / gm["dsd"]))
+        z_cov = gm["nv"] * gm["dv"] / 2 * (gm["dso"] - r_xy) / gm["dsd"]
+        mask = (r_xy[None] <= r_fov) & (np.abs(z)[:, None, None] <= z_cov[None])
+        eps_d = 2e-5 / min(gm["hx"], gm["hy"], gm["hz"])
+        E = cbct.cbct_energy(G, Y, f, mu, eps_d, tv_mode=args.tv_mode)
+        E0 = cbct.cbct_energy(G, Y, f, mu, 0.0, tv_mode=args.tv_mode)
+        quality = {"rmse_fully_sampled": float(np.sqrt(np.mean((rec - truth)[mask] ** 2))),
+                   "truth_rms_fully_sampled": float(np.sqrt(np.mean(truth[mask] ** 2))),
+                   "fully_sampled_fraction": float(mask.mean()), "unit": "1/mm",
+                   "E": float(E[0]), "E1_eps": float(E[1]), "E1_exact": float(E0[1]), "muE2": float(E[2]),
+                   "truth": f"ellipsoid phantom voxelised with {ss}^3 sub-samples per voxel",
+                   "region": "inside the transverse field of view and the cone seen from every view"}
+
+    # ---- float16 data storage: the reconstruction against the float32 one ------------
+    fp16_err = None
+    if args.sino_fp16:
+        f32r = torch.empty_like(f)
+        cbct.cbct_reconstruct(G, Y, mu, iters, levels, f_out=f32r, tv_mode=args.tv_mode,
+                              adjoint_mode=args.adjoint_mode)
+        a64, b64 = f.double(), f32r.double()
+        fp16_err = {"rel_l2_vs_float32_data": float(torch.linalg.vector_norm(a64 - b64) /
+                                                    torch.linalg.vector_norm(b64)),
+                    "note": "the same reconstruction with float32 data storage (within 1e-4 of the FP64 "
+                            "oracle by the parity tests)"}
 
     launches = int(n_launch)   # every kernel the library launched inside the timed region
     line = {
@@ -399,9 +468,13 @@ def run_gpu(args, world, rank, local):
         "kernel_split_note": "every launch timed with CUDA events in a separate pass of the same steps; the "
                              "timed steps time only the project and backproject launches",
         "gpu_launches": launches,
+        "per_iteration": per_iter,
+        "quality": quality,
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
+    if fp16_err is not None:
+        line["fp16_error"] = fp16_err
     print(json.dumps(line), flush=True)
 
 
@@ -677,6 +750,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="medium", choices=sorted(WORKLOAD_TEXT))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-quality", action="store_true", help="skip the ground-truth comparison (voxelisation)")
     ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "vcycle", "kernels"],
                     help="kernels: --steps single-level iterations at full size (a profiler target)")
     ap.add_argument("--cycles", type=int, default=10, help="vcycle: V-cycles per step")

@@ -207,7 +207,8 @@ cbct_status cbct_power_iteration(cbct_geometry *geom, int iters, double *lambda_
 
 /* Energy of Eq. 1 on the grid, float64: out_host = {E, E1, mu*E2} with
  * E1 = TV_eps(f) / Nv (tv_mode as in cbct_options) and
- * E2 = |P f - Y|^2 / (n_angles nu nv).  Synchronises. */
+ * E2 = |P f - Y|^2 / (n_angles nu nv).  eps >= 0: eps = 0 gives the unsmoothed TV
+ * (sum of |grad f|).  Synchronises. */
 cbct_status cbct_energy(cbct_geometry *geom, const float *Y_dev, const float *f_dev, double mu,
                         double eps, int tv_mode, double out_host[3], cudaStream_t stream);
 

@@ -800,8 +800,13 @@ cbct_status cbct_energy(cbct_geometry *G, const float *Y_dev, const float *f_dev
     Level *L;
     ST(ensure_level(G, 0, &L));
     ST(ensure_workspace(L, false));
+    if (!(eps >= 0) || !isfinite(eps)) {
+        set_error("eps must be >= 0");
+        return CBCT_ERR_INVALID_ARG;
+    }
     SolveParams P;
-    ST(solve_params(L, mu, 1.0, eps, 1, 0, false, &P, tv_mode));
+    ST(solve_params(L, mu, 1.0, eps > 0 ? eps : 1.0, 1, 0, false, &P, tv_mode));
+    P.eps2 = (float)(eps * eps);  // eps = 0: the unsmoothed TV (the energy pass takes square roots in float64)
     double *dtrace;
     ST(get_trace(G, TRACE_W, &dtrace));
     const GeoDev &g = L->gd;

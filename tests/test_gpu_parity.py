@@ -267,6 +267,16 @@ def test_energy_and_power_iteration(lib):
     lam = lib.cbct_power_iteration(G, 30)
     lam_ref = oracle.power_iteration(g, 30)
     assert abs(lam - lam_ref) <= 1e-5 * lam_ref
+    # eps = 0: the unsmoothed TV, E1 = sum |grad f| / Nv, in both readings; a piecewise
+    # constant volume has exactly flat voxels, where the smoothed and exact terms differ most
+    fp = np.where(f > 0.01, 0.02, 0.0)
+    for tv_mode in (0, 1):
+        for vol in (f, fp):
+            E0 = lib.cbct_energy(G, dev(case["Y"]), dev(vol), case["mu"], 0.0, tv_mode=tv_mode)
+            ref0 = oracle.energy(g, f32(case["Y"]), f32(vol), case["mu"], 0.0, tv_mode=tv_mode)
+            assert np.all(np.abs(E0 - ref0) <= 1e-5 * np.abs(ref0)), (tv_mode, E0, ref0)
+    with pytest.raises(lib.CbctError):
+        lib.cbct_energy(G, dev(case["Y"]), dev(f), case["mu"], -1.0)
 
 
 # ---------------------------------------------------------------------------------
