@@ -200,7 +200,9 @@ cbct_status cbct_fbs(cbct_geometry *geom, const float *Y_dev, double mu, double 
                      int inner_iters, int clamp_mode, int tv_mode, int iters, float *f_inout_dev,
                      double *energy_trace, double *step_trace, cudaStream_t stream);
 
-/* Largest eigenvalue of P^T P by `iters` power iterations from the all-ones volume;
+/* Largest eigenvalue of P^T P by `iters` power iterations from a seeded uniform(0,1)
+ * volume (value of voxel a, in [nz][ny][nx] order: the top 24 bits of SplitMix64 with
+ * seed 10023675 at counter a, over 2^24);
  * the estimate is the Rayleigh quotient of the last normalised iterate.  Writes
  * *lambda_out (host) and synchronises the stream. */
 cbct_status cbct_power_iteration(cbct_geometry *geom, int iters, double *lambda_out, cudaStream_t stream);

@@ -70,6 +70,8 @@ def _load():
             "or_default_eps": (C.c_double, [G]),
             "or_energy": (None, [G, _D, _D, C.c_double, C.c_double, _D, _D]),
             "or_power_iteration": (C.c_double, [G, C.c_int]),
+            "or_splitmix64": (C.c_uint64, [C.c_uint64, C.c_uint64]),
+            "or_uniform01": (C.c_double, [C.c_uint64, C.c_uint64]),
             "or_auto_beta": (C.c_double, [G, C.c_double, C.c_int]),
             "or_fbs": (None, [G, _D, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
                               C.c_double, C.c_int, _D, _D, _D]),
@@ -246,6 +248,19 @@ def energy(geom, Y, f, mu, eps, return_residual=False, tv_mode=0):
     h = _g(geom, tv_mode)
     _load().or_energy(C.byref(h.s), _ptr(Y), _ptr(f), mu, eps, _ptr(out), _ptr(r))
     return (out, r) if return_residual else out
+
+
+def splitmix64(seed, i):
+    """Value i of the counter-based SplitMix64 generator with seed `seed`."""
+    return int(_load().or_splitmix64(seed, i))
+
+
+def uniform01(seed, i):
+    """The top 24 bits of splitmix64(seed, i) as a number in [0, 1)."""
+    return float(_load().or_uniform01(seed, i))
+
+
+POWER_SEED = 10023675  # seed of the power iteration's start volume
 
 
 def power_iteration(geom, K=30):

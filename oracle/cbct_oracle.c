@@ -35,6 +35,7 @@
  */
 #include <math.h>
 #include <stdlib.h>
+#include <stdint.h>
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
@@ -568,8 +569,32 @@ void or_energy(const or_geom *g, const double *Y, const double *f, double mu, do
 }
 
 /*
- * lambda_max(P^T P) by K power iterations from the all-ones vector; the estimate is
- * the Rayleigh quotient <x, P^T P x> of the last normalised iterate.
+ * The start of the power iteration is a seeded uniform(0,1) volume.  Its values come
+ * from SplitMix64 (Steele, Lea and Flood 2014, "Fast splittable pseudorandom number
+ * generators"), used as a counter-based generator: value i of seed s is the 64-bit
+ * finaliser applied to s + (i + 1) * 0x9E3779B97F4A7C15, and its top 24 bits make a
+ * uniform number in [0, 1) that float32 holds exactly.
+ */
+uint64_t or_splitmix64(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+double or_uniform01(uint64_t seed, uint64_t i)
+{
+    return (double)(or_splitmix64(seed, i) >> 40) * (1.0 / 16777216.0);
+}
+
+/* Fixed seed of the power iteration's start volume (voxel index in [nz][ny][nx] order). */
+#define OR_POWER_SEED 10023675ull
+
+/*
+ * lambda_max(P^T P) by K power iterations (the step-size estimate of beta) from the
+ * seeded uniform(0,1) volume, normalised; the estimate is the Rayleigh quotient
+ * <x, P^T P x> of the last normalised iterate.
  */
 double or_power_iteration(const or_geom *g, int K)
 {
@@ -578,8 +603,12 @@ double or_power_iteration(const or_geom *g, int K)
     double *x = (double *)malloc(sizeof(double) * nvox);
     double *y = (double *)malloc(sizeof(double) * nvox);
     double *p = (double *)malloc(sizeof(double) * nr);
-    double inv = 1.0 / sqrt((double)nvox);
-    for (long j = 0; j < nvox; ++j) x[j] = inv;
+    double uu = 0.0;
+    for (long j = 0; j < nvox; ++j) {
+        x[j] = or_uniform01(OR_POWER_SEED, (uint64_t)j);
+        uu += x[j] * x[j];
+    }
+    for (long j = 0; j < nvox; ++j) x[j] /= sqrt(uu);  /* |x| = 1 */
     double lam = 0.0;
     for (int it = 0; it < K; ++it) {
         or_project(g, x, p);

@@ -260,7 +260,7 @@ cbct_status run_level(cbct_geometry *G, Level *L, const SolveParams &P, int iter
     return CBCT_OK;
 }
 
-// lambda_max(P^T P) by K power iterations from the normalised all-ones volume.
+// lambda_max(P^T P) by K power iterations from the seeded uniform(0,1) volume.
 cbct_status power_iteration(cbct_geometry *G, Level *L, int K, double *lam, Prof &prof, cudaStream_t s) {
     const GeoDev &gd = L->gd;
     const size_t nv = vol_elems(gd);
@@ -269,7 +269,13 @@ cbct_status power_iteration(cbct_geometry *G, Level *L, int K, double *lam, Prof
     float *dscale = (float *)(G->dscalars + 1);
     {
         Launch l(prof, CBCT_K_REDUCE);
-        CK(launch_fill(x, (float)(1.0 / sqrt((double)nv)), nv, s), "fill");
+        // x = u / |u| for the seeded uniform volume u (built in y), by the same reductions
+        // as every iteration, so that every estimate is a Rayleigh quotient
+        CK(launch_fill_uniform(y, gd.nx, gd.ny, gd.nz, POWER_SEED, s), "start volume");
+        int nb = 0;
+        CK(launch_dot2(y, y, nv, L->partial, s, &nb), "dot");
+        CK(launch_power_finalize(L->partial, nb, dlam, dscale, s), "power finalize");
+        CK(launch_scale(y, dscale, x, nv, s), "scale");
     }
     for (int it = 0; it < K; ++it) {
         {

@@ -375,7 +375,13 @@ cbct_status Engine::start_level(Job *j) {
     if (beta > 0) return begin_fbs(j, beta);
     if (j->o.reuse_lambda && L->lambda_iters == j->K)
         return begin_fbs(j, std::max(10.0 * j->mu, 1.05 * gamma_of(L, j->mu) * L->lambda));
-    ECK(launch_fill(L->A, (float)(1.0 / sqrt((double)vol_elems(g))), vol_elems(g), stream), "fill");
+    // the start x = u / |u| in L->A, with the kernels of the single-request path
+    ECK(launch_fill_uniform(L->B, g.nx, g.ny, g.nz, POWER_SEED, stream), "start volume");
+    int nb = 0;
+    ECK(launch_dot2(L->B, L->B, vol_elems(g), L->partial, stream, &nb), "dot");
+    ECK(launch_power_finalize(L->partial, nb, j->G->dscalars, (float *)(j->G->dscalars + 1), stream),
+        "power finalize");
+    ECK(launch_scale(L->B, (float *)(j->G->dscalars + 1), L->A, vol_elems(g), stream), "scale");
     j->pi_it = 0;
     j->phase = PH_POWER;
     return CBCT_OK;

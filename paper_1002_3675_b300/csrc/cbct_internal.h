@@ -226,6 +226,9 @@ cudaError_t launch_power_finalize(const double *partial, int nblk, double *lam, 
                                   cudaStream_t s);
 cudaError_t launch_scale(const float *y, const float *scale, float *x, size_t n, cudaStream_t s);
 cudaError_t launch_fill(float *x, float v, size_t n, cudaStream_t s);
+// seeded uniform(0,1) volume (internal layout) of the power iteration's start
+constexpr unsigned long long POWER_SEED = 10023675ull;
+cudaError_t launch_fill_uniform(float *x, int nx, int ny, int nz, unsigned long long seed, cudaStream_t s);
 
 // V-cycle kernels (k_mg.cu); volumes [n0][n1][n2], coarse sizes ceil(n / 2)
 cudaError_t launch_restrict_vol(const float *f, int n0, int n1, int n2, float *fc, cudaStream_t s);

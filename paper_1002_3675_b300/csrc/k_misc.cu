@@ -346,6 +346,37 @@ cudaError_t launch_scale(const float *y, const float *scale, float *x, size_t n,
     return cudaGetLastError();
 }
 
+// Start volume of the power iteration: seeded uniform(0,1) values from the counter-based
+// SplitMix64 generator (Steele, Lea and Flood 2014): value a = the 64-bit finaliser of
+// seed + (a + 1) * 0x9E3779B97F4A7C15, top 24 bits over 2^24 (exact in float32), where a
+// is the voxel's index in the [nz][ny][nx] order of the C ABI; written in the internal
+// [nx][ny][nz] layout.
+__device__ __forceinline__ unsigned long long sm64_value(unsigned long long seed, unsigned long long a) {
+    unsigned long long z = seed + (a + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_fill_uniform(float *__restrict__ x, int nx, int ny, int nz, unsigned long long seed) {
+    const size_t n = (size_t)nx * ny * nz;
+    for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(o % nz);
+        const size_t t = o / nz;
+        const int j = (int)(t % ny), i = (int)(t / ny);
+        const unsigned long long a = ((unsigned long long)k * ny + j) * nx + i;
+        x[o] = (float)(unsigned)(sm64_value(seed, a) >> 40) * (1.f / 16777216.f);
+    }
+}
+
+cudaError_t launch_fill_uniform(float *x, int nx, int ny, int nz, unsigned long long seed, cudaStream_t s) {
+    size_t nb = ((size_t)nx * ny * nz + 255) / 256;
+    if (nb > 148u * 32u) nb = 148u * 32u;
+    k_fill_uniform<<<(unsigned)(nb > 0 ? nb : 1), 256, 0, s>>>(x, nx, ny, nz, seed);
+    count_launch();
+    return cudaGetLastError();
+}
+
 __global__ void k_fill(float *x, float v, size_t n) {
     for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x)
         x[o] = v;

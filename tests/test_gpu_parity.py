@@ -267,6 +267,10 @@ def test_energy_and_power_iteration(lib):
     lam = lib.cbct_power_iteration(G, 30)
     lam_ref = oracle.power_iteration(g, 30)
     assert abs(lam - lam_ref) <= 1e-5 * lam_ref
+    # one iteration: the Rayleigh quotient of the seeded start volume itself, so both
+    # sides must draw the same start (counter-based generator, same voxel order)
+    lam1, lam1_ref = lib.cbct_power_iteration(G, 1), oracle.power_iteration(g, 1)
+    assert abs(lam1 - lam1_ref) <= 1e-5 * lam1_ref and lam1 < lam
     # eps = 0: the unsmoothed TV, E1 = sum |grad f| / Nv, in both readings; a piecewise
     # constant volume has exactly flat voxels, where the smoothed and exact terms differ most
     fp = np.where(f > 0.01, 0.02, 0.0)

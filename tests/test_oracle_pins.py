@@ -514,6 +514,23 @@ def test_fbs_converges_to_lbfgsb_minimiser():
     assert obj(f.ravel())[0] <= res.fun * (1 + 1e-9)
 
 
+def test_power_start_generator_matches_published_vectors():
+    """The power iteration's start volume comes from SplitMix64 used as a counter-based
+    generator (value i of seed s = output i + 1 of the generator started at state s);
+    pinned to the generator's published test vectors."""
+    ref = json.load(open(os.path.join(GOLDEN, "splitmix64.json")))
+    for v in ref["vectors"]:
+        got = [f"{oracle.splitmix64(v['seed'], i):016x}" for i in range(len(v["outputs"]))]
+        assert got == v["outputs"], (v["seed"], got)
+    # uniform(0,1) from the top 24 bits: exact multiples of 2^-24, mean 1/2, variance 1/12
+    u = np.array([oracle.uniform01(oracle.POWER_SEED, i) for i in range(100000)])
+    assert np.all((u >= 0) & (u < 1)) and np.all(u * 2 ** 24 == np.floor(u * 2 ** 24))
+    assert u[0] == (oracle.splitmix64(oracle.POWER_SEED, 0) >> 40) / 2 ** 24
+    n = u.size
+    assert abs(u.mean() - 0.5) < 4 * np.sqrt(1 / 12 / n)
+    assert abs(u.var() - 1 / 12) < 4 * np.sqrt(1 / 180 / n)
+
+
 def test_power_iteration_bounds_spectrum():
     """lambda_hat from 30 power iterations is within 1% below the largest eigenvalue
     of A^T A (numpy eigvalsh on the dense matrix)."""
