@@ -163,9 +163,10 @@ struct TvArgs {
 };
 // Forms of the TV sweep, chosen from the sizes alone (so every launch of a level, alone
 // or batched, uses the same tiles):
-//  * full column (tv_col_vz > 0): a warp owns whole z-columns of at most 128 voxels (up
-//    to 4 per lane) and walks jc rows in y; z-neighbours come by shuffle, with no halo.
-//    Used when walks of 4 rows still give 8192 warp tiles.
+//  * full column (tv_col_vz > 0): a warp owns whole z-columns of at most 64 voxels (up
+//    to 2 per lane) and walks jc rows in y; z-neighbours come by shuffle, with no halo.
+//    Used when walks of 4 rows still give 8192 warp tiles (3 voxels per lane needed up
+//    to 80 registers and was slower than the row walk).
 //  * row walk (jc > 0, vz = 0): a warp owns 32 consecutive z-voxels and walks 16 rows;
 //    for taller volumes (measured on B300: 1.3-1.5x faster than one thread per voxel
 //    from 256x256x48 up).

@@ -17,9 +17,7 @@ static void launch_form(const TvArgs &a, dim3 grid, const float *fin, const floa
         case 0: k_tv_sweep<CLAMP, ACC, ANISO, 0><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p); break;
         case 1: k_tv_sweep<CLAMP, ACC, ANISO, 1><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p); break;
         case 2: k_tv_sweep<CLAMP, ACC, ANISO, 2><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p); break;
-        case 3: k_tv_sweep<CLAMP, ACC, ANISO, 3><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p); break;
-        case 4: k_tv_sweep<CLAMP, ACC, ANISO, 4><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p); break;
-        default: k_tv_sweep<CLAMP, ACC, ANISO, 5><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p); break;
+        default: k_tv_sweep<CLAMP, ACC, ANISO, 3><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p); break;
     }
     count_launch();
 }

@@ -188,10 +188,13 @@ __device__ __forceinline__ void tv_warp(const TvArgs &A, const float *__restrict
     // f(i-1, j, k), gv: g, d*: the halo voxel (i, j, k-1) and its +x/+y neighbours),
     // issued one row ahead so that they are in flight during the previous row's
     // arithmetic
-    float fy, fx, fz, my, mz, gv, d, dx, dy;
+    // (fo: with the step accumulator, f_k where the result goes, read with the row's
+    // other loads rather than at its store, which would expose its latency)
+    float fy, fx, fz, my, mz, gv, d, dx, dy, fo;
     auto load_row = [&](int jr, size_t orow, float cr, float mr, float &ly, float &lx, float &lz, float &lmy,
-                        float &lmz, float &lg, float &ld, float &ldx, float &ldy) {
+                        float &lmz, float &lg, float &ld, float &ldx, float &ldy, float &lfo) {
         const bool ypr = jr < A.ny - 1;
+        lfo = ACC == TV_ACC_STEP ? fout[orow] : 0.f;
         ly = ypr ? __ldg(fin + orow + sy) : cr;
         lx = xp ? __ldg(fin + orow + sx) : cr;
         lz = zp ? __ldg(fin + orow + 1) : cr;
@@ -206,12 +209,13 @@ __device__ __forceinline__ void tv_warp(const TvArgs &A, const float *__restrict
             ld = ldx = ldy = 0.f;
         }
     };
-    load_row(j0, o, c, m, fy, fx, fz, my, mz, gv, d, dx, dy);
+    load_row(j0, o, c, m, fy, fx, fz, my, mz, gv, d, dx, dy, fo);
 #pragma unroll 1
     for (int j = j0; j < j1; ++j) {
         // next row: its own value is fy, its (i-1) value my
-        float nfy = 0.f, nfx = 0.f, nfz = 0.f, nmy = 0.f, nmz = 0.f, ngv = 0.f, nd = 0.f, ndx = 0.f, ndy = 0.f;
-        if (j + 1 < j1) load_row(j + 1, o + sy, fy, my, nfy, nfx, nfz, nmy, nmz, ngv, nd, ndx, ndy);
+        float nfy = 0.f, nfx = 0.f, nfz = 0.f, nmy = 0.f, nmz = 0.f, ngv = 0.f, nd = 0.f, ndx = 0.f, ndy = 0.f,
+              nfo = 0.f;
+        if (j + 1 < j1) load_row(j + 1, o + sy, fy, my, nfy, nfx, nfz, nmy, nmz, ngv, nd, ndx, ndy, nfo);
         const TvOwn own = tv_own<E1, ANISO>(A, c, fx, fy, fz);
         float div = own.div;
         if (xm) div = __fmaf_rn(tv_px_minus<ANISO>(A, c, m, my, mz), A.ihx, div);
@@ -222,8 +226,8 @@ __device__ __forceinline__ void tv_warp(const TvArgs &A, const float *__restrict
         if (kin) {
             const float x = __fmaf_rn(-A.s, __fmaf_rn(A.beta, __fsub_rn(c, gv), div), c);
             const float y = CLAMP ? fmaxf(x, 0.f) : x;
-            if (ACC == TV_ACC_STEP) {  // fout holds f_k here (read before it is overwritten)
-                const float dd = __fsub_rn(y, fout[o]);
+            if (ACC == TV_ACC_STEP) {  // fo: f_k, read before it is overwritten
+                const float dd = __fsub_rn(y, fo);
                 e1 = __fmaf_rn(dd, dd, e1);
             }
             fout[o] = y;
@@ -232,7 +236,7 @@ __device__ __forceinline__ void tv_warp(const TvArgs &A, const float *__restrict
         py_prev = own.py;
         c = fy;
         m = my;
-        fy = nfy; fx = nfx; fz = nfz; my = nmy; mz = nmz; gv = ngv; d = nd; dx = ndx; dy = ndy;
+        fy = nfy; fx = nfx; fz = nfz; my = nmy; mz = nmz; gv = ngv; d = nd; dx = ndx; dy = ndy; fo = nfo;
         o += sy;
     }
     if (ACC != TV_ACC_NONE) {
@@ -297,13 +301,16 @@ __device__ __forceinline__ void tv_col(const TvArgs &A, const float *__restrict_
 #pragma unroll 1
     for (int j = j0; j < j1; ++j) {
         const bool yp = j < A.ny - 1;
-        float fy[VZ], fx[VZ], my[VZ], gv[VZ];
+        float fy[VZ], fx[VZ], my[VZ], gv[VZ], fo[VZ];
 #pragma unroll
         for (int v = 0; v < VZ; ++v) {
             fy[v] = yp ? __ldg(fin + o + sy + kq[v]) : c[v];
             fx[v] = xp ? __ldg(fin + o + sx + kq[v]) : c[v];
             my[v] = (xm && yp) ? __ldg(fin + o - sx + sy + kq[v]) : m[v];
             gv[v] = __ldg(g + o + kq[v]);
+            // f_k where the result goes, read with this row's other loads (before any of
+            // the row's stores), not at the store: its latency then overlaps theirs
+            fo[v] = ACC == TV_ACC_STEP ? fout[o + kq[v]] : 0.f;
         }
         float pz[VZ], div[VZ];
 #pragma unroll
@@ -329,8 +336,8 @@ __device__ __forceinline__ void tv_col(const TvArgs &A, const float *__restrict_
                 const size_t ov = o + kq[v];
                 const float x = __fmaf_rn(-A.s, __fmaf_rn(A.beta, __fsub_rn(c[v], gv[v]), d), c[v]);
                 const float y = CLAMP ? fmaxf(x, 0.f) : x;
-                if (ACC == TV_ACC_STEP) {  // fout holds f_k here (read before it is overwritten)
-                    const float dd = __fsub_rn(y, fout[ov]);
+                if (ACC == TV_ACC_STEP) {  // fo: f_k, read before it is overwritten
+                    const float dd = __fsub_rn(y, fo[v]);
                     e1 = __fmaf_rn(dd, dd, e1);
                 }
                 fout[ov] = y;
@@ -383,8 +390,8 @@ __device__ __forceinline__ void tv_voxels(const TvArgs &A, const float *__restri
 }
 
 // One block of the sweep (block index blk): TV_WARPS warp tiles (FORM 1: row walks;
-// FORM 2 + v: full columns with v + 1 voxels per lane), or TV_THREADS voxels in the
-// per-voxel form (FORM 0).  With TV_ACC_STEP, fout holds f_k on entry.
+// FORM 2 + v: full columns with v + 1 voxels per lane, v < 2), or TV_THREADS voxels in
+// the per-voxel form (FORM 0).  With TV_ACC_STEP, fout holds f_k on entry.
 template <bool CLAMP, int ACC, bool ANISO, int FORM>
 __device__ __forceinline__ void tv_block_t(const TvArgs &A, const float *__restrict__ fin, const float *__restrict__ g,
                                            float *__restrict__ fout, double *__restrict__ partial, const long blk) {
