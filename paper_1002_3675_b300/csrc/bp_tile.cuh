@@ -23,8 +23,8 @@
 // t* = (z - zO_b) cot_b otherwise (at most one row per plane here).  Hence
 //   sum_b r_b len = (thi - tlo) sum_{b in [N(z_k), N(z_k+1))} r_b + P(z_k+1) - P(z_k),
 // with N(z) the rows below both ends and P(z) the partial rows' sum.  The sum over
-// full rows is a difference of running sums along the detector column (kept in
-// float64 and stored as a float32 pair, so the difference keeps float32 accuracy).  Each lane
+// full rows is a difference of running sums along the detector column (double-float
+// sums stored as a float32 pair, so the difference keeps float32 accuracy).  Each lane
 // evaluates the planes below its voxels and takes the plane above its last voxel from
 // its neighbour.
 // The residual is pre-scaled by sec(phi) (3D length = t-length * sec(phi)).  Sums are

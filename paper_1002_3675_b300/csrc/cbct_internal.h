@@ -54,7 +54,7 @@ struct GeoDev {
                                  // meets the cell, per cell in view then column order
     const float2 *view;          // [na]      cos, sin
     float2 *rowsum;              // [na][nu][nv+1] running sums of the scaled residual along each
-                                 // detector column, float64 split as (hi, lo) float32 (workspace)
+                                 // detector column, as double-float (hi, lo) float32 pairs (workspace)
     // launch shapes (0 = default); none of them changes any result bit
     int proj_threads;            // projector block size (>= 32 ceil(nv/32) up to 512, multiple of 32)
     int proj_smem;               // projector dynamic shared memory, bytes (0 = default; see proj_smem_of)

@@ -28,27 +28,71 @@ static void launch_vpl(const GeoDev &g, const float *rs, const float *fin, float
     count_launch();
 }
 
-// Running sums of rs along every detector column (one thread per column, float64, in
-// row order): rowsum[b] = sum_{b' < b} rs[b'], stored as hi = float(s), lo = float(s - hi).
-__global__ void k_row_prefix(const float *__restrict__ rs, float2 *__restrict__ out, long ncol, int nv) {
-    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < ncol; c += (long)gridDim.x * blockDim.x) {
+// Running sums of rs along every detector column, kept as unevaluated sums of two
+// float32 (hi + lo, |lo| <= ulp(hi)/2: about 48 bits, as the float64 sum rounded to a
+// pair) by error-free transformations in float32 arithmetic (Knuth's TwoSum, then a
+// renormalisation), which B300 runs far faster than float64: rowsum[b] = sum_{b' < b}
+// rs[b'].  One warp per column: lane l owns the rows [l L, (l + 1) L), L = ceil(nv/32);
+// the lane totals are scanned across the warp (fixed order), then every lane re-adds its
+// rows from its exclusive prefix and writes them.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_norm(float s, float e) {
+    const float hi = __fadd_rn(s, e);
+    return {hi, __fsub_rn(e, __fsub_rn(hi, s))};
+}
+__device__ __forceinline__ DF df_add(DF a, float b) {  // (a.hi + a.lo) + b
+    const float s = __fadd_rn(a.hi, b);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return df_norm(s, __fadd_rn(e, a.lo));
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    return df_norm(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+
+__global__ void __launch_bounds__(256)
+k_row_prefix(const float *__restrict__ rs, float2 *__restrict__ out, long ncol, int nv) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
+    const int L = (nv + 31) >> 5;
+    const int b0 = min(lane * L, nv), b1 = min(b0 + L, nv);
+    for (long c = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < ncol; c += nwarps) {
         const float *r = rs + c * nv;
         float2 *o = out + c * (nv + 1);
-        double sum = 0.0;
-        o[0] = make_float2(0.f, 0.f);
-        for (int b = 0; b < nv; ++b) {
-            sum += (double)__ldg(r + b);
-            const float hi = (float)sum;
-            o[b + 1] = make_float2(hi, (float)(sum - (double)hi));
+        DF t = {0.f, 0.f};
+        for (int b = b0; b < b1; ++b) t = df_add(t, __ldg(r + b));
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {  // inclusive scan of the lane totals
+            DF u;
+            u.hi = __shfl_up_sync(FULL, t.hi, d);
+            u.lo = __shfl_up_sync(FULL, t.lo, d);
+            if (lane >= d) t = df_add(u, t);
+        }
+        DF run;
+        run.hi = __shfl_up_sync(FULL, t.hi, 1);
+        run.lo = __shfl_up_sync(FULL, t.lo, 1);
+        if (lane == 0) {
+            run = {0.f, 0.f};
+            o[0] = make_float2(0.f, 0.f);
+        }
+        for (int b = b0; b < b1; ++b) {
+            run = df_add(run, __ldg(r + b));
+            o[b + 1] = make_float2(run.hi, run.lo);
         }
     }
 }
 
 cudaError_t launch_row_prefix(const GeoDev &g, const float *rs, cudaStream_t s) {
     const long ncol = (long)g.na * g.nu;
-    long nb = (ncol + 127) / 128;
-    if (nb > 148 * 16) nb = 148 * 16;
-    k_row_prefix<<<(unsigned)nb, 128, 0, s>>>(rs, g.rowsum, ncol, g.nv);
+    long nb = (ncol + 7) / 8;  // 8 warps (columns) per block
+    if (nb > 148 * 32) nb = 148 * 32;
+    k_row_prefix<<<(unsigned)nb, 256, 0, s>>>(rs, g.rowsum, ncol, g.nv);
     count_launch();
     return cudaGetLastError();
 }
