@@ -138,42 +138,15 @@ k_tv_batch(const TvItem *__restrict__ items, const long *__restrict__ start, int
 }
 
 // per-block partials of <x, y> and <y, y> (same partition and arithmetic as k_dot2)
-__global__ void k_dot_batch(const VecItem *__restrict__ items, const long *__restrict__ start, int n, long total) {
-    __shared__ float a[8], b[8];
+__global__ void __launch_bounds__(VEC_THREADS)
+k_dot_batch(const VecItem *__restrict__ items, const long *__restrict__ start, int n, long total) {
     for (long t = blockIdx.x; t < total; t += gridDim.x) {
         const int r = find_item(start, n, t);
         const VecItem it = items[r];
-        const long blk = t - start[r];
-        float sxy = 0.f, syy = 0.f;
-        const long o = blk * 256 + threadIdx.x;
-        if (o < it.n) {
-            const float xv = it.x[o], yv = it.y[o];
-            sxy = xv * yv;
-            syy = yv * yv;
-        }
-        for (int off = 16; off > 0; off >>= 1) {
-            sxy += __shfl_down_sync(0xffffffffu, sxy, off);
-            syy += __shfl_down_sync(0xffffffffu, syy, off);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            a[threadIdx.x >> 5] = sxy;
-            b[threadIdx.x >> 5] = syy;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s1 = 0.0, s2 = 0.0;
-            for (int w = 0; w < 8; ++w) {
-                s1 += (double)a[w];
-                s2 += (double)b[w];
-            }
-            it.partial[2 * blk] = s1;
-            it.partial[2 * blk + 1] = s2;
-        }
-        __syncthreads();
+        dot2_tile(it.x, it.y, it.n, t - start[r], it.partial);
     }
 }
 
-// lam = <x, y>, scale = 1/|y| per item (one block per item; same tree as k_power_finalize)
 __global__ void k_pfin_batch(const VecItem *__restrict__ items) {
     const VecItem it = items[blockIdx.x];
     __shared__ double sh1[256], sh2[256];
@@ -198,12 +171,12 @@ __global__ void k_pfin_batch(const VecItem *__restrict__ items) {
     }
 }
 
-__global__ void k_scale_batch(const VecItem *__restrict__ items, const long *__restrict__ start, int n, long total) {
+__global__ void __launch_bounds__(VEC_THREADS)
+k_scale_batch(const VecItem *__restrict__ items, const long *__restrict__ start, int n, long total) {
     for (long t = blockIdx.x; t < total; t += gridDim.x) {
         const int r = find_item(start, n, t);
         const VecItem it = items[r];
-        const long o = (t - start[r]) * 256 + threadIdx.x;
-        if (o < it.n) it.out[o] = it.y[o] * *it.scale;
+        scale_tile(it.y, it.scale, it.out, it.n, t - start[r]);
     }
 }
 
@@ -507,7 +480,7 @@ cbct_status Engine::build_tables() {
                 ch.vec.lam = j->G->dscalars;
                 ch.vec.scale = (float *)(j->G->dscalars + 1);
                 ch.vec.n = (long)vol_elems(g);
-                ch.vec.nblk = (int)((ch.vec.n + 255) / 256);
+                ch.vec.nblk = (int)vec_tiles(ch.vec.n);
             } else {
                 max_m = std::max(max_m, j->P.M);
                 const size_t np = project_partials(g);
@@ -575,7 +548,7 @@ cbct_status Engine::build_tables() {
             vi.lam = j->G->dscalars;
             vi.scale = (float *)(j->G->dscalars + 1);
             vi.n = (long)vol_elems(g);
-            vi.nblk = (int)((vi.n + 255) / 256);
+            vi.nblk = (int)vec_tiles(vi.n);
             hdot.push_back(vi);
             dstart.push_back(dtot);
             dtot += vi.nblk;

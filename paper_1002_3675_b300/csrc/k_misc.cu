@@ -261,42 +261,17 @@ cudaError_t launch_step_copy(const float *v, float *f, size_t n, double *partial
     return cudaGetLastError();
 }
 
-// per-block partials of <x, y> and <y, y>: float32 within a warp (pairwise tree),
-// float64 across warps and blocks
-__global__ void k_dot2(const float *__restrict__ x, const float *__restrict__ y, size_t n, double *partial) {
-    float sxy = 0.f, syy = 0.f;
-    const size_t o = (size_t)blockIdx.x * 256 + threadIdx.x;
-    if (o < n) {
-        const float xv = x[o], yv = y[o];
-        sxy = xv * yv;
-        syy = yv * yv;
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-        sxy += __shfl_down_sync(0xffffffffu, sxy, off);
-        syy += __shfl_down_sync(0xffffffffu, syy, off);
-    }
-    __shared__ double a[8], b[8];
-    if ((threadIdx.x & 31) == 0) {
-        a[threadIdx.x >> 5] = (double)sxy;
-        b[threadIdx.x >> 5] = (double)syy;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s1 = 0.0, s2 = 0.0;
-        for (int w = 0; w < 8; ++w) {
-            s1 += a[w];
-            s2 += b[w];
-        }
-        partial[2 * blockIdx.x] = s1;
-        partial[2 * blockIdx.x + 1] = s2;
-    }
+// per-tile partials of <x, y> and <y, y> (dot2_tile)
+__global__ void __launch_bounds__(VEC_THREADS)
+k_dot2(const float *__restrict__ x, const float *__restrict__ y, size_t n, double *partial) {
+    dot2_tile(x, y, (long)n, blockIdx.x, partial);
 }
 
 cudaError_t launch_dot2(const float *x, const float *y, size_t n, double *partial, cudaStream_t s,
                         int *nblocks_out) {
-    const unsigned nb = (unsigned)((n + 255) / 256);
+    const unsigned nb = (unsigned)vec_tiles((long)n);
     if (nblocks_out) *nblocks_out = (int)nb;
-    k_dot2<<<nb, 256, 0, s>>>(x, y, n, partial);
+    k_dot2<<<nb, VEC_THREADS, 0, s>>>(x, y, n, partial);
     count_launch();
     return cudaGetLastError();
 }
@@ -331,17 +306,14 @@ cudaError_t launch_power_finalize(const double *partial, int nblk, double *lam, 
     return cudaGetLastError();
 }
 
-__global__ void k_scale(const float *__restrict__ y, const float *__restrict__ scale, float *__restrict__ x,
-                        size_t n) {
-    const float sc = *scale;
-    for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x)
-        x[o] = y[o] * sc;
+__global__ void __launch_bounds__(VEC_THREADS)
+k_scale(const float *__restrict__ y, const float *__restrict__ scale, float *__restrict__ x, size_t n) {
+    scale_tile(y, scale, x, (long)n, blockIdx.x);
 }
 
 cudaError_t launch_scale(const float *y, const float *scale, float *x, size_t n, cudaStream_t s) {
-    unsigned nb = (unsigned)((n + 255) / 256);
-    if (nb > 148u * 32u) nb = 148u * 32u;
-    k_scale<<<nb > 0 ? nb : 1, 256, 0, s>>>(y, scale, x, n);
+    const unsigned nb = (unsigned)vec_tiles((long)n);
+    k_scale<<<nb > 0 ? nb : 1, VEC_THREADS, 0, s>>>(y, scale, x, n);
     count_launch();
     return cudaGetLastError();
 }

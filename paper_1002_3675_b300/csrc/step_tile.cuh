@@ -1,5 +1,6 @@
-// Device-side block of the step norm |f_k+1 - f_k| of Algorithm A1 (shared by the
-// single-request and batched kernels, so both give the same partials bit for bit).
+// Device-side blocks of the step norm |f_k+1 - f_k| of Algorithm A1 and of the power
+// iteration's dot products and scaling (shared by the single-request and batched
+// kernels, so both give the same partials bit for bit).
 #pragma once
 #include "cbct_internal.h"
 
@@ -29,6 +30,57 @@ __device__ __forceinline__ void step_block(const float *__restrict__ v, float *_
         partial[blk] = s;
     }
     __syncthreads();
+}
+
+// Power iteration: tiles of VEC_TILE elements, 4 per thread of a 256-thread block.
+constexpr int VEC_THREADS = 256;
+constexpr int VEC_TILE = 4 * VEC_THREADS;
+__host__ __device__ __forceinline__ long vec_tiles(long n) { return (n + VEC_TILE - 1) / VEC_TILE; }
+
+// partial[2 t] = <x, y>, partial[2 t + 1] = <y, y> over tile t: float32 per thread (4
+// elements in order) and within a warp (pairwise tree), float64 across the 8 warps.
+__device__ __forceinline__ void dot2_tile(const float *__restrict__ x, const float *__restrict__ y, long n,
+                                          long t, double *__restrict__ partial) {
+    __shared__ double a[VEC_THREADS / 32], b[VEC_THREADS / 32];
+    float sxy = 0.f, syy = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const long o = t * VEC_TILE + q * VEC_THREADS + threadIdx.x;
+        if (o < n) {
+            const float xv = x[o], yv = y[o];
+            sxy = __fmaf_rn(xv, yv, sxy);
+            syy = __fmaf_rn(yv, yv, syy);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        sxy = __fadd_rn(sxy, __shfl_down_sync(0xffffffffu, sxy, off));
+        syy = __fadd_rn(syy, __shfl_down_sync(0xffffffffu, syy, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        a[threadIdx.x >> 5] = (double)sxy;
+        b[threadIdx.x >> 5] = (double)syy;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int w = 0; w < VEC_THREADS / 32; ++w) {
+            s1 += a[w];
+            s2 += b[w];
+        }
+        partial[2 * t] = s1;
+        partial[2 * t + 1] = s2;
+    }
+    __syncthreads();
+}
+
+// x = y * scale over tile t
+__device__ __forceinline__ void scale_tile(const float *y, const float *scale, float *x, long n, long t) {
+    const float sc = *scale;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const long o = t * VEC_TILE + q * VEC_THREADS + threadIdx.x;
+        if (o < n) x[o] = __fmul_rn(y[o], sc);
+    }
 }
 
 }  // namespace cbct
