@@ -180,27 +180,12 @@ k_scale_batch(const VecItem *__restrict__ items, const long *__restrict__ start,
     }
 }
 
-__device__ double block_sum_fixed_b(const double *p, int n) {
-    __shared__ double sh[256];
-    double s = 0.0;
-    for (int q = threadIdx.x; q < n; q += 256) s += p[q];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-        __syncthreads();
-    }
-    double r = sh[0];
-    __syncthreads();
-    return r;
-}
-
 // The same sums and trace entries as the single-request energy finalisation.
-__global__ void k_energy_batch(const EnItem *__restrict__ items) {
+__global__ void __launch_bounds__(ENERGY_THREADS) k_energy_batch(const EnItem *__restrict__ items) {
     const EnItem it = items[blockIdx.x];
-    const double q = block_sum_fixed_b(it.pe2, it.n2);
-    const double t = block_sum_fixed_b(it.pe1, it.n1);
-    const double d = block_sum_fixed_b(it.pstep, it.nstep);
+    __shared__ double sums[3];
+    sum3_fixed(it.pe2, it.n2, it.pe1, it.n1, it.pstep, it.nstep, sums);
+    const double q = sums[0], t = sums[1], d = sums[2];
     if (threadIdx.x == 0) {
         const int k = *it.counter;
         const double e1 = t * it.inv_nv, e2 = q * it.mu_over_nr;
@@ -892,7 +877,7 @@ cbct_status Engine::launch_stages() {
         ECK(cudaStreamWaitEvent(s, side_events[q + 1], 0), "join wait");
     }
     if (!hen.empty()) {
-        k_energy_batch<<<(unsigned)hen.size(), 256, 0, s>>>(d_en);
+        k_energy_batch<<<(unsigned)hen.size(), ENERGY_THREADS, 0, s>>>(d_en);
         count_launch();
         ECK(cudaGetLastError(), "batched energy");
     }

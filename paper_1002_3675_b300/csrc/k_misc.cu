@@ -203,30 +203,15 @@ cudaError_t launch_prolong(const float *fc, int c0, int c1, int c2, float *f, in
 // Deterministic float64 reductions (fixed partition, fixed tree)
 // ---------------------------------------------------------------------------------
 
-__device__ double block_sum_fixed(const double *p, int n) {
-    // one block of 256 threads: strided serial sums, then a fixed tree
-    __shared__ double sh[256];
-    double s = 0.0;
-    for (int q = threadIdx.x; q < n; q += 256) s += p[q];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-        __syncthreads();
-    }
-    double r = sh[0];
-    __syncthreads();
-    return r;
-}
-
 // E = E1 + mu E2 with E1 = sum|grad f|_eps / Nv and mu E2 = mu |r|^2 / Nr, and (when
 // pstep is given) |f_k+1 - f_k|_2 from its partials; written to trace[TRACE_W * (*counter)]
 // and the counter advanced (so a captured graph can be replayed).
-__global__ void k_energy_finalize(const double *pe2, int n2, const double *pe1, int n1, const double *pstep,
-                                  int nstep, double inv_nv, double mu_over_nr, double *trace, int *counter) {
-    const double q = block_sum_fixed(pe2, n2);
-    const double t = block_sum_fixed(pe1, n1);
-    const double d = pstep ? block_sum_fixed(pstep, nstep) : 0.0;
+__global__ void __launch_bounds__(ENERGY_THREADS)
+k_energy_finalize(const double *pe2, int n2, const double *pe1, int n1, const double *pstep, int nstep,
+                  double inv_nv, double mu_over_nr, double *trace, int *counter) {
+    __shared__ double sums[3];
+    sum3_fixed(pe2, n2, pe1, n1, pstep, pstep ? nstep : 0, sums);
+    const double q = sums[0], t = sums[1], d = sums[2];
     if (threadIdx.x == 0) {
         const int it = *counter;
         const double e1 = t * inv_nv, e2 = q * mu_over_nr;
@@ -241,7 +226,8 @@ __global__ void k_energy_finalize(const double *pe2, int n2, const double *pe1, 
 cudaError_t launch_energy_finalize(const double *pe2, int n2, const double *pe1, int n1, double inv_nv,
                                    double mu_over_nr, double *trace, int *counter, cudaStream_t s,
                                    const double *pstep, int nstep) {
-    k_energy_finalize<<<1, 256, 0, s>>>(pe2, n2, pe1, n1, pstep, nstep, inv_nv, mu_over_nr, trace, counter);
+    k_energy_finalize<<<1, ENERGY_THREADS, 0, s>>>(pe2, n2, pe1, n1, pstep, nstep, inv_nv, mu_over_nr, trace,
+                                                   counter);
     count_launch();
     return cudaGetLastError();
 }

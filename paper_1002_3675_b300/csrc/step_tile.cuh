@@ -32,6 +32,29 @@ __device__ __forceinline__ void step_block(const float *__restrict__ v, float *_
     __syncthreads();
 }
 
+// Energy finalisation: the three float64 sums of a trace entry at once, one group of
+// 256 threads per array (block of ENERGY_THREADS): group g sums its array strided by
+// 256 (thread q: p[q], p[q + 256], ...), then by a fixed tree, so each sum is that of a
+// single 256-thread block.  out[g] (shared) receives sum g; n = 0 gives 0.
+constexpr int ENERGY_THREADS = 768;
+__device__ __forceinline__ void sum3_fixed(const double *p0, int n0, const double *p1, int n1, const double *p2,
+                                           int n2, double *out) {
+    __shared__ double sh[ENERGY_THREADS];
+    const int grp = threadIdx.x >> 8, q0 = threadIdx.x & 255;
+    const double *p = grp == 0 ? p0 : grp == 1 ? p1 : p2;
+    const int n = grp == 0 ? n0 : grp == 1 ? n1 : n2;
+    double s = 0.0;
+    for (int q = q0; q < n; q += 256) s += p[q];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (q0 < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (q0 == 0) out[grp] = sh[threadIdx.x];
+    __syncthreads();
+}
+
 // Power iteration: tiles of VEC_TILE elements, 4 per thread of a 256-thread block.
 constexpr int VEC_THREADS = 256;
 constexpr int VEC_TILE = 4 * VEC_THREADS;
