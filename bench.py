@@ -219,10 +219,11 @@ def run_reference(args, world, rank):
     sample = (f"1 Algorithm A1 iteration (P, P^T, 10 prox sweeps) of the finest level per step "
               f"({WORKLOAD_TEXT[args.workload].split(',')[0]}), {args.steps} steps")
     line = {"impl": "reference", "metric": "FBS iterations/s", "value": value, "unit": "iter/s",
-            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded ellipsoid phantom, analytic line integrals, Poisson/log noise)",
-            "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "host_cores": os.cpu_count()},
+            "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "host_cores": os.cpu_count(),
+                       "note": "the FP64 oracle on the host cores (rank 0 only); n_gpus is the launch's rank count"},
             "cpu_baseline": {"value": value, "unit": "iter/s", "cores": cores, "cpu_model": cpu_model(), "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
