@@ -449,6 +449,59 @@ def test_kernel_timing_report(lib):
     assert m["kernel_ms"]["backproject"] > 0 and m["kernel_ms"]["tv"] == 0 and m["kernel_ms"]["project"] == 0
 
 
+@pytest.mark.parametrize("g", [
+    dict(nx=1, ny=1, nz=1, hx=2.0, hy=2.0, hz=2.0, nu=1, nv=1, du=3.0, dv=3.0, dso=100.0, dsd=150.0,
+         angles=np.array([0.3])),                                   # one voxel, one ray
+    dict(nx=2, ny=3, nz=1, hx=1.5, hy=2.0, hz=2.5, nu=5, nv=1, du=1.2, dv=4.0, dso=120.0, dsd=200.0,
+         angles=2 * math.pi * np.arange(3) / 3 + 0.1),              # one slice, one imager row
+    dict(nx=1, ny=1, nz=40, hx=3.0, hy=3.0, hz=1.0, nu=1, nv=50, du=5.0, dv=1.3, dso=150.0, dsd=250.0,
+         angles=np.array([0.0, 1.7])),                              # one column, one imager column
+])
+def test_degenerate_sizes_match_oracle(lib, g):
+    """Single voxels, single imager rows and columns: projection, adjoint, one prox and
+    two Algorithm A1 iterations against the oracle."""
+    rng = np.random.default_rng(33)
+    shape, sshape = (g["nz"], g["ny"], g["nx"]), (len(g["angles"]), g["nv"], g["nu"])
+    f = rng.uniform(0.0, 0.02, size=shape)
+    y = rng.uniform(0.0, 1.0, size=sshape)
+    G = lib.cbct_geometry_create(g)
+    p_ref = oracle.project(g, f32(f))
+    p_gpu = host(lib.cbct_project(G, dev(f)))
+    assert np.abs(p_gpu - p_ref).max() <= P_TOL * max(np.abs(p_ref).max(), 1e-30)
+    b_ref = oracle.backproject(g, f32(y))
+    b_gpu = host(lib.cbct_backproject(G, dev(y)))
+    assert np.abs(b_gpu - b_ref).max() <= P_TOL * max(np.abs(b_ref).max(), 1e-30)
+    h = (g["hx"], g["hy"], g["hz"])
+    gv = f + rng.normal(scale=0.002, size=shape)
+    ft = dev(f)
+    lib.cbct_tv_prox(G, dev(gv), ft, 1.0e4, 1e-3, 5)
+    ref = oracle.prox(f32(gv), f32(f), h, 1.0e4, 1e-3, 5)
+    assert np.abs(host(ft) - ref).max() <= 1e-5 * max(np.abs(ref).max(), 1e-30)
+    Y = f32(oracle.project(g, f32(f))) * 1.1
+    beta = 2.0 * max(1.0, oracle.gamma(g, 1.0) * oracle.power_iteration(g, 30))
+    f_ref, tr_ref = oracle.fbs(g, Y, 1.0, beta, 1e-3, 10, 2)
+    fg, tr = lib.cbct_fbs(G, dev(Y), 1.0, beta, 1e-3, 10, 0, 2, dev(np.zeros(shape)), trace=True)
+    fg = host(fg)
+    assert (fg >= 0).all() and np.abs(fg - f_ref).max() <= VOL_TOL * max(np.abs(f_ref).max(), 1e-30)
+    assert np.all(np.abs(tr - tr_ref) <= 1e-4 * np.abs(tr_ref) + 1e-12)
+
+
+def test_zero_iterations_and_zero_data(lib):
+    """iters = 0 returns the start (zero) volume and an empty trace; zero data keep the
+    iterate at exactly +0.0 (every gradient vanishes there)."""
+    case = synth.make_case("small")
+    g = case["geom"]
+    G = lib.cbct_geometry_create(g)
+    f, info = lib.cbct_reconstruct(G, dev(case["Y"]), case["mu"], 0, 2, betas=[1.0e6, 1.0e6], trace=True)
+    f = host(f)
+    assert np.all(f == 0) and not np.signbit(f).any() and info["trace"].shape == (2, 0, 3)
+    fz, tr = lib.cbct_fbs(G, dev(np.zeros((20, 48, 64))), case["mu"], 1.0e6, 1e-3, 10, 0, 3,
+                          dev(np.zeros((64, 64, 64))), trace=True)
+    fz = host(fz)
+    assert np.all(fz == 0) and not np.signbit(fz).any()
+    assert np.all(tr[:, 2] == 0) and np.allclose(tr[:, 1], 1e-3, rtol=1e-6)   # E1 = eps, mu E2 = 0
+
+
 def test_invalid_arguments_on_device(lib):
     case = synth.make_case("small")
     G = lib.cbct_geometry_create(case["geom"])
