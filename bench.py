@@ -251,9 +251,10 @@ def run_gpu(args, world, rank, local):
     # launching stream); every class is timed in a separate pass after the timed region
     timed_mask = (1 << cbct.KERNEL_CLASSES.index("project")) | (1 << cbct.KERNEL_CLASSES.index("backproject"))
 
-    def step(kernel_times, mask=timed_mask):
+    def step(kernel_times, mask=timed_mask, serial_power=False):
         return cbct.cbct_reconstruct(G, Y, mu, iters, levels, f_out=f, kernel_times=kernel_times, kernel_mask=mask,
-                                     tv_mode=args.tv_mode, adjoint_mode=args.adjoint_mode, sino_fp16=args.sino_fp16)
+                                     tv_mode=args.tv_mode, adjoint_mode=args.adjoint_mode, sino_fp16=args.sino_fp16,
+                                     serial_power=serial_power)
 
     for _ in range(args.warmup):
         step(False)
@@ -263,7 +264,7 @@ def run_gpu(args, world, rank, local):
     sampler = ClockSampler(local) if rank == 0 else None
     barrier(world)
     torch.cuda.synchronize()
-    step_ms, kms, klaunch = [], {}, {}
+    step_ms, kms, klaunch, kms_f, kl_f = [], {}, {}, {}, {}
     n_launch0 = cbct.cbct_kernel_launch_count()
     for _ in range(args.steps):
         flush.fill_(1)
@@ -277,6 +278,10 @@ def run_gpu(args, world, rank, local):
             kms[k] = kms.get(k, 0.0) + v
         for k, v in info["kernel_launches"].items():
             klaunch[k] = klaunch.get(k, 0) + v
+        for k, v in info["kernel_ms_finest"].items():
+            kms_f[k] = kms_f.get(k, 0.0) + v
+        for k, v in info["kernel_launches_finest"].items():
+            kl_f[k] = kl_f.get(k, 0) + v
     torch.cuda.synchronize()
     n_launch = cbct.cbct_kernel_launch_count() - n_launch0
     barrier(world)
@@ -302,11 +307,12 @@ def run_gpu(args, world, rank, local):
     e2e_tot = max_over_ranks(sum(e2e_ms), world)
     e2e_value = world * args.steps * n_iter / (e2e_tot / 1e3)
 
-    # ---- every kernel class timed launch by launch (a separate pass of the same steps) --
+    # ---- every kernel class timed launch by launch (a separate pass of the same steps, the
+    #      power iterations in level order so that no two streams share the event windows) --
     split_ms, split_n = {}, {}
     for _ in range(args.steps):
         flush.fill_(1)
-        _, info = step(True, mask=0)
+        _, info = step(True, mask=0, serial_power=True)
         for k, v in info["kernel_ms"].items():
             split_ms[k] = split_ms.get(k, 0.0) + v
         for k, v in info["kernel_launches"].items():
@@ -347,16 +353,22 @@ def run_gpu(args, world, rank, local):
     clock_mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") \
         or peaks.get("sm_max_mhz", 2032.0)
     alu_peak = sm_count * 128 * clock_mhz * 1e6 / 1e12      # T lane-ops/s (FP32 pipes x clock)
+    # rates from the finest level's Algorithm A1 iterations, timed inside the timed steps:
+    # they run after every power iteration has finished, so nothing shares their event
+    # windows (the finer levels' power iterations overlap the coarser levels on a side
+    # stream); the per-class totals come from the separate serial pass
+    units_f = {k: nnz[0] * iters for k in ("project", "backproject")}
     per_kernel = {}
     for k in ("project", "backproject"):
-        t = kms[k] / 1e3
+        t = kms_f[k] / 1e3
+        per_kernel[k] = {"ms_per_step": split_ms[k] / args.steps, "launches_per_step": split_n[k] / args.steps,
+                         "finest_fbs_ms_per_step": kms_f[k] / args.steps,
+                         "finest_fbs_launches_per_step": kl_f[k] / args.steps}
         if k == "backproject" and args.adjoint_mode == 1:
-            per_kernel[k] = {"ms_per_step": kms[k] / args.steps, "launches_per_step": klaunch[k] / args.steps,
-                             "note": "Eq. 2 adjoint in the FBS iterations, exact transpose in the power iterations"}
+            per_kernel[k]["note"] = "Eq. 2 adjoint in the FBS iterations: no nonzero-based rate"
             continue
-        per_kernel[k] = {"ms_per_step": kms[k] / args.steps, "launches_per_step": klaunch[k] / args.steps,
-                         "gnnz_per_s": units[k] * args.steps / t / 1e9,
-                         "alu_tops": units[k] * args.steps * OPS_PER_NNZ[k] / t / 1e12}
+        per_kernel[k]["gnnz_per_s"] = units_f[k] * args.steps / t / 1e9
+        per_kernel[k]["alu_tops"] = units_f[k] * args.steps * OPS_PER_NNZ[k] / t / 1e12
     nvox = [np.prod([(n + (1 << l) - 1) >> l for n in cfg["vol"]]) for l in range(levels)]
     tv_bytes = sum(12.0 * v * iters * 10 for v in nvox) * args.steps   # read f, read g, write f per sweep
     per_kernel["tv"] = {"ms_per_step": split_ms["tv"] / args.steps,
@@ -366,11 +378,13 @@ def run_gpu(args, world, rank, local):
         ach = per_kernel[dom]["alu_tops"]
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tlane-op/s",
                 "frac": ach / alu_peak, "traffic": profile_traffic(dom, args.workload),
-                "launch_ms": kms[dom] / (args.steps * levels * (iters + K_pi)),
-                "timing": "CUDA events around every operation of the class inside the timed steps; launch_ms is "
+                "launch_ms": kms_f[dom] / (args.steps * iters),
+                "timing": "CUDA events around every operation of the class in the finest level's Algorithm A1 "
+                          "iterations inside the timed steps (no other stream's work beside them); launch_ms is "
                           "the time of one operation (the adjoint: column running sums + gather)",
-                "basis": f"{OPS_PER_NNZ[dom]:.0f} lane-ops per nonzero x exact nnz; peak = {sm_count} SMs x 128 "
-                         f"FP32 lanes x {clock_mhz:.0f} MHz (median SM clock in the timed region)"}
+                "basis": f"{OPS_PER_NNZ[dom]:.0f} lane-ops per nonzero x the finest level's exact nnz; peak = "
+                         f"{sm_count} SMs x 128 FP32 lanes x {clock_mhz:.0f} MHz (median SM clock in the timed "
+                         "region)"}
     else:
         ach = per_kernel["tv"]["gbs"]
         roof = {"kernel": "tv", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -466,8 +480,10 @@ def run_gpu(args, world, rank, local):
         "roofline": roof,
         "kernels": per_kernel,
         "kernel_ms_per_step": {k: v / args.steps for k, v in split_ms.items()},
-        "kernel_split_note": "every launch timed with CUDA events in a separate pass of the same steps; the "
-                             "timed steps time only the project and backproject launches",
+        "kernel_split_note": "kernel_ms_per_step: every launch timed with CUDA events in a separate pass of the "
+                             "same steps, the power iterations in level order (serial_power); the timed steps "
+                             "time the project and backproject launches, and the rates and the roofline use "
+                             "those of the finest level's Algorithm A1 iterations",
         "gpu_launches": launches,
         "per_iteration": per_iter,
         "quality": quality,

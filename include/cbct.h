@@ -132,6 +132,14 @@ typedef struct {
                              iteration (float64 sum of float32 squares), coarsest
                              level first, like energy_trace; with mg_cycle 1,
                              [iters]: the change of the finest iterate over each cycle */
+    int serial_power;     /* 1: the power iterations of the finer levels of a cascade run
+                             in level order on `stream`; 0 [default]: they run on a
+                             side stream of the geometry while the coarser levels iterate
+                             (they depend on the geometry alone; the same results)     */
+    float *kernel_ms_finest; /* optional host out [CBCT_NUM_KERNEL_CLASSES]: like
+                             kernel_ms, over the finest level's Algorithm A1 iterations
+                             alone (no other stream's work runs beside them)           */
+    int *kernel_launches_finest; /* optional host out [CBCT_NUM_KERNEL_CLASSES]         */
 } cbct_options;
 
 /* Kernel classes reported through cbct_options.kernel_ms. */

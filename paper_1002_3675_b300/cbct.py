@@ -47,7 +47,8 @@ class Options(C.Structure):
                 ("tv_mode", C.c_int),
                 ("adjoint_mode", C.c_int), ("mg_cycle", C.c_int), ("mg_pre", C.c_int), ("mg_post", C.c_int),
                 ("mg_coarse", C.c_int), ("mg_accepted", C.POINTER(C.c_int)),
-                ("step_trace", C.POINTER(C.c_double))]
+                ("step_trace", C.POINTER(C.c_double)), ("serial_power", C.c_int),
+                ("kernel_ms_finest", C.POINTER(C.c_float)), ("kernel_launches_finest", C.POINTER(C.c_int))]
 
 
 class Request(C.Structure):
@@ -292,11 +293,12 @@ def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=N
                      betas=None, eps=0.0, inner_iters=0, clamp_mode=0, sino_fp16=False, power_iters=0,
                      f_init=None, start_level=0, use_graphs=False, trace=False, kernel_times=False,
                      reuse_lambda=False, tv_mode=0, adjoint_mode=0, mg_cycle=0, mg_pre=0, mg_post=0, mg_coarse=0,
-                     kernel_mask=0):
+                     kernel_mask=0, serial_power=False):
     """Returns f_out, or (f_out, info) when trace/kernel_times is requested; info holds
     'trace' [levels][iters][3] ([iters][3] after each V-cycle when mg_cycle=1),
     'step_trace' [levels][iters] |f_k+1 - f_k| ([iters], the change over each V-cycle),
-    'betas' [levels], 'accepted' [levels] (V-cycles), 'kernel_ms'/'kernel_launches'."""
+    'betas' [levels], 'accepted' [levels] (V-cycles), 'kernel_ms'/'kernel_launches' and
+    'kernel_ms_finest'/'kernel_launches_finest' (the finest level's A1 iterations)."""
     f_out = _empty(g.vol_shape) if f_out is None else f_out
     o = Options()
     o.beta = beta
@@ -315,6 +317,7 @@ def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=N
     o.tv_mode = int(tv_mode)
     o.adjoint_mode = int(adjoint_mode)
     o.mg_cycle, o.mg_pre, o.mg_post, o.mg_coarse = int(mg_cycle), int(mg_pre), int(mg_post), int(mg_coarse)
+    o.serial_power = int(bool(serial_power))
     acc = (C.c_int * 8)()
     o.mg_accepted = acc
     tr = np.full((levels, max(iters, 1), 3), np.nan) if trace else None
@@ -326,9 +329,13 @@ def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=N
     o.beta_out = bo.ctypes.data_as(C.POINTER(C.c_double))
     km = (C.c_float * NUM_KERNEL_CLASSES)() if kernel_times else None
     kl = (C.c_int * NUM_KERNEL_CLASSES)() if kernel_times else None
+    kmf = (C.c_float * NUM_KERNEL_CLASSES)() if kernel_times else None
+    klf = (C.c_int * NUM_KERNEL_CLASSES)() if kernel_times else None
     if kernel_times:
         o.kernel_ms = km
         o.kernel_launches = kl
+        o.kernel_ms_finest = kmf
+        o.kernel_launches_finest = klf
         o.kernel_mask = int(kernel_mask)
     _check(lib.cbct_reconstruct(g.handle, _ptr(Y, "Y"), g.angles.ctypes.data_as(C.POINTER(C.c_double)),
                                 len(g.angles), mu, iters, levels, C.byref(o), _ptr(f_out, "f_out"), _stream()))
@@ -343,6 +350,8 @@ def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=N
     if kernel_times:
         info["kernel_ms"] = dict(zip(KERNEL_CLASSES, list(km)))
         info["kernel_launches"] = dict(zip(KERNEL_CLASSES, list(kl)))
+        info["kernel_ms_finest"] = dict(zip(KERNEL_CLASSES, list(kmf)))
+        info["kernel_launches_finest"] = dict(zip(KERNEL_CLASSES, list(klf)))
     return f_out, info
 
 

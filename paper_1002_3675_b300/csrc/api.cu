@@ -104,53 +104,63 @@ struct Prof {
     unsigned mask = ~0u;     // kernel classes timed with events (all launches are counted)
     bool timing = false;     // the current launch is timed
     int cur = 0;             // class of the current operation
+    cudaStream_t cur_s = 0;  // stream of the current operation
+    int tag = 0;             // 1 while the finest level's Algorithm A1 iterations are enqueued
     unsigned long long k0 = 0;
-    std::vector<int> cls;
+    std::vector<int> cls, tags;
     std::vector<cudaEvent_t> a, b;
-    int count[CBCT_NUM_KERNEL_CLASSES] = {};
-    void begin(int c) {
+    int count[CBCT_NUM_KERNEL_CLASSES] = {}, count_tag[CBCT_NUM_KERNEL_CLASSES] = {};
+    void begin(int c, cudaStream_t st) {
         if (!on) return;
         cur = c;
+        cur_s = st;
         k0 = g_kernel_launches.load(std::memory_order_relaxed);
         timing = (mask >> c) & 1u;
         if (!timing) return;
         cudaEvent_t e0 = G->events.get();
-        cudaEventRecord(e0, s);
+        cudaEventRecord(e0, st);
         a.push_back(e0);
         cls.push_back(c);
+        tags.push_back(tag);
     }
     void end() {
         if (!on) return;
-        count[cur] += (int)(g_kernel_launches.load(std::memory_order_relaxed) - k0);  // kernels it launched
+        const int n = (int)(g_kernel_launches.load(std::memory_order_relaxed) - k0);  // kernels it launched
+        count[cur] += n;
+        if (tag) count_tag[cur] += n;
         if (!timing) return;
         cudaEvent_t e1 = G->events.get();
-        cudaEventRecord(e1, s);
+        cudaEventRecord(e1, cur_s);
         b.push_back(e1);
         timing = false;
     }
-    cbct_status collect(float *ms, int *cnt) {
+    // ms/cnt: every timed operation; ms_t/cnt_t: those enqueued with the tag set
+    cbct_status collect(float *ms, int *cnt, float *ms_t = nullptr, int *cnt_t = nullptr) {
         if (!on) return CBCT_OK;
         CK(cudaStreamSynchronize(s), "synchronising for kernel timing");
         for (int c = 0; c < CBCT_NUM_KERNEL_CLASSES; ++c) {
             if (ms) ms[c] = 0.f;
-            if (cnt) cnt[c] = 0;
+            if (ms_t) ms_t[c] = 0.f;
         }
         for (size_t q = 0; q < cls.size() && q < b.size(); ++q) {
             float t = 0.f;
             cudaEventElapsedTime(&t, a[q], b[q]);
             if (ms) ms[cls[q]] += t;
+            if (ms_t && tags[q]) ms_t[cls[q]] += t;
         }
-        for (int c = 0; c < CBCT_NUM_KERNEL_CLASSES; ++c)
+        for (int c = 0; c < CBCT_NUM_KERNEL_CLASSES; ++c) {
             if (cnt) cnt[c] = count[c];
+            if (cnt_t) cnt_t[c] = count_tag[c];
+        }
         G->events.release_all();
         return CBCT_OK;
     }
 };
 
-struct Launch {  // wraps one kernel launch with optional timing
+struct Launch {  // wraps one kernel launch with optional timing (on prof's stream, or st)
     Prof &p;
     int c;
-    Launch(Prof &pp, int cc) : p(pp), c(cc) { p.begin(c); }
+    Launch(Prof &pp, int cc, cudaStream_t st = nullptr) : p(pp), c(cc) { p.begin(c, st ? st : p.s); }
     ~Launch() { p.end(); }
 };
 
@@ -260,15 +270,14 @@ cbct_status run_level(cbct_geometry *G, Level *L, const SolveParams &P, int iter
     return CBCT_OK;
 }
 
-// lambda_max(P^T P) by K power iterations from the seeded uniform(0,1) volume.
-cbct_status power_iteration(cbct_geometry *G, Level *L, int K, double *lam, Prof &prof, cudaStream_t s) {
+// Enqueues K power iterations on level L (no synchronisation): lambda into *dlam, the
+// scale scratch at *dscale.
+cbct_status enqueue_power(Level *L, int K, double *dlam, float *dscale, Prof &prof, cudaStream_t s) {
     const GeoDev &gd = L->gd;
     const size_t nv = vol_elems(gd);
     float *x = L->A, *y = L->B;
-    double *dlam = G->dscalars;
-    float *dscale = (float *)(G->dscalars + 1);
     {
-        Launch l(prof, CBCT_K_REDUCE);
+        Launch l(prof, CBCT_K_REDUCE, s);
         // x = u / |u| for the seeded uniform volume u (built in y), by the same reductions
         // as every iteration, so that every estimate is a Rayleigh quotient
         CK(launch_fill_uniform(y, gd.nx, gd.ny, gd.nz, POWER_SEED, s), "start volume");
@@ -279,21 +288,40 @@ cbct_status power_iteration(cbct_geometry *G, Level *L, int K, double *lam, Prof
     }
     for (int it = 0; it < K; ++it) {
         {
-            Launch l(prof, CBCT_K_PROJECT);
+            Launch l(prof, CBCT_K_PROJECT, s);
             CK(launch_project(gd, x, nullptr, nullptr, L->rs, nullptr, PROJ_SCALED, s, nullptr), "projection");
         }
         {
-            Launch l(prof, CBCT_K_BACKPROJECT);
+            Launch l(prof, CBCT_K_BACKPROJECT, s);
             CK(launch_backproject(gd, L->rs, nullptr, y, 0.f, BP_PLAIN, s), "backprojection");
         }
         int nb = 0;
-        Launch l(prof, CBCT_K_REDUCE);
+        Launch l(prof, CBCT_K_REDUCE, s);
         CK(launch_dot2(x, y, nv, L->partial, s, &nb), "dot");
         CK(launch_power_finalize(L->partial, nb, dlam, dscale, s), "power finalize");
         CK(launch_scale(y, dscale, x, nv, s), "scale");
     }
+    return CBCT_OK;
+}
+
+// lambda_max(P^T P) by K power iterations from the seeded uniform(0,1) volume.
+cbct_status power_iteration(cbct_geometry *G, Level *L, int K, double *lam, Prof &prof, cudaStream_t s) {
+    double *dlam = G->dscalars;
+    ST(enqueue_power(L, K, dlam, (float *)(G->dscalars + 1), prof, s));
     CK(cudaMemcpyAsync(lam, dlam, sizeof(double), cudaMemcpyDeviceToHost, s), "lambda copy");
     CK(cudaStreamSynchronize(s), "power iteration");
+    return CBCT_OK;
+}
+
+// The geometry's side stream, its events and the pinned lambda slots (created once).
+cbct_status ensure_side(cbct_geometry *G) {
+    if (G->side) return CBCT_OK;
+    cudaStream_t st = nullptr;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "side stream");
+    G->side = st;
+    CK(cudaEventCreateWithFlags(&G->side_fork, cudaEventDisableTiming), "side event");
+    for (auto &e : G->side_done) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "side event");
+    CK(cudaMallocHost(&G->host_lam, 13 * sizeof(double)), "pinned lambda slots");
     return CBCT_OK;
 }
 
@@ -652,6 +680,13 @@ cbct_status cbct_geometry_create(const cbct_geometry_desc *desc, const double *a
 
 void cbct_geometry_destroy(cbct_geometry *G) {
     if (!G) return;
+    if (G->side) {
+        cudaStreamSynchronize(G->side);
+        cudaStreamDestroy(G->side);
+        cudaEventDestroy(G->side_fork);
+        for (auto e : G->side_done) cudaEventDestroy(e);
+        cudaFreeHost(G->host_lam);
+    }
     for (auto *L : G->levels) free_level(L);
     cudaFree(G->dscalars);
     cudaFree(G->dcounter);
@@ -901,7 +936,8 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
     Prof prof;
     prof.G = G;
     prof.s = s;
-    prof.on = o.kernel_ms != nullptr || o.kernel_launches != nullptr;
+    prof.on = o.kernel_ms != nullptr || o.kernel_launches != nullptr || o.kernel_ms_finest != nullptr ||
+              o.kernel_launches_finest != nullptr;
     if (o.kernel_mask) prof.mask = o.kernel_mask;
     if (prof.on) G->events.release_all();
 
@@ -919,6 +955,30 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
         if (fp16) CK(launch_to_half(Ls[l]->Y, Ls[l]->Yh, sino_elems(Ls[l]->gd), s), "half copy");
     }
 
+    // Cascade with the automatic beta: the power iterations of the finer levels depend
+    // on the geometry alone, so they run on the geometry's side stream while the
+    // coarser levels iterate; a level waits for its own before its buffers are reused.
+    // The kernels and their inputs are those of the plain order, so is every bit.
+    bool side_lam[13] = {};
+    if (o.mg_cycle != 1 && !o.serial_power && !o.betas && !(o.beta > 0) && start > 0) {
+        bool any = false;
+        for (int l = start - 1; l >= 0; --l) any = any || !(o.reuse_lambda && Ls[l]->lambda_iters == K);
+        if (any) {
+            ST(ensure_side(G));
+            CK(cudaEventRecord(G->side_fork, s), "fork");
+            CK(cudaStreamWaitEvent(G->side, G->side_fork, 0), "fork");
+            for (int l = start - 1; l >= 0; --l) {
+                if (o.reuse_lambda && Ls[l]->lambda_iters == K) continue;
+                double *dl = G->dscalars + 16 + 2 * l;
+                ST(enqueue_power(Ls[l], K, dl, (float *)(dl + 1), prof, G->side));
+                CK(cudaMemcpyAsync(G->host_lam + l, dl, sizeof(double), cudaMemcpyDeviceToHost, G->side),
+                   "lambda copy");
+                CK(cudaEventRecord(G->side_done[l], G->side), "join");
+                side_lam[l] = true;
+            }
+        }
+    }
+
     auto level_beta = [&](int l, double *beta) -> cbct_status {
         Level *L = Ls[l];
         if (o.betas) {
@@ -927,7 +987,13 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
             *beta = o.beta;
         } else {
             double lam = 0.0;
-            if (o.reuse_lambda && L->lambda_iters == K) {
+            if (side_lam[l]) {  // computed on the side stream
+                CK(cudaEventSynchronize(G->side_done[l]), "power iteration");
+                CK(cudaStreamWaitEvent(s, G->side_done[l], 0), "join");
+                lam = G->host_lam[l];
+                L->lambda = lam;
+                L->lambda_iters = K;
+            } else if (o.reuse_lambda && L->lambda_iters == K) {
                 lam = L->lambda;
             } else {
                 ST(power_iteration(G, L, K, &lam, prof, s));
@@ -988,7 +1054,7 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
             const GeoDev &g0 = Ls[0]->gd;
             CK(launch_vol_to_api(Ls[0]->f, f_out_dev, g0.nx, g0.ny, g0.nz, s), "volume layout");
         }
-        return prof.collect(o.kernel_ms, o.kernel_launches);
+        return prof.collect(o.kernel_ms, o.kernel_launches, o.kernel_ms_finest, o.kernel_launches_finest);
     }
 
     for (int l = start; l >= 0; --l) {
@@ -1010,7 +1076,9 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
         const double eps = o.eps > 0 ? o.eps : default_eps(L);
         SolveParams P;
         ST(solve_params(L, mu, beta, eps, M, o.clamp_mode, fp16, &P, o.tv_mode, o.adjoint_mode));
+        prof.tag = l == 0 ? 1 : 0;
         ST(run_level(G, L, P, iters, dtrace, o.use_graphs != 0, prof, s));
+        prof.tag = 0;
         if ((o.energy_trace || o.step_trace) && iters > 0) {
             const size_t lv = (size_t)iters * (levels - 1 - l);
             ST(copy_trace(dtrace, iters, o.energy_trace ? o.energy_trace + 3 * lv : nullptr,
@@ -1023,7 +1091,7 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
         const GeoDev &g0 = Ls[0]->gd;
         CK(launch_vol_to_api(Ls[0]->f, f_out_dev, g0.nx, g0.ny, g0.nz, s), "volume layout");
     }
-    return prof.collect(o.kernel_ms, o.kernel_launches);
+    return prof.collect(o.kernel_ms, o.kernel_launches, o.kernel_ms_finest, o.kernel_launches_finest);
 }
 
 cbct_status cbct_restrict_sino(int n_angles, int nv, int nu, const float *y_dev, float *y_coarse_dev,

@@ -115,6 +115,12 @@ struct cbct_geometry {
     double *dtrace = nullptr;            // device energy trace
     size_t dtrace_len = 0;
     cbct::EventPool events;
+    // power iterations of the finer levels of a cascade, run on a side stream while the
+    // coarser levels iterate (they depend on the geometry alone)
+    cudaStream_t side = nullptr;
+    cudaEvent_t side_fork = nullptr;
+    cudaEvent_t side_done[13] = {};
+    double *host_lam = nullptr;          // pinned host [13]: lambda of each level
 };
 
 namespace cbct {

@@ -225,6 +225,8 @@ void cbct_server::run() {
             j.o.step_trace = nullptr;
             j.o.kernel_ms = nullptr;
             j.o.kernel_launches = nullptr;
+            j.o.kernel_ms_finest = nullptr;
+            j.o.kernel_launches_finest = nullptr;
             j.f_out = p->req.f_out_dev;
             cbct_status st = E.add(&j);
             if (st != CBCT_OK) {

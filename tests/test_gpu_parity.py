@@ -354,6 +354,28 @@ def test_reconstruct_auto_beta_matches_oracle(lib):
     assert rel(host(ft), f_ref) <= VOL_TOL
 
 
+def test_cascade_power_iterations_on_the_side_stream(lib):
+    """With the automatic beta the finer levels' power iterations run on a side stream
+    while the coarser levels iterate: the volume equals, bit for bit, the run with the
+    same betas passed in (no power iteration at all), and the betas match the oracle."""
+    case = synth.make_case("small")
+    g = case["geom"]
+    Y = dev(case["Y"])
+    for levels in (2, 3):
+        G = lib.cbct_geometry_create(g)
+        fa, ia = lib.cbct_reconstruct(G, Y, case["mu"], 4, levels, trace=True)
+        G2 = lib.cbct_geometry_create(g)
+        fb, ib = lib.cbct_reconstruct(G2, Y, case["mu"], 4, levels, betas=list(ia["betas"]), trace=True)
+        assert np.array_equal(host(fa), host(fb)) and np.array_equal(ia["trace"], ib["trace"])
+        G3 = lib.cbct_geometry_create(g)   # the power iterations in level order on one stream
+        fc, ic = lib.cbct_reconstruct(G3, Y, case["mu"], 4, levels, trace=True, serial_power=True)
+        assert np.array_equal(host(fa), host(fc)) and np.array_equal(ia["betas"], ic["betas"])
+        for l in range(levels):
+            lg = oracle.level_geom(g, l)
+            ref = max(10 * case["mu"], 1.05 * oracle.gamma(lg, case["mu"]) * oracle.power_iteration(lg, 30))
+            assert abs(ia["betas"][l] - ref) <= 1e-5 * ref, (levels, l)
+
+
 def test_medium_one_iteration_full_size(lib):
     """One Algorithm A1 iteration at the full 256x256x64 / 40x256x192 size, from an
     iterate produced by the GPU's own multigrid run (the benchmark configuration)."""
@@ -442,6 +464,10 @@ def test_kernel_timing_report(lib):
     assert n["project"] == 2 * (3 + 30) and n["backproject"] == 2 * 2 * (3 + 30)
     assert n["tv"] == 2 * 3 * 10
     assert all(ms[k] > 0 for k in ("project", "backproject", "tv"))
+    # the finest level's Algorithm A1 iterations alone: 3 projections, 3 adjoints
+    nf, msf = info["kernel_launches_finest"], info["kernel_ms_finest"]
+    assert nf["project"] == 3 and nf["backproject"] == 2 * 3 and nf["tv"] == 3 * 10
+    assert all(0 < msf[k] < ms[k] for k in ("project", "backproject", "tv"))
     # a class mask times only the chosen classes and still counts every launch
     mask = 1 << lib.KERNEL_CLASSES.index("backproject")
     _, m = lib.cbct_reconstruct(G, dev(case["Y"]), case["mu"], 3, 2, kernel_times=True, kernel_mask=mask)
