@@ -169,16 +169,16 @@ struct TvArgs {
 };
 // Forms of the TV sweep, chosen from the sizes alone (so every launch of a level, alone
 // or batched, uses the same tiles):
-//  * full column (tv_col_vz > 0): a warp owns whole z-columns of at most 64 voxels (up
-//    to 2 per lane) and walks jc rows in y; z-neighbours come by shuffle, with no halo.
-//    Used when walks of 4 rows still give 8192 warp tiles (3 voxels per lane needed up
-//    to 80 registers and was slower than the row walk).
+//  * full column (tv_col_vz > 0): a warp owns whole z-columns of at most 96 voxels (up
+//    to 3 per lane) and walks jc rows in y; z-neighbours come by shuffle, with no halo.
+//    Used when walks of 4 rows still give 8192 warp tiles (3 voxels per lane run with
+//    a 64-register cap: 15 % faster than the row walk on 96-voxel columns).
 //  * row walk (jc > 0, vz = 0): a warp owns 32 consecutive z-voxels and walks 16 rows;
 //    for taller volumes (measured on B300: 1.3-1.5x faster than one thread per voxel
 //    from 256x256x48 up).
 //  * one thread per voxel (jc = 0): smaller volumes.
 __host__ __device__ __forceinline__ int tv_col_vz(int nx, int ny, int nz) {
-    return (nz <= 64 && (long)nx * ((ny + 3) / 4) >= 8192) ? (nz + 31) / 32 : 0;
+    return (nz <= 96 && (long)nx * ((ny + 3) / 4) >= 8192) ? (nz + 31) / 32 : 0;
 }
 __host__ __device__ __forceinline__ int tv_rows_per_tile(int nx, int ny, int nz) {
     if (tv_col_vz(nx, ny, nz)) {

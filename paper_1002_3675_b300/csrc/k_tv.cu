@@ -3,8 +3,9 @@
 
 namespace cbct {
 
+// (3 voxels per lane: 64 registers, 4 blocks per SM; uncapped it took 80 and was slower)
 template <bool CLAMP, int ACC, bool ANISO, int FORM>
-__global__ void __launch_bounds__(TV_THREADS)
+__global__ void __launch_bounds__(TV_THREADS, FORM == 4 ? 4 : 1)
 k_tv_sweep(TvArgs A, const float *__restrict__ fin, const float *__restrict__ g, float *__restrict__ fout,
            double *__restrict__ partial) {
     tv_block_t<CLAMP, ACC, ANISO, FORM>(A, fin, g, fout, partial, blockIdx.x);
@@ -17,7 +18,8 @@ static void launch_form(const TvArgs &a, dim3 grid, const float *fin, const floa
         case 0: k_tv_sweep<CLAMP, ACC, ANISO, 0><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p); break;
         case 1: k_tv_sweep<CLAMP, ACC, ANISO, 1><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p); break;
         case 2: k_tv_sweep<CLAMP, ACC, ANISO, 2><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p); break;
-        default: k_tv_sweep<CLAMP, ACC, ANISO, 3><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p); break;
+        case 3: k_tv_sweep<CLAMP, ACC, ANISO, 3><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p); break;
+        default: k_tv_sweep<CLAMP, ACC, ANISO, 4><<<grid, TV_THREADS, 0, s>>>(a, fin, g, fout, p); break;
     }
     count_launch();
 }

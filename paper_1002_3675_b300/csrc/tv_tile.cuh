@@ -390,7 +390,7 @@ __device__ __forceinline__ void tv_voxels(const TvArgs &A, const float *__restri
 }
 
 // One block of the sweep (block index blk): TV_WARPS warp tiles (FORM 1: row walks;
-// FORM 2 + v: full columns with v + 1 voxels per lane, v < 2), or TV_THREADS voxels in
+// FORM 2 + v: full columns with v + 1 voxels per lane, v < 3), or TV_THREADS voxels in
 // the per-voxel form (FORM 0).  With TV_ACC_STEP, fout holds f_k on entry.
 template <bool CLAMP, int ACC, bool ANISO, int FORM>
 __device__ __forceinline__ void tv_block_t(const TvArgs &A, const float *__restrict__ fin, const float *__restrict__ g,
