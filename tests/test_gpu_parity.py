@@ -231,7 +231,7 @@ def test_tv_prox_matches_oracle(lib):
 
 
 @pytest.mark.parametrize("dims,form", [((29, 206, 160), "full columns, 1 voxel per lane"),
-                                       ((45, 206, 160), "full columns, 2 voxels per lane"),
+                                       ((45, 206, 163), "full columns, 2 voxels per lane, odd nx"),
                                        ((70, 256, 180), "full columns, 3 voxels per lane"),
                                        ((100, 256, 128), "32-voxel row walks")])
 @pytest.mark.parametrize("tv_mode", [0, 1])
