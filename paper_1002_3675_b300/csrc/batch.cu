@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "batch.h"
@@ -226,12 +227,17 @@ static bool tv_sweep_solo(int nx, int ny, int nz, long sms) {
     return (long)tv_blocks(nx, ny, nz) >= 16 * sms || tv_col_vz(nx, ny, nz) > 0;
 }
 
+// SM count of the current device, looked up once per device (atomics: the server's
+// worker threads call this concurrently).
 static int sm_count() {
-    static int n = 0;
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    int n = cache[dev].load(std::memory_order_relaxed);
     if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+        cache[dev].store(n, std::memory_order_relaxed);
     }
     return n;
 }
@@ -719,7 +725,8 @@ cbct_status Engine::build_tables() {
     return CBCT_OK;
 }
 
-static bool attr_done[64] = {};
+// per device: the attributes belong to the device's context (setting them twice is harmless)
+static std::atomic<bool> attr_done[64];
 
 // Blocks of `kernel` that stay resident on one SM with this block size and dynamic
 // shared memory (persistent grids are sized to exactly fill the GPU once).

@@ -1,6 +1,7 @@
 // Forward projection launchers (single request).  The arithmetic is in
 // project_tile.cuh.
 #include <algorithm>
+#include <atomic>
 
 #include "project_tile.cuh"
 
@@ -47,7 +48,8 @@ cudaError_t launch_project(const GeoDev &g, const float *vol, const float *y32, 
     // the segment list and one level of running sums must fit
     const int smem = proj_smem_of(g);
     if (smem > PROJ_SMEM) return cudaErrorInvalidValue;
-    static bool attr_set[64] = {};   // per device: the attribute belongs to the device's context
+    // per device: the attribute belongs to the device's context (setting it twice is harmless)
+    static std::atomic<bool> attr_set[64];
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;

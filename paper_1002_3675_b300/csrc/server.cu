@@ -17,6 +17,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -114,9 +115,17 @@ struct cbct_server {
     void finish(const std::shared_ptr<Pending> &p, cbct_status st);
 };
 
-static int g_fail_allocs = 0;  // test hook: make the next n slot set-ups fail as if out of memory
+static std::atomic<int> g_fail_allocs{0};  // test hook: make the next n slot set-ups fail as if out of memory
 
 extern "C" void cbct_debug_fail_next_allocations(int n) { g_fail_allocs = n; }
+
+// Takes one injected failure if any is pending (workers may race for the last one).
+static bool take_injected_failure() {
+    int n = g_fail_allocs.load();
+    while (n > 0 && !g_fail_allocs.compare_exchange_weak(n, n - 1)) {
+    }
+    return n > 0;
+}
 
 void cbct_server::finish(const std::shared_ptr<Pending> &p, cbct_status st) {
     p->result.status = st;
@@ -170,8 +179,7 @@ bool cbct_server::try_admit(const std::shared_ptr<Pending> &p, std::unique_lock<
     lk.unlock();
     cbct_geometry *G = nullptr;
     cbct_status st;
-    if (g_fail_allocs > 0) {
-        --g_fail_allocs;
+    if (take_injected_failure()) {
         set_error("injected allocation failure");
         st = CBCT_ERR_OOM;
     } else {
