@@ -274,6 +274,9 @@ typedef struct {
     int proj_levels;   /* z-levels per projector launch, 1..nz: a projection of a volume
                           larger than the L2 cache runs as consecutive launches over
                           slabs of levels, each ray's sum carried between them        */
+    int bp_layout;     /* adjoint lane layout: 1 consecutive voxels per lane, 2 interleaved
+                          (0: interleaved when a warp's gathers would span 400 or more
+                          detector rows)                                              */
 } cbct_tuning;
 /* Time the candidate launch shapes of level `level` with CUDA events on `stream`
  * (synchronises), keep the fastest in the geometry and report it in *out. */

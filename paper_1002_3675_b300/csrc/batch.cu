@@ -91,8 +91,9 @@ k_bp_batch(const BpItem *__restrict__ items, const long *__restrict__ start, int
             first = __ldg(start + r);
             next = r + 1 < n ? __ldg(start + r + 1) : total;
         }
-        bp_warp<VPL>(it[w].G, it[w].mode, it[w].rs, it[w].fin, it[w].out, it[w].c, t - first,
-                     rec + w * BP_REC_PER_WARP);
+        // consecutive layout for every item (the interleaved one gives the same bits)
+        bp_warp<VPL, false>(it[w].G, it[w].mode, it[w].rs, it[w].fin, it[w].out, it[w].c, t - first,
+                            rec + w * BP_REC_PER_WARP);
     }
 }
 
@@ -1061,25 +1062,28 @@ extern "C" cbct_status cbct_autotune(cbct_geometry *G, int level, cbct_tuning *o
     }
     g.proj_threads = best_t;
     g.proj_smem = best_m;
-    // adjoint voxels per lane and block size
-    int best_v = 0, best_b = 0;
+    // adjoint voxels per lane, block size and lane layout
+    int best_v = 0, best_b = 0, best_l = 0;
     float best_q = 1e30f;
     const int vmax = std::min(4, (g.nz + 31) / 32);
     for (int v = 1; v <= vmax; ++v)
-        for (int T : {64, 128, 256}) {
-            g.bp_vpl = v;
-            g.bp_threads = T;
-            launch_backproject(g, L->rs, nullptr, L->B, 0.f, BP_PLAIN, s);
-            cudaEventRecord(e0, s);
-            for (int q = 0; q < reps; ++q) launch_backproject(g, L->rs, nullptr, L->B, 0.f, BP_PLAIN, s);
-            cudaEventRecord(e1, s);
-            const float ms = time_ms(s, e0, e1) / reps;
-            if (ms < best_q) {
-                best_q = ms;
-                best_v = v;
-                best_b = T;
+        for (int T : {64, 128, 256})
+            for (int lay : {1, 2}) {
+                g.bp_vpl = v;
+                g.bp_threads = T;
+                g.bp_layout = lay;
+                launch_backproject(g, L->rs, nullptr, L->B, 0.f, BP_PLAIN, s);
+                cudaEventRecord(e0, s);
+                for (int q = 0; q < reps; ++q) launch_backproject(g, L->rs, nullptr, L->B, 0.f, BP_PLAIN, s);
+                cudaEventRecord(e1, s);
+                const float ms = time_ms(s, e0, e1) / reps;
+                if (ms < best_q) {
+                    best_q = ms;
+                    best_v = v;
+                    best_b = T;
+                    best_l = lay;
+                }
             }
-        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ECK(cudaGetLastError(), "autotune");
@@ -1087,11 +1091,13 @@ extern "C" cbct_status cbct_autotune(cbct_geometry *G, int level, cbct_tuning *o
     L->gd.proj_smem = best_m;
     L->gd.bp_vpl = best_v;
     L->gd.bp_threads = best_b;
+    L->gd.bp_layout = best_l;
     out->proj_threads = best_t;
     out->proj_smem = best_m;
     out->proj_levels = L->gd.proj_levels;
     out->bp_vpl = best_v;
     out->bp_threads = best_b;
+    out->bp_layout = best_l;
     out->proj_ms = best_p;
     out->bp_ms = best_q;
     return CBCT_OK;
@@ -1108,7 +1114,7 @@ extern "C" cbct_status cbct_set_tuning(cbct_geometry *G, int level, const cbct_t
     if ((t->proj_threads && (t->proj_threads < need || t->proj_threads > PROJ_MAX_THREADS || t->proj_threads % 32)) ||
         t->bp_vpl < 0 || t->bp_vpl > 4 ||
         (t->bp_threads && t->bp_threads != 64 && t->bp_threads != 128 && t->bp_threads != 256) ||
-        t->proj_levels < 0 || t->proj_levels > L->gd.nz) {
+        t->proj_levels < 0 || t->proj_levels > L->gd.nz || t->bp_layout < 0 || t->bp_layout > 2) {
         set_error("tuning values out of range");
         return CBCT_ERR_INVALID_ARG;
     }
@@ -1125,5 +1131,6 @@ extern "C" cbct_status cbct_set_tuning(cbct_geometry *G, int level, const cbct_t
     L->gd.proj_levels = t->proj_levels;
     L->gd.bp_vpl = t->bp_vpl;
     L->gd.bp_threads = t->bp_threads;
+    L->gd.bp_layout = t->bp_layout;
     return CBCT_OK;
 }

@@ -10,7 +10,11 @@
 // g = f - c P^T r with c = gamma / beta.
 //
 // Work decomposition.  One warp owns 32*VPL voxels of one z-column (i, j); lane l
-// holds the consecutive voxels k = base + VPL l + v, v < VPL.  The (view, detector
+// holds VPL of them, in one of two layouts (IL, bitwise the same results):
+// consecutive, k = base + VPL l + v, or interleaved, k = base + l + 32 v, v < VPL, where
+// each gather of a detector column's running sums spans the rows of 32 planes instead
+// of 32 VPL (fewer cache lines when a voxel covers several detector rows, for a few
+// more shuffles).  The (view, detector
 // column) pairs whose ray plane meets the xy-cell come from a precomputed per-cell
 // table; for each, the part of the rays' horizontal parameter t inside the cell,
 // [tlo, thi], is the same for the whole z-column.
@@ -25,8 +29,8 @@
 // with N(z) the rows below both ends and P(z) the partial rows' sum.  The sum over
 // full rows is a difference of running sums along the detector column (double-float
 // sums stored as a float32 pair, so the difference keeps float32 accuracy).  Each lane
-// evaluates the planes below its voxels and takes the plane above its last voxel from
-// its neighbour.
+// evaluates the planes below its voxels and takes the plane above from its own next
+// voxel or from the next lane (the chunk's top plane for the last voxel).
 // The residual is pre-scaled by sec(phi) (3D length = t-length * sec(phi)).  Sums are
 // taken in a fixed order with no atomics, so results are deterministic.
 #include "cbct_internal.h"
@@ -64,10 +68,11 @@ __host__ __device__ __forceinline__ long bp_warp_tiles(const GeoDev &G) {
     return (long)G.nx * G.ny * ((G.nz + 32 * VPL - 1) / (32 * VPL));
 }
 
-// One warp tile (warp-uniform): z-chunk kc of xy-cell colid.  Lane l holds the VPL
-// consecutive voxels base + VPL l + v and evaluates the planes below them; the plane
-// above its last voxel is the next lane's first plane (the chunk's top plane for lane
-// 31).  mode: BP_PLAIN writes P^T rs, BP_STEP writes fin - c P^T rs.  Shared by the
+// One warp tile (warp-uniform): z-chunk kc of xy-cell colid.  Lane l holds VPL voxels
+// and evaluates the planes below them.  Consecutive layout: the plane above its last
+// voxel is the next lane's first plane (the chunk's top plane for lane 31).
+// Interleaved: the plane above voxel base + l + 32 v is the next lane's plane of the
+// same slot (for lane 31, lane 0's plane of the next slot, or the chunk's top plane).  mode: BP_PLAIN writes P^T rs, BP_STEP writes fin - c P^T rs.  Shared by the
 // single-request and batched kernels, so a request's result does not depend on what
 // else is in the launch.
 //
@@ -78,7 +83,7 @@ __host__ __device__ __forceinline__ long bp_warp_tiles(const GeoDev &G) {
 // a broadcast.  The sums are taken in the same order as a pair-by-pair walk.
 constexpr int BP_REC_PER_WARP = 64;  // float4 records of one warp
 
-template <int VPL>
+template <int VPL, bool IL>
 __device__ __forceinline__ void bp_warp(const GeoDev &G, const int mode, const float *__restrict__ rs,
                                          const float *__restrict__ fin, float *__restrict__ out, const float c,
                                          const long wtile, float4 *__restrict__ rec) {
@@ -89,7 +94,8 @@ __device__ __forceinline__ void bp_warp(const GeoDev &G, const int mode, const f
     const long colid = wtile / nkc;
     const int j = (int)(colid % G.ny);
     const int i = (int)(colid / G.ny);
-    const int base = kc * 32 * VPL + lane * VPL;     // first voxel of this lane
+    const int base = kc * 32 * VPL + (IL ? lane : lane * VPL);  // voxel v: base + (IL ? 32 v : v)
+    constexpr int VS = IL ? 32 : 1;
     float acc[VPL];
 #pragma unroll
     for (int v = 0; v < VPL; ++v) acc[v] = 0.f;
@@ -151,27 +157,57 @@ __device__ __forceinline__ void bp_warp(const GeoDev &G, const int mode, const f
             float pbv[VPL + 1];
 #pragma unroll
             for (int v = 0; v < VPL; ++v)
-                eval_plane(plane_at(base + v, G.hz, G.z0), q1, q2, G.cv, G.nv, tlo, thi, rzp, rsp, nb[v], pbv[v]);
-            nb[VPL] = __shfl_down_sync(FULL, nb[0], 1);
-            pbv[VPL] = __shfl_down_sync(FULL, pbv[0], 1);
-            if (lane == 31) {
-                nb[VPL] = __float_as_int(r1.z);
-                pbv[VPL] = r1.w;
-            }
-            float2 c0 = __ldg(cum + nb[0]);
+                eval_plane(plane_at(base + VS * v, G.hz, G.z0), q1, q2, G.cv, G.nv, tlo, thi, rzp, rsp, nb[v],
+                           pbv[v]);
+            if constexpr (!IL) {
+                nb[VPL] = __shfl_down_sync(FULL, nb[0], 1);
+                pbv[VPL] = __shfl_down_sync(FULL, pbv[0], 1);
+                if (lane == 31) {
+                    nb[VPL] = __float_as_int(r1.z);
+                    pbv[VPL] = r1.w;
+                }
+                float2 c0 = __ldg(cum + nb[0]);
 #pragma unroll
-            for (int v = 0; v < VPL; ++v) {
-                const float2 c1 = __ldg(cum + nb[v + 1]);
-                const float full = __fadd_rn(__fsub_rn(c1.x, c0.x), __fsub_rn(c1.y, c0.y));
-                acc[v] += __fmaf_rn(w, full, pbv[v + 1] - pbv[v]);
-                c0 = c1;
+                for (int v = 0; v < VPL; ++v) {
+                    const float2 c1 = __ldg(cum + nb[v + 1]);
+                    const float full = __fadd_rn(__fsub_rn(c1.x, c0.x), __fsub_rn(c1.y, c0.y));
+                    acc[v] += __fmaf_rn(w, full, pbv[v + 1] - pbv[v]);
+                    c0 = c1;
+                }
+            } else {
+                float2 cb[VPL];
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) cb[v] = __ldg(cum + nb[v]);
+                float2 ctop = make_float2(0.f, 0.f);  // lane 31: the chunk's top plane
+                if (lane == 31) ctop = __ldg(cum + __float_as_int(r1.z));
+                // the plane above each voxel: the next lane's plane of the same slot
+                const int nxt = (lane + 1) & 31;
+                float pu[VPL];
+                float2 cu[VPL];
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) {
+                    pu[v] = __shfl_sync(FULL, pbv[v], nxt);
+                    cu[v].x = __shfl_sync(FULL, cb[v].x, nxt);
+                    cu[v].y = __shfl_sync(FULL, cb[v].y, nxt);
+                }
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) {
+                    float p1 = pu[v];
+                    float2 c1 = cu[v];
+                    if (lane == 31) {  // lane 0's next slot, or the chunk's top plane
+                        p1 = v + 1 < VPL ? pu[v + 1 < VPL ? v + 1 : v] : r1.w;
+                        c1 = v + 1 < VPL ? cu[v + 1 < VPL ? v + 1 : v] : ctop;
+                    }
+                    const float full = __fadd_rn(__fsub_rn(c1.x, cb[v].x), __fsub_rn(c1.y, cb[v].y));
+                    acc[v] += __fmaf_rn(w, full, p1 - pbv[v]);
+                }
             }
         }
         __syncwarp();  // the next chunk's setup overwrites the records
     }
 #pragma unroll
     for (int v = 0; v < VPL; ++v) {
-        const int k = base + v;
+        const int k = base + VS * v;
         if (k >= G.nz) continue;
         const size_t o = ((size_t)i * G.ny + j) * G.nz + k;
         out[o] = (mode == BP_PLAIN) ? acc[v] : __fmaf_rn(-c, acc[v], __ldg(fin + o));

@@ -61,6 +61,8 @@ struct GeoDev {
     int proj_levels;             // z-levels per projector launch (0 = default; see project_levels_per_launch)
     int bp_vpl;                  // adjoint voxels per lane (1..4)
     int bp_threads;              // adjoint block size (64, 128 or 256)
+    int bp_layout;               // adjoint lane layout: 0 by gather span (bp_interleaved), 1 consecutive
+                                 // voxels per lane, 2 interleaved
 };
 
 __host__ __device__ __forceinline__ size_t vol_elems(const GeoDev &g) { return (size_t)g.nx * g.ny * g.nz; }
@@ -158,6 +160,8 @@ cudaError_t launch_backproject_eq2(const GeoDev &g, const float *r, const float 
                                    int mode, cudaStream_t s);
 double eq2_scale(const Level *L);  // dV / (du dv)
 int bp_default_vpl(const GeoDev &g);
+// Whether the adjoint's lanes hold interleaved voxels (bp_tile.cuh) with vpl voxels per lane.
+bool bp_interleaved(const GeoDev &g, int vpl);
 
 struct TvArgs {
     int nx, ny, nz;          // internal layout [nx][ny][nz]

@@ -115,6 +115,7 @@ def test_autotune_keeps_results_and_caches(lib, tmp_path):
     assert len(shapes) == c["levels"] and os.path.exists(path)
     for s in shapes.values():
         assert s["proj_threads"] % 32 == 0 and 1 <= s["bp_vpl"] <= 4 and s["bp_threads"] in (64, 128, 256)
+        assert s["bp_layout"] in (1, 2)
     f1, i1 = lib.cbct_reconstruct(G, dev(c["Y"]), c["mu"], c["iters"], c["levels"], trace=True)
     assert np.array_equal(f0, host(f1)) and np.array_equal(i0["trace"], i1["trace"])
     # a second geometry of the same size class takes the cached shapes without timing
