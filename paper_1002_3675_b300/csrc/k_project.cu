@@ -19,13 +19,15 @@ k_project(GeoDev G, const float *__restrict__ vol, const float *__restrict__ y32
 
 // Levels per launch: G.proj_levels if set, else the whole volume in one launch while it fits comfortably in the
 // 126 MB L2 next to the projection data; otherwise slabs of whole 32-level groups of at
-// most 32 MB, so that the blocks of one launch (every view and column) find their slab
-// in L2 instead of re-reading the volume from HBM for every view.
+// most 64 MB, so that the blocks of one launch (every view and column) find their slab
+// in L2 instead of re-reading the volume from HBM for every view.  Timed on B300 for
+// 512x512x96 (1 MB per level): 64 + 32 levels 2.63 ms per projection, 3 x 32 levels
+// 2.79 ms, one launch 2.89 ms, 2 x 48 levels 3.04 ms.
 int project_levels_per_launch(const GeoDev &g) {
     if (g.proj_levels >= 1 && g.proj_levels <= g.nz) return g.proj_levels;
     const size_t level_bytes = (size_t)g.nx * g.ny * sizeof(float);
     if (level_bytes * g.nz <= (size_t)48 << 20) return g.nz;
-    int r = (int)(((size_t)32 << 20) / level_bytes);
+    int r = (int)(((size_t)64 << 20) / level_bytes);
     if (r >= 32) r &= ~31;
     return std::max(1, std::min(r, g.nz));
 }
