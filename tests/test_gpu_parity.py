@@ -189,6 +189,8 @@ def test_backproject_lane_layouts_agree_bitwise(lib):
                     first = bt
                     assert rel(bt, ref) <= P_TOL, rel(bt, ref)
                 assert np.array_equal(bt, first), (g["nz"], vpl, layout)
+        with pytest.raises(lib.CbctError):
+            lib.cbct_set_tuning(G, 0, {"bp_layout": 3})
 
 
 def test_backproject_medium_full_size(lib):
