@@ -137,8 +137,10 @@ using namespace proj_detail;
 constexpr int PROJ_SMEM = 110 * 1024;   // largest size used
 constexpr int PROJ_SMEM_MIN = 16 * 1024;
 constexpr int PROJ_MAX_THREADS = 512;
-constexpr int CHUNK_LOG = 6;            // prefix chunks of 64 segments
-constexpr int CHUNK = 1 << CHUNK_LOG;
+// prefix chunks of 48 segments: a whole number of 8-load batches, and about one chunk per
+// warp for the 250-730 segments of a column at 256 to 512 threads (timed on B300 against
+// 16, 32, 40 and 64: 64 was 1.6 % slower on 512x512x96, the others slower still)
+constexpr int CHUNK = 48;
 constexpr int PROJ_BATCH = 8;           // voxel loads in flight per thread
 
 // Projector block size (rows per tile): G.proj_threads if valid, else the default: one
@@ -192,9 +194,9 @@ __device__ __forceinline__ SegPos seg_pos(const float *seg_t, int S, float tin, 
 // coff[chunk][kk] adds the totals of the preceding chunks.  C is piecewise linear in t
 // between segment ends.
 __device__ __forceinline__ float eval_c(const float *C, const float *coff, int nk, int kk, const SegPos p) {
-    const int ch = p.s >> CHUNK_LOG;
+    const int ch = p.s / CHUNK;
     const float base = coff[ch * nk + kk];
-    const bool first = (p.s & (CHUNK - 1)) == 0;   // previous value is the chunk's base
+    const bool first = p.s == ch * CHUNK;   // previous value is the chunk's base
     const float cp = first ? base : base + C[(p.s - 1) * nk + kk];
     const float cs = base + C[p.s * nk + kk];
     return __fmaf_rn(p.frac, cs - cp, cp);
@@ -218,7 +220,7 @@ __device__ __forceinline__ void project_tile(const GeoDev &G, const int mode, co
                                              const bool carry_out = false) {
     if (kr1 < 0) kr1 = G.nz;
     const int slots = G.nx + G.ny + 1;
-    const int max_chunks = (slots + CHUNK - 1) >> CHUNK_LOG;
+    const int max_chunks = (slots + CHUNK - 1) / CHUNK;
     float *seg_t = smem;                          // exit t of each segment
     int *seg_off = (int *)(smem + slots);         // z-column offset of each segment's cell
     float *coff = smem + 2 * slots;               // [chunk][level - band start]
@@ -278,10 +280,10 @@ __device__ __forceinline__ void project_tile(const GeoDev &G, const int mode, co
     for (int kb = kr0; kb < kr1 && S > 0; kb += kband) {
         const int nk = min(kband, kr1 - kb);
         float *C = coff + max_chunks * nk;        // [s][kk], chunk-local running sums
-        // 2. warps over (32-level group, 64-segment chunk) pairs; lanes over levels, so
+        // 2. warps over (32-level group, 48-segment chunk) pairs; lanes over levels, so
         //    each load is a contiguous piece of a z-column
         const int nkg = (nk + 31) >> 5;
-        const int nch = (S + CHUNK - 1) >> CHUNK_LOG;
+        const int nch = (S + CHUNK - 1) / CHUNK;
         for (int w = warp; w < nkg * nch; w += nwarp) {
             const int kk = (w % nkg) * 32 + lane, ch = w / nkg;
             if (kk >= nk) continue;
