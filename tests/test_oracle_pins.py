@@ -592,6 +592,60 @@ def test_two_level_cascade_runs_and_descends():
     assert (lg["nx"], lg["nu"], lg["nv"], lg["hx"], lg["du"]) == (32, 32, 24, 8.0, 16.0)
 
 
+def _cascade_by_hand(g, Y, mu, iters, levels, betas, M, start_zero=False, wrong_data=False):
+    """The coarse-to-fine cascade (multigrid sentence after Eq. 2) composed from its
+    separately pinned parts: 2x2 binning of the data per level, Algorithm A1 on each
+    level, trilinear prolongation to the next finer level, starting from 0 on the
+    coarsest.  start_zero / wrong_data plant the two wiring mistakes the cascade must
+    not make (a finer level restarted from 0, a coarse level fed decimated instead of
+    binned data)."""
+    Ys = [np.asarray(Y, dtype=np.float64)]
+    for _ in range(1, levels):
+        Ys.append(oracle.restrict_sino(Ys[-1]))
+    lg = [oracle.level_geom(g, l) for l in range(levels)]
+    f, traces = None, []
+    for l in range(levels - 1, -1, -1):
+        shape = oracle.vol_shape(lg[l])
+        f0 = np.zeros(shape) if (f is None or start_zero) else oracle.prolong_vol(f, shape)
+        # a plausible wiring slip: decimating the finer data instead of binning it
+        data = Ys[l - 1][:, ::2, ::2].copy() if (wrong_data and l > 0) else Ys[l]
+        eps = oracle.default_eps(lg[l])
+        f, tr = oracle.fbs(lg[l], data, mu, betas[l], eps, M, iters, f0=f0)
+        traces.append((l, f0, tr))
+    return f, traces
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_cascade_wiring_matches_composed_parts(levels):
+    """or_reconstruct is bitwise the composition of restriction, A1 and prolongation in
+    the cascade's order; a finer level restarted from 0, or a level fed the wrong data,
+    gives another volume; the finer level's first trace energy is the energy of the
+    prolonged coarse result."""
+    case = synth.make_case("small")
+    g, Y, mu = case["geom"], case["Y"], case["mu"]
+    iters, M = 3, 4
+    betas = [1.05 * oracle.gamma(oracle.level_geom(g, l), mu) * 1.3e4 / 4 ** l for l in range(levels)]
+    f_rec, tr_rec = oracle.reconstruct(g, Y, mu, iters, levels, betas=betas, M=M)
+    f_hand, traces = _cascade_by_hand(g, Y, mu, iters, levels, betas, M)
+    assert np.array_equal(f_rec, f_hand)
+    # trace entries, coarsest level first in or_reconstruct
+    for q, (l, f0, tr) in enumerate(traces):
+        np.testing.assert_allclose(tr_rec[q], tr, rtol=1e-12, atol=0)
+        if l < levels - 1:
+            lgl = oracle.level_geom(g, l)
+            Yl = np.asarray(Y, dtype=np.float64)
+            for _ in range(l):
+                Yl = oracle.restrict_sino(Yl)
+            E0 = oracle.energy(lgl, Yl, f0, mu, oracle.default_eps(lgl))
+            assert abs(tr_rec[q][0, 0] - E0[0]) <= 1e-12 * abs(E0[0])
+            assert np.abs(f0).max() > 0    # the finer level starts from the coarse result
+    f_zero, _ = _cascade_by_hand(g, Y, mu, iters, levels, betas, M, start_zero=True)
+    f_data, _ = _cascade_by_hand(g, Y, mu, iters, levels, betas, M, wrong_data=True)
+    scale = np.linalg.norm(f_rec)
+    assert np.linalg.norm(f_zero - f_rec) > 1e-6 * scale
+    assert np.linalg.norm(f_data - f_rec) > 1e-6 * scale
+
+
 # ---------------------------------------------------------------------------------
 # Synthetic data (inputs only)
 # ---------------------------------------------------------------------------------
