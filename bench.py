@@ -1,33 +1,42 @@
 """Benchmark: FBS iterations/s of the full multigrid reconstruction on one B300.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload medium]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload large]
     python -m torch.distributed.run --nproc-per-node N ... bench.py --gpus N
 
 A step is one complete ``cbct_reconstruct`` call (Algorithm A1 on every multigrid
 level: forward projection + residual, adjoint gather + gradient step, M TV-prox
 sweeps with f >= 0, float64 energies; the automatic beta's power iterations; the
 2x2 data binning and the prolongations) on seeded synthetic data of the workload's
-shape.  Inputs are resident in HBM when the timed region starts; L2 is flushed
-(256 MiB write) between steps, outside the timed events.  Each GPU runs independent
-reconstructions (no data-path collective; weak scaling).
+shape.  The default workload is the large one: 512x512x96 voxels, 40 views of
+512x384, 3 levels x 50 iterations.  Inputs are resident in HBM when the timed region
+starts; L2 is flushed (256 MiB write) between steps, outside the timed events.  The
+timed steps carry no per-launch events (one event pair per step and per level); the
+per-kernel split and the roofline come from a separate pass of the same steps.  Each
+GPU runs independent reconstructions (no data-path collective; weak scaling).
 
-Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead, on
-the host cores, one Algorithm A1 iteration of the finest level per step.
+Prints one JSON line.  Besides ``value`` (FBS iterations of every level per second of
+whole reconstructions) it carries ``recon_s`` and ``finest_fbs_iter_s`` (the finest
+level's iterations alone), and at N = 1 a ``serve`` block: 200 seeded Poisson arrivals
+over the medium workload and the large one at 20, 30 and 40 views, served by the
+continuous-batching server at 0.5, 0.8 and 1.0 x the one-at-a-time capacity, with
+p50/p99 latency against a one-at-a-time FIFO queue fed the same arrivals.
 
-Two serving modes print their own line (reconstructions/s):
+``--impl reference`` times the FP64 CPU oracle on the host cores in the same unit: FBS
+iterations per second with every level weighted as in a reconstruction (levels /
+the sum over levels of one iteration's time), each step one iteration of one level,
+the steps cycling through the levels.
+
+Other modes print their own line:
 
 * ``--mode batch``: 16 heterogeneous requests (six volume sizes from 128^3 to
   384x384x64, 20-60 views, random start angles, 2 levels x 30 iterations), run one at
   a time through ``cbct_reconstruct`` and together through ``cbct_reconstruct_batch``;
   ``--batch-mix small --requests 32`` takes 32 requests of the small workload instead.
-* ``--mode serve``: requests (by default drawn uniformly from the medium workload and
-  the large one at 20, 30 and 40 views; ``--mix batch16`` takes the 16 requests above)
-  arrive as a Poisson stream at a fixed fraction of the one-at-a-time capacity and go
-  through the continuous-batching server with a 150 GB budget; latency percentiles are
-  compared with a one-at-a-time FIFO queue fed the same arrival times and the
-  measured per-request service times.
+* ``--mode serve``: the serving block alone (``--serve-loads``, ``--serve-requests``,
+  ``--mix batch16`` for the 16 requests above, ``--mix small`` for small scans).
 * ``--mode vcycle``: V-cycles (mg_cycle 1) against the cascade on the workload: time
   per reconstruction and the energy of Eq. 1 each reaches.
+* ``--mode kernels``: a profiler target (finest-level iterations with a fixed beta).
 """
 from __future__ import annotations
 
@@ -61,10 +70,16 @@ WORKLOAD_TEXT = {
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-# Lane-operations per nonzero that no implementation of the exact-length operators can
-# avoid: adjoint 8 (two z-crossings: 2 sub + 2 mul, clip:
-# 1 max + 1 min, length: 1 sub, accumulate: 1 fma); projector 4 (pick next crossing:
-# 1 min, length: 1 sub, accumulate: 1 fma, advance the crossing: 1 fma).
+# Normalised rate of the projector and the adjoint: lane-operations per nonzero of the
+# system matrix.  The primary basis is a flat 5 per nonzero for both operators (a
+# Siddon step: next crossing, length, accumulate, advance; the floor the scope table
+# of the measurement plan states).  The secondary basis counts what an exact-length
+# gather needs per nonzero: adjoint 8 (two z-crossings: 2 sub + 2 mul, clip: 1 max +
+# 1 min, length: 1 sub, accumulate: 1 fma), projector 4 (next crossing: 1 min,
+# length: 1 sub, accumulate: 1 fma, advance: 1 fma).  Neither kernel does per-nonzero
+# work (running slice integrals, a plane sweep over running sums), so both are
+# normalised rates, not floors of these kernels.
+OPS_PER_NNZ_SURVEY = 5.0
 OPS_PER_NNZ = {"backproject": 8.0, "project": 4.0}
 # Sources of each timed kernel; the DRAM traffic recorded in profiles/ counts only while
 # they are unchanged since the capture.
@@ -75,9 +90,10 @@ KERNEL_SOURCES = {
 }
 
 
-def profile_traffic(kernel, workload):
-    """DRAM bytes per launch from the committed ncu summary, or None when there is no
-    summary for this workload or the kernel's sources changed since it was taken."""
+def profile_fields(kernel, workload):
+    """Figures of the committed ncu summary of a kernel on a workload (DRAM and L2 bytes
+    per operation, issue activity), or {} when there is no summary or the kernel's
+    sources changed since it was taken."""
     import hashlib
     import re
     name, files = KERNEL_SOURCES[kernel]
@@ -88,12 +104,21 @@ def profile_traffic(kernel, workload):
             with open(os.path.join(ROOT, "paper_1002_3675_b300", "csrc", f), "rb") as fh:
                 h.update(fh.read())
     except OSError:
-        return None
-    t = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
+        return {}
     s = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
-    if not t or not s or s.group(1) != h.hexdigest()[:16]:
-        return None
-    return int(t.group(1))
+    if not s or s.group(1) != h.hexdigest()[:16]:
+        return {}
+    out = {}
+    for key, conv in (("traffic_bytes_per_launch", int), ("l2_bytes_per_launch", int),
+                      ("issue_active_pct", float)):
+        m = re.search(key + r":\s*([0-9.]+)", text)
+        if m:
+            out[key] = conv(m.group(1))
+    return out
+
+
+def profile_traffic(kernel, workload):
+    return profile_fields(kernel, workload).get("traffic_bytes_per_launch")
 
 
 def load_nnz(workload):
@@ -190,42 +215,86 @@ def cpu_model():
     return None
 
 
-def cpu_oracle_iterations(case, n_iter):
-    """Time n_iter Algorithm A1 iterations of the oracle on the finest level."""
+def _oracle_levels(case, levels):
+    """Per-level oracle inputs of the cascade: level geometry, 2x2-binned data and a
+    fixed beta of the right size (beta does not change the work of an iteration)."""
     import oracle
     g = case["geom"]
-    mu = case["mu"]
-    eps = oracle.default_eps(g)
-    beta = 1.05 * oracle.gamma(g, mu) * 1.6e4  # fixed value of the right size; not timed work
-    Y = np.asarray(case["Y"], dtype=np.float64)
+    Ys = [np.asarray(case["Y"], dtype=np.float64)]
+    for _ in range(1, levels):
+        Ys.append(oracle.restrict_sino(Ys[-1]))
+    out = []
+    for l in range(levels):
+        lg = oracle.level_geom(g, l)
+        out.append(dict(geom=lg, Y=Ys[l], beta=1.05 * oracle.gamma(lg, case["mu"]) * 1.6e4 / 4 ** l,
+                        eps=oracle.default_eps(lg)))
+    return out
+
+
+def oracle_iteration_s(case, lvl):
+    """Seconds of one Algorithm A1 iteration of the oracle (P, P^T, 10 prox sweeps) on
+    one level, from f = 0."""
+    import oracle
+    g = lvl["geom"]
     f0 = np.zeros((g["nz"], g["ny"], g["nx"]))
     t0 = time.perf_counter()
-    oracle.fbs(g, Y, mu, beta, eps, 10, n_iter, f0=f0)
-    return time.perf_counter() - t0, oracle.num_threads()
+    oracle.fbs(g, lvl["Y"], case["mu"], lvl["beta"], lvl["eps"], 10, 1, f0=f0)
+    return time.perf_counter() - t0
+
+
+def oracle_level_rate(case, levels, steps, warmup):
+    """The oracle's FBS iterations/s with every level weighted as in a reconstruction
+    (the same number of iterations per level): levels / sum_l t_l, t_l the mean time of
+    one iteration on level l.  Step q runs one iteration on level q mod levels (at
+    least one step per level); the warm-up steps run on the coarsest level."""
+    import oracle
+    lv = _oracle_levels(case, levels)
+    for _ in range(warmup):
+        oracle_iteration_s(case, lv[-1])
+    per = [[] for _ in range(levels)]
+    n = max(steps, levels)
+    for q in range(n):
+        per[q % levels].append(oracle_iteration_s(case, lv[q % levels]))
+    t_l = [statistics.mean(x) for x in per]
+    return {"value": levels / sum(t_l), "level_s": t_l, "steps": n, "total_s": sum(map(sum, per)),
+            "cores": oracle.num_threads()}
+
+
+def config_of(args, cfg, world):
+    """The `config` object of the line, the same in both arms (what each arm did beyond
+    it goes to the line's `run` object)."""
+    return {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "inner_iters": 10,
+            "parallelism": f"replicas x{world}",
+            "variant": {"tv_mode": ["isotropic", "anisotropic"][args.tv_mode],
+                        "adjoint": ["exact transpose", "Eq. 2 interpolation"][args.adjoint_mode],
+                        "data_storage": "float16" if args.sino_fp16 else "float32"},
+            "fbs_iterations_per_step": cfg["levels"] * cfg["iters"],
+            "unit_note": "FBS iterations per second with every multigrid level weighted as in one "
+                         "reconstruction (the same number of iterations on each level)"}
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return
+    cfg = synth.CONFIGS[args.workload]
     case = synth.make_case(args.workload)
-    for _ in range(args.warmup):
-        cpu_oracle_iterations(case, 1)
-    times = []
-    for _ in range(args.steps):
-        dt, cores = cpu_oracle_iterations(case, 1)
-        times.append(dt)
-    tot = sum(times)
-    value = args.steps / tot
-    sample = (f"1 Algorithm A1 iteration (P, P^T, 10 prox sweeps) of the finest level per step "
-              f"({WORKLOAD_TEXT[args.workload].split(',')[0]}), {args.steps} steps")
-    line = {"impl": "reference", "metric": "FBS iterations/s", "value": value, "unit": "iter/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+    r = oracle_level_rate(case, cfg["levels"], args.steps, args.warmup)
+    sample = (f"{r['steps']} steps, each one Algorithm A1 iteration (P, P^T, 10 prox sweeps, from f = 0, fixed "
+              f"beta) on one level of the {cfg['levels']}-level cascade in turn; value = levels / sum of the "
+              f"per-level mean times ({', '.join(f'{t:.3f}' for t in r['level_s'])} s, finest first); "
+              f"warm-up on the coarsest level")
+    config = config_of(args, cfg, world)
+    run = {"beta": "fixed per level (no power iteration)", "host_cores": os.cpu_count(),
+           "ranks": "the FP64 oracle on the host cores (rank 0 only); n_gpus is the launch's rank count"}
+    line = {"impl": "reference", "metric": "FBS iterations/s", "value": r["value"], "unit": "iter/s",
+            "n_gpus": world, "steps": r["steps"], "warmup": args.warmup, "ms_per_step": 1e3 * r["total_s"] / r["steps"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded ellipsoid phantom, analytic line integrals, Poisson/log noise)",
-            "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "host_cores": os.cpu_count(),
-                       "note": "the FP64 oracle on the host cores (rank 0 only); n_gpus is the launch's rank count"},
-            "cpu_baseline": {"value": value, "unit": "iter/s", "cores": cores, "cpu_model": cpu_model(), "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": config, "run": run,
+            "finest_fbs_iter_s": 1.0 / r["level_s"][0],
+            "cpu_baseline": {"value": r["value"], "unit": "iter/s", "cores": r["cores"], "cpu_model": cpu_model(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": r["value"], "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -245,50 +314,50 @@ def run_gpu(args, world, rank, local):
     f = torch.empty((cfg["vol"][2], cfg["vol"][1], cfg["vol"][0]), dtype=torch.float32, device=dev)
     f_host = torch.empty(f.shape, dtype=torch.float32).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
+    # a stream of its own: the library replays each level's iteration as a CUDA graph
+    # (graphs need a stream other than the legacy default one)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        res = _gpu_steps(args, cbct, G, Y, Y_host, f, f_host, flush, stream, levels, iters, mu, world,
+                         local if rank == 0 else None)
+    if rank != 0:
+        return
+    _gpu_line(args, cbct, torch, dev, G, case, cfg, Y, Y_host, f, f_host, res, world)
 
-    # the timed steps time the two operator classes launch by launch (CUDA events on the
-    # launching stream); every class is timed in a separate pass after the timed region
-    timed_mask = (1 << cbct.KERNEL_CLASSES.index("project")) | (1 << cbct.KERNEL_CLASSES.index("backproject"))
 
-    def step(kernel_times, mask=timed_mask, serial_power=False):
-        return cbct.cbct_reconstruct(G, Y, mu, iters, levels, f_out=f, kernel_times=kernel_times, kernel_mask=mask,
-                                     tv_mode=args.tv_mode, adjoint_mode=args.adjoint_mode, sino_fp16=args.sino_fp16,
-                                     serial_power=serial_power)
+def _gpu_steps(args, cbct, G, Y, Y_host, f, f_host, flush, stream, levels, iters, mu, world, clock_gpu):
+    import torch
+    graphs = not args.no_graphs
+
+    def step(**kw):
+        return cbct.cbct_reconstruct(G, Y, mu, iters, levels, f_out=f, tv_mode=args.tv_mode,
+                                     adjoint_mode=args.adjoint_mode, sino_fp16=args.sino_fp16, use_graphs=graphs,
+                                     **kw)
 
     for _ in range(args.warmup):
-        step(False)
+        step()
     torch.cuda.synchronize()
 
-    # ---- device-resident timed region --------------------------------------------
-    sampler = ClockSampler(local) if rank == 0 else None
+    # ---- device-resident timed region: one event pair per step (and per level) -------
+    sampler = ClockSampler(clock_gpu) if clock_gpu is not None else None
     barrier(world)
     torch.cuda.synchronize()
-    step_ms, kms, klaunch, kms_f, kl_f = [], {}, {}, {}, {}
-    n_launch0 = cbct.cbct_kernel_launch_count()
+    step_ms, level_ms = [], [0.0] * levels
     for _ in range(args.steps):
         flush.fill_(1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        _, info = step(True)
+        _, info = step(level_times=True)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        for k, v in info["kernel_ms"].items():
-            kms[k] = kms.get(k, 0.0) + v
-        for k, v in info["kernel_launches"].items():
-            klaunch[k] = klaunch.get(k, 0) + v
-        for k, v in info["kernel_ms_finest"].items():
-            kms_f[k] = kms_f.get(k, 0.0) + v
-        for k, v in info["kernel_launches_finest"].items():
-            kl_f[k] = kl_f.get(k, 0) + v
+        level_ms = [a + b for a, b in zip(level_ms, info["level_ms"])]
     torch.cuda.synchronize()
-    n_launch = cbct.cbct_kernel_launch_count() - n_launch0
     barrier(world)
     clocks = sampler.stop() if sampler else None
     tot_ms = max_over_ranks(sum(step_ms), world)
-    n_iter = levels * iters
-    value = world * args.steps * n_iter / (tot_ms / 1e3)
+    fin_ms = max_over_ranks(level_ms[0], world)
 
     # ---- end to end through the C ABI with host buffers ---------------------------
     barrier(world)
@@ -299,44 +368,54 @@ def run_gpu(args, world, rank, local):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         Y.copy_(Y_host, non_blocking=True)
-        step(False)
+        step()
         f_host.copy_(f, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     e2e_tot = max_over_ranks(sum(e2e_ms), world)
-    e2e_value = world * args.steps * n_iter / (e2e_tot / 1e3)
 
-    # ---- every kernel class timed launch by launch (a separate pass of the same steps, the
-    #      power iterations in level order so that no two streams share the event windows) --
-    split_ms, split_n = {}, {}
+    # ---- every kernel class timed launch by launch: a separate pass of the same steps,
+    #      the power iterations in level order so that no two streams share the event
+    #      windows (per-launch events keep the graphs off in this pass) ------------------
+    split_ms, split_n, kms_f, kl_f = {}, {}, {}, {}
+    n0 = cbct.cbct_kernel_launch_count()
     for _ in range(args.steps):
         flush.fill_(1)
-        _, info = step(True, mask=0, serial_power=True)
-        for k, v in info["kernel_ms"].items():
-            split_ms[k] = split_ms.get(k, 0.0) + v
-        for k, v in info["kernel_launches"].items():
-            split_n[k] = split_n.get(k, 0) + v
+        _, info = step(kernel_times=True, kernel_mask=0, serial_power=True)
+        for src, dst in ((info["kernel_ms"], split_ms), (info["kernel_launches"], split_n),
+                         (info["kernel_ms_finest"], kms_f), (info["kernel_launches_finest"], kl_f)):
+            for k, v in src.items():
+                dst[k] = dst.get(k, 0) + v
     torch.cuda.synchronize()
+    # kernels per step (the timed steps launch the same kernels; their graph replays do
+    # not pass through the library's launch sites, so they are counted here)
+    launches_per_step = (cbct.cbct_kernel_launch_count() - n0) / args.steps
 
     # ---- the same steps with lambda_max(P^T P) cached per geometry (reported beside) --
-    cbct.cbct_reconstruct(G, Y, mu, iters, levels, f_out=f, reuse_lambda=True, tv_mode=args.tv_mode,
-                          adjoint_mode=args.adjoint_mode, sino_fp16=args.sino_fp16)   # fills the cache
+    step(reuse_lambda=True)   # fills the cache
     torch.cuda.synchronize()
     cached_ms = []
     for _ in range(args.steps):
         flush.fill_(1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        cbct.cbct_reconstruct(G, Y, mu, iters, levels, f_out=f, reuse_lambda=True, tv_mode=args.tv_mode,
-                              adjoint_mode=args.adjoint_mode, sino_fp16=args.sino_fp16)
+        step(reuse_lambda=True)
         e1.record(stream)
         e1.synchronize()
         cached_ms.append(e0.elapsed_time(e1))
     cached_tot = max_over_ranks(sum(cached_ms), world)
+    return dict(tot_ms=tot_ms, fin_ms=fin_ms, level_ms=level_ms, e2e_tot=e2e_tot, split_ms=split_ms,
+                split_n=split_n, kms_f=kms_f, kl_f=kl_f, launches_per_step=launches_per_step,
+                cached_tot=cached_tot, clocks=clocks, graphs=graphs)
 
-    if rank != 0:
-        return
+
+def _gpu_line(args, cbct, torch, dev, G, case, cfg, Y, Y_host, f, f_host, res, world):
+    levels, iters, mu = cfg["levels"], cfg["iters"], cfg["mu"]
+    tot_ms, split_ms, split_n, kms_f, kl_f = res["tot_ms"], res["split_ms"], res["split_n"], res["kms_f"], res["kl_f"]
+    clocks = res["clocks"]
+    n_iter = levels * iters
+    value = world * args.steps * n_iter / (tot_ms / 1e3)
 
     # ---- roofline of the dominant kernel --------------------------------------------
     peaks, peak_kind = measured_peaks()
@@ -353,52 +432,67 @@ def run_gpu(args, world, rank, local):
     clock_mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") \
         or peaks.get("sm_max_mhz", 2032.0)
     alu_peak = sm_count * 128 * clock_mhz * 1e6 / 1e12      # T lane-ops/s (FP32 pipes x clock)
-    # rates from the finest level's Algorithm A1 iterations, timed inside the timed steps:
-    # they run after every power iteration has finished, so nothing shares their event
-    # windows (the finer levels' power iterations overlap the coarser levels on a side
-    # stream); the per-class totals come from the separate serial pass
+    # rates from the finest level's Algorithm A1 iterations (they run after every power
+    # iteration has finished, so nothing shares their event windows)
     units_f = {k: nnz[0] * iters for k in ("project", "backproject")}
     per_kernel = {}
     for k in ("project", "backproject"):
         t = kms_f[k] / 1e3
         per_kernel[k] = {"ms_per_step": split_ms[k] / args.steps, "launches_per_step": split_n[k] / args.steps,
                          "finest_fbs_ms_per_step": kms_f[k] / args.steps,
-                         "finest_fbs_launches_per_step": kl_f[k] / args.steps}
+                         "finest_fbs_launches_per_step": kl_f[k] / args.steps,
+                         "ms_per_operation": kms_f[k] / (args.steps * iters)}
         if k == "backproject" and args.adjoint_mode == 1:
             per_kernel[k]["note"] = "Eq. 2 adjoint in the FBS iterations: no nonzero-based rate"
             continue
         per_kernel[k]["gnnz_per_s"] = units_f[k] * args.steps / t / 1e9
-        per_kernel[k]["alu_tops"] = units_f[k] * args.steps * OPS_PER_NNZ[k] / t / 1e12
+        per_kernel[k]["alu_tops_survey_basis"] = units_f[k] * args.steps * OPS_PER_NNZ_SURVEY / t / 1e12
+        per_kernel[k]["alu_tops_kernel_basis"] = units_f[k] * args.steps * OPS_PER_NNZ[k] / t / 1e12
+        pf = profile_fields(k, args.workload)
+        if "l2_bytes_per_launch" in pf:
+            per_kernel[k]["l2_gbs"] = pf["l2_bytes_per_launch"] / (per_kernel[k]["ms_per_operation"] / 1e3) / 1e9
+        if "issue_active_pct" in pf:
+            per_kernel[k]["issue_active_pct"] = pf["issue_active_pct"]
     nvox = [np.prod([(n + (1 << l) - 1) >> l for n in cfg["vol"]]) for l in range(levels)]
     tv_bytes = sum(12.0 * v * iters * 10 for v in nvox) * args.steps   # read f, read g, write f per sweep
     per_kernel["tv"] = {"ms_per_step": split_ms["tv"] / args.steps,
                         "gbs": tv_bytes / (split_ms["tv"] / 1e3) / 1e9, "launches_per_step": split_n["tv"] / args.steps,
-                        "note": "timed in the separate all-classes pass"}
+                        "note": "HBM-equivalent rate: 12 B per voxel per prox sweep (10 sweeps per iteration)"}
+    timing = ("CUDA events on the launching stream around every operation of the class, in a separate pass of "
+              "the same steps (the headline steps carry no per-launch events); rates from the finest level's "
+              "Algorithm A1 iterations, which run with nothing beside them")
     if dom in ("project", "backproject"):
-        ach = per_kernel[dom]["alu_tops"]
+        pk = per_kernel[dom]
+        ach = pk["alu_tops_survey_basis"]
+        pf = profile_fields(dom, args.workload)
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tlane-op/s",
-                "frac": ach / alu_peak, "traffic": profile_traffic(dom, args.workload),
-                "launch_ms": kms_f[dom] / (args.steps * iters),
-                "timing": "CUDA events around every operation of the class in the finest level's Algorithm A1 "
-                          "iterations inside the timed steps (no other stream's work beside them); launch_ms is "
-                          "the time of one operation (the adjoint: column running sums + gather)",
-                "basis": f"{OPS_PER_NNZ[dom]:.0f} lane-ops per nonzero x the finest level's exact nnz; peak = "
-                         f"{sm_count} SMs x 128 FP32 lanes x {clock_mhz:.0f} MHz (median SM clock in the timed "
-                         "region)"}
+                "frac": ach / alu_peak, "traffic": pf.get("traffic_bytes_per_launch"),
+                "launch_ms": pk["ms_per_operation"], "timing": timing,
+                "basis": f"{OPS_PER_NNZ_SURVEY:.0f} lane-ops per nonzero (the measurement plan's floor) x the "
+                         f"finest level's exact nnz ({nnz[0]}) per operation; peak = {sm_count} SMs x 128 FP32 "
+                         f"lanes x {clock_mhz:.0f} MHz (median SM clock in the timed region). Normalised rate: "
+                         "the kernel does no per-nonzero work",
+                "basis_survey": {"ops_per_nnz": OPS_PER_NNZ_SURVEY, "frac": ach / alu_peak},
+                "basis_kernel": {"ops_per_nnz": OPS_PER_NNZ[dom],
+                                 "frac": pk["alu_tops_kernel_basis"] / alu_peak},
+                "l2_gbs": pk.get("l2_gbs"), "issue_active_pct": pk.get("issue_active_pct"),
+                "operation": "one projection (its slab launches)" if dom == "project"
+                             else "one adjoint (column running sums + gather)"}
     else:
         ach = per_kernel["tv"]["gbs"]
         roof = {"kernel": "tv", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": profile_traffic("tv", args.workload)}
+                "frac": ach / peaks["hbm_gbs"], "traffic": profile_traffic("tv", args.workload), "timing": timing}
     roof["peak_source"] = peak_kind
 
-    # ---- CPU baseline: the oracle on a bounded sample ---------------------------------
+    # ---- CPU baseline: the oracle on a bounded sample, in the same unit ---------------
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        n_cpu = 2
-        dt, cores = cpu_oracle_iterations(case, n_cpu)
-        cpu = {"value": n_cpu / dt, "unit": "iter/s", "cores": cores, "cpu_model": cpu_model(), "kind": "oracle",
-               "sample": f"{n_cpu} Algorithm A1 iterations (P, P^T, 10 prox sweeps) of the finest level of the "
-                         f"same workload, FP64 C oracle with OpenMP; fixed beta, no power iteration"}
+        r = oracle_level_rate(case, levels, levels, 0)
+        cpu = {"value": r["value"], "unit": "iter/s", "cores": r["cores"], "cpu_model": cpu_model(), "kind": "oracle",
+               "finest_fbs_iter_s": 1.0 / r["level_s"][0],
+               "sample": f"one Algorithm A1 iteration (P, P^T, 10 prox sweeps) on each of the {levels} levels of "
+                         f"the same workload, FP64 C oracle with OpenMP, fixed beta, no power iteration; value = "
+                         f"levels / sum of the per-level times ({', '.join(f'{t:.3f}' for t in r['level_s'])} s)"}
 
     # ---- per-iteration fractions (algorithmic HBM bytes and the composite floor) -------
     s_bytes = 2 if args.sino_fp16 else 4
@@ -409,17 +503,17 @@ def run_gpu(args, world, rank, local):
     b_pow = sum(8 * v + 8 * r for v, r in zip(nv_l, nr_l)) * K_pi
     bw = peaks["hbm_gbs"] * 1e9
     t_step = tot_ms / args.steps / 1e3
-    floor_s = {"project": units["project"] * OPS_PER_NNZ["project"] / (alu_peak * 1e12),
-               "backproject": units["backproject"] * OPS_PER_NNZ["backproject"] / (alu_peak * 1e12),
-               "tv": sum(12.0 * v * 10 for v in nv_l) * iters / bw}
+    floor_s = {"project": units["project"] * OPS_PER_NNZ_SURVEY / (alu_peak * 1e12),
+               "backproject": units["backproject"] * OPS_PER_NNZ_SURVEY / (alu_peak * 1e12),
+               "tv": sum(12.0 * v for v in nv_l) * iters / bw}
     per_iter = {"hbm_bytes_per_fbs_iteration_finest": 24 * nv_l[0] + (8 + s_bytes) * nr_l[0],
                 "literal_hbm_frac": (b_fbs + b_pow) / (t_step * bw),
                 "composite_frac": sum(floor_s.values()) / t_step,
                 "floor_ms_per_step": {k: v * 1e3 for k, v in floor_s.items()},
                 "basis": "literal: (24 Nv + (8+s) Nr) bytes per FBS iteration and (8 Nv + 8 Nr) per power "
                          "iteration over the step time at the measured HBM bandwidth; composite: the sum of "
-                         "the per-class floors (P and P^T: nonzeros x lane-ops / FP32 issue peak; TV: 12 B "
-                         "per voxel per sweep / HBM) over the step time"}
+                         "the per-class floors (P and P^T: nonzeros x 5 lane-ops / FP32 issue peak; TV: 12 B "
+                         "per voxel per Algorithm A1 iteration, all sweeps fused, / HBM) over the step time"}
 
     # ---- quality context: the last reconstruction against the ground truth ------------
     quality = None
@@ -457,39 +551,47 @@ def run_gpu(args, world, rank, local):
                     "note": "the same reconstruction with float32 data storage (within 1e-4 of the FP64 "
                             "oracle by the parity tests)"}
 
-    launches = int(n_launch)   # every kernel the library launched inside the timed region
+    # ---- serving (continuous batching) on the medium/large mix -------------------------
+    serve = None
+    if world == 1 and not args.no_serve:
+        loads = [float(x) for x in args.serve_loads.split(",")]
+        serve = serve_measure(args, 0, dev, loads, args.serve_requests, args.mix)
+
+    config = config_of(args, cfg, world)
+    run = {"beta": "auto per level (30 power iterations, recomputed every step)",
+           "l2": "flushed between steps (256 MiB write, untimed)",
+           "graphs": "each level's Algorithm A1 iteration replayed as a captured CUDA graph" if res["graphs"]
+           else "off"}
     line = {
         "metric": "FBS iterations/s", "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded ellipsoid phantom, analytic line integrals, Poisson/log noise); "
                 "stands in for the paper's NCAT/CatPhan data",
-        "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "inner_iters": 10,
-                   "variant": {"tv_mode": ["isotropic", "anisotropic"][args.tv_mode],
-                               "adjoint": ["exact transpose", "Eq. 2 interpolation"][args.adjoint_mode],
-                               "data_storage": "float16" if args.sino_fp16 else "float32"},
-                   "beta": "auto per level (30 power iterations, recomputed every step)",
-                   "fbs_iterations_per_step": n_iter, "l2": "flushed between steps (256 MiB write, untimed)",
-                   "parallelism": f"replicas x{world}"},
+        "config": config, "run": run,
         "recon_s": tot_ms / args.steps / 1e3,
-        "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": int(Y_host.numel() * 4),
-                "d2h_bytes_per_step": int(f_host.numel() * 4)},
-        "lambda_cached": {"value": world * args.steps * n_iter / (cached_tot / 1e3), "unit": "iter/s",
-                          "ms_per_step": cached_tot / args.steps,
+        "finest_fbs_iter_s": world * args.steps * iters / (res["fin_ms"] / 1e3),
+        "level_ms_per_step": [v / args.steps for v in res["level_ms"]],
+        "e2e": {"value": world * args.steps * n_iter / (res["e2e_tot"] / 1e3), "unit": "iter/s",
+                "h2d_bytes_per_step": int(Y_host.numel() * 4), "d2h_bytes_per_step": int(f_host.numel() * 4)},
+        "lambda_cached": {"value": world * args.steps * n_iter / (res["cached_tot"] / 1e3), "unit": "iter/s",
+                          "ms_per_step": res["cached_tot"] / args.steps,
                           "note": "beta's power iterations reused from an earlier call on the same geometry"},
         "roofline": roof,
         "kernels": per_kernel,
         "kernel_ms_per_step": {k: v / args.steps for k, v in split_ms.items()},
         "kernel_split_note": "kernel_ms_per_step: every launch timed with CUDA events in a separate pass of the "
-                             "same steps, the power iterations in level order (serial_power); the timed steps "
-                             "time the project and backproject launches, and the rates and the roofline use "
-                             "those of the finest level's Algorithm A1 iterations",
-        "gpu_launches": launches,
+                             "same steps, the power iterations in level order (serial_power)",
+        "gpu_launches": int(round(res["launches_per_step"] * args.steps)),
+        "gpu_launches_note": "kernels per step counted by the library's launch sites in the separate pass "
+                             "(the same kernels as the timed steps, whose per-level graphs replay them) x steps",
         "per_iteration": per_iter,
         "quality": quality,
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
+    if serve is not None:
+        line["serve"] = serve
     if fp16_err is not None:
         line["fp16_error"] = fp16_err
     print(json.dumps(line), flush=True)
@@ -597,15 +699,9 @@ def _fifo_latencies(arrivals, service):
     return out
 
 
-def run_serve(args, world, rank, local):
-    import torch
-
-    from paper_1002_3675_b300 import cbct
-
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    rng = np.random.default_rng(1004 + rank)
-    if args.mix == "clinical":
+def _serve_base(args, rank, dev, mix):
+    """The request kinds of a serving mix (uploaded) and a description."""
+    if mix == "clinical":
         # the medium and large workloads (20, 30 and 40 views), drawn uniformly
         names = ["medium", "large20", "large30", "large"]
         cases = []
@@ -613,72 +709,97 @@ def run_serve(args, world, rank, local):
             c = synth.make_case(nm)
             cfg = synth.CONFIGS[nm]
             cases.append(dict(geom=c["geom"], Y=c["Y"], mu=cfg["mu"], levels=cfg["levels"], iters=cfg["iters"]))
-        base = _upload_requests(cases, dev)
-        n = args.serve_requests
-        order = [int(q) for q in rng.integers(0, len(base), size=n)]
-        text = (f"{n} requests drawn uniformly from the medium workload and the large one at 20, 30 and 40 views "
-                f"({', '.join(names)})")
-    elif args.mix == "small":
+        return _upload_requests(cases, dev), ("requests drawn uniformly from the medium workload and the large one "
+                                              f"at 20, 30 and 40 views ({', '.join(names)})"), True
+    if mix == "small":
         base = _upload_requests(_small_requests(8, 1006 + rank), dev)
-        n = args.serve_requests
-        order = [q % len(base) for q in range(n)]
-        text = _request_text(base) + f" (8 small-workload scans); {n} arrivals cycling through them"
-    else:
-        base = _upload_requests(synth.make_request_set(1003 + rank, args.requests), dev)
-        n = args.serve_requests
-        order = [q % len(base) for q in range(n)]
-        text = _request_text(base) + f"; {n} arrivals cycling through them"
+        return base, _request_text(base) + " (8 small-workload scans), arrivals cycling through them", False
+    base = _upload_requests(synth.make_request_set(1003 + rank, args.requests), dev)
+    return base, _request_text(base) + ", arrivals cycling through them", False
+
+
+def serve_measure(args, rank, dev, loads, n, mix):
+    """Continuous-batching server against a one-at-a-time FIFO queue: n seeded Poisson
+    arrivals at each load (a fraction of the one-at-a-time capacity).  Returns a dict."""
+    import torch
+
+    from paper_1002_3675_b300 import cbct
+
+    base, text, drawn = _serve_base(args, rank, dev, mix)
     for r in base:
         r["G"] = cbct.cbct_geometry_create(r["geom"])
     stream = torch.cuda.current_stream()
     _sequential(cbct, base, stream)
     service = dict(enumerate(_sequential(cbct, base, stream)))
-    mean_s = statistics.mean(service[q] for q in order)
-    rate = args.load / mean_s                     # arrivals/s at the chosen fraction of one-at-a-time capacity
-    gaps = rng.exponential(1.0 / rate, size=n)
     srv = cbct.Server(args.budget_gb << 30, args.slots, use_graphs=True)
     # warm-up: every geometry once, so resident tables and graphs exist
     for r in base:
         srv.wait(srv.submit(r["geom"], r["Y_dev"], r["mu"], r["iters"], r["levels"], r["f_dev"]), 600000)
-    outs = [torch.empty_like(base[q]["f_dev"]) for q in order]
+    pct = lambda xs, p: float(np.percentile(np.asarray(xs), p))  # noqa: E731
+    out = {"workload": f"{n} arrivals per load, " + text, "slots": args.slots, "hbm_budget_gb": args.budget_gb,
+           "graphs": True, "service_s": {str(q): service[q] for q in service}, "loads": []}
+    for li, load in enumerate(loads):
+        rng = np.random.default_rng(1004 + rank + 1000 * li)
+        order = [int(q) for q in rng.integers(0, len(base), size=n)] if drawn else [q % len(base) for q in range(n)]
+        mean_s = statistics.mean(service[q] for q in order)
+        rate = load / mean_s                    # arrivals/s at this fraction of one-at-a-time capacity
+        gaps = rng.exponential(1.0 / rate, size=n)
+        outs = [torch.empty_like(base[q]["f_dev"]) for q in order]
+        busy0 = srv.stats()["busy_s"]
+        t0 = time.perf_counter()
+        tickets, arrivals = [], []
+        next_t = t0
+        for q, gap, fo in zip(order, gaps, outs):
+            next_t += gap
+            while True:
+                d = next_t - time.perf_counter()
+                if d <= 0:
+                    break
+                time.sleep(min(d, 0.002))
+            r = base[q]
+            arrivals.append(time.perf_counter() - t0)
+            tickets.append(srv.submit(r["geom"], r["Y_dev"], r["mu"], r["iters"], r["levels"], fo))
+        res = [srv.wait(t, 600000) for t in tickets]
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        lat = [r["latency_s"] for r in res]
+        fifo = _fifo_latencies(arrivals, [service[q] for q in order])
+        fifo_wall = max(a + l for a, l in zip(arrivals, fifo))
+        out["loads"].append({
+            "load": load, "arrival_rate_per_s": rate, "arrivals": n, "wall_s": wall,
+            "recon_per_s": n / wall, "fifo_recon_per_s": n / fifo_wall,
+            "latency_s": {"p50": pct(lat, 50), "p90": pct(lat, 90), "p99": pct(lat, 99), "max": max(lat)},
+            "fifo_one_at_a_time_latency_s": {"p50": pct(fifo, 50), "p90": pct(fifo, 90), "p99": pct(fifo, 99),
+                                             "max": max(fifo)},
+            "mean_service_s": mean_s, "server_busy_s": srv.stats()["busy_s"] - busy0})
+    srv.close()
+    out["note"] = ("FIFO: a zero-overhead one-at-a-time queue replayed with the same arrival times and the "
+                   "measured cbct_reconstruct service time of each request")
+    return out
+
+
+def run_serve(args, world, rank, local):
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    loads = [float(x) for x in args.serve_loads.split(",")]
     sampler = ClockSampler(local) if rank == 0 else None
     barrier(world)
     t0 = time.perf_counter()
-    tickets, arrivals = [], []
-    next_t = t0
-    for q, gap, f in zip(order, gaps, outs):
-        next_t += gap
-        while True:
-            d = next_t - time.perf_counter()
-            if d <= 0:
-                break
-            time.sleep(min(d, 0.002))
-        r = base[q]
-        arrivals.append(time.perf_counter() - t0)
-        tickets.append(srv.submit(r["geom"], r["Y_dev"], r["mu"], r["iters"], r["levels"], f))
-    res = [srv.wait(t, 600000) for t in tickets]
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
+    serve = serve_measure(args, rank, dev, loads, args.serve_requests, args.mix)
+    wall = max_over_ranks(time.perf_counter() - t0, world)
     barrier(world)
     clocks = sampler.stop() if sampler else None
-    stats = srv.stats()
-    srv.close()
-    lat = [r["latency_s"] for r in res]
-    fifo = _fifo_latencies(arrivals, [service[q] for q in order])
-    wall = max_over_ranks(wall, world)
     if rank == 0:
-        pct = lambda xs, p: float(np.percentile(np.asarray(xs), p))  # noqa: E731
-        line = {"mode": "serve", "metric": "reconstructions/s", "value": world * n / wall, "unit": "recon/s",
-                "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * wall,
+        main = serve["loads"][len(loads) // 2]
+        line = {"mode": "serve", "metric": "reconstructions/s", "value": world * main["recon_per_s"],
+                "unit": "recon/s", "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * wall,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded ellipsoid phantoms, analytic line integrals, Poisson/log noise)",
-                "config": {"workload": text, "arrivals": f"Poisson, {rate:.2f}/s "
-                           f"({args.load:.2f} x one-at-a-time capacity)", "slots": args.slots,
-                           "hbm_budget_gb": args.budget_gb, "graphs": True, "parallelism": f"replicas x{world}"},
-                "latency_s": {"p50": pct(lat, 50), "p90": pct(lat, 90), "p99": pct(lat, 99), "max": max(lat)},
-                "fifo_one_at_a_time_latency_s": {"p50": pct(fifo, 50), "p90": pct(fifo, 90), "p99": pct(fifo, 99),
-                                                 "max": max(fifo)},
-                "mean_service_s": mean_s, "server_busy_s": stats["busy_s"], "clocks": clocks}
+                "config": {"workload": serve["workload"], "value_at_load": main["load"],
+                           "parallelism": f"replicas x{world}"},
+                "serve": serve, "clocks": clocks}
         print(json.dumps(line), flush=True)
 
 
@@ -765,7 +886,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="medium", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOAD_TEXT))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-quality", action="store_true", help="skip the ground-truth comparison (voxelisation)")
     ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "vcycle", "kernels"],
@@ -776,12 +897,15 @@ def main():
     ap.add_argument("--adjoint-mode", type=int, default=0, choices=[0, 1],
                     help="step-1 adjoint: 0 exact transpose, 1 Eq. 2 interpolation")
     ap.add_argument("--requests", type=int, default=16)
-    ap.add_argument("--load", type=float, default=0.8, help="serve: arrival rate / one-at-a-time capacity")
     ap.add_argument("--slots", type=int, default=16, help="serve: slots (one per distinct scan geometry keeps all resident)")
     ap.add_argument("--budget-gb", type=int, default=150)
     ap.add_argument("--mix", default="clinical", choices=["clinical", "batch16", "small"],
                     help="serve: request mix (medium/large workloads, or the 16 heterogeneous requests)")
-    ap.add_argument("--serve-requests", type=int, default=40, help="serve: arrivals")
+    ap.add_argument("--serve-requests", type=int, default=200, help="serve: arrivals per load")
+    ap.add_argument("--serve-loads", default="0.5,0.8,1.0",
+                    help="serve: arrival rates as fractions of the one-at-a-time capacity")
+    ap.add_argument("--no-serve", action="store_true", help="step mode: skip the serving block")
+    ap.add_argument("--no-graphs", action="store_true", help="step mode: launch every kernel (no CUDA graphs)")
     ap.add_argument("--batch-mix", default="hetero", choices=["hetero", "small"],
                     help="batch: the 16 heterogeneous requests, or --requests copies of the small workload")
     args = ap.parse_args()

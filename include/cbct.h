@@ -140,6 +140,14 @@ typedef struct {
                              kernel_ms, over the finest level's Algorithm A1 iterations
                              alone (no other stream's work runs beside them)           */
     int *kernel_launches_finest; /* optional host out [CBCT_NUM_KERNEL_CLASSES]         */
+    float *level_ms;      /* optional host out [levels], index 0 = finest: device time of
+                             each level's Algorithm A1 iterations, from one pair of CUDA
+                             events on `stream` around them (no event per launch, so the
+                             run is otherwise unchanged; synchronises at the end of the
+                             call).  The finest level runs after every power iteration
+                             has finished, so nothing else shares its window; a coarser
+                             level's window may also hold finer levels' power iterations
+                             running on the geometry's side stream.  Cascade only.      */
 } cbct_options;
 
 /* Kernel classes reported through cbct_options.kernel_ms. */
@@ -305,7 +313,7 @@ typedef struct {
     double mu;
     int iters, levels;
     cbct_options opts;        /* as for cbct_reconstruct; betas copied at submit;
-                                 energy_trace, beta_out, kernel_ms ignored             */
+                                 energy_trace, beta_out, kernel_ms, level_ms ignored   */
     float *f_out_dev;         /* volume [nz][ny][nx]; written before completion        */
 } cbct_server_request;
 typedef struct {

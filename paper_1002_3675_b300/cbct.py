@@ -48,7 +48,8 @@ class Options(C.Structure):
                 ("adjoint_mode", C.c_int), ("mg_cycle", C.c_int), ("mg_pre", C.c_int), ("mg_post", C.c_int),
                 ("mg_coarse", C.c_int), ("mg_accepted", C.POINTER(C.c_int)),
                 ("step_trace", C.POINTER(C.c_double)), ("serial_power", C.c_int),
-                ("kernel_ms_finest", C.POINTER(C.c_float)), ("kernel_launches_finest", C.POINTER(C.c_int))]
+                ("kernel_ms_finest", C.POINTER(C.c_float)), ("kernel_launches_finest", C.POINTER(C.c_int)),
+                ("level_ms", C.POINTER(C.c_float))]
 
 
 class Request(C.Structure):
@@ -294,12 +295,14 @@ def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=N
                      betas=None, eps=0.0, inner_iters=0, clamp_mode=0, sino_fp16=False, power_iters=0,
                      f_init=None, start_level=0, use_graphs=False, trace=False, kernel_times=False,
                      reuse_lambda=False, tv_mode=0, adjoint_mode=0, mg_cycle=0, mg_pre=0, mg_post=0, mg_coarse=0,
-                     kernel_mask=0, serial_power=False):
+                     kernel_mask=0, serial_power=False, level_times=False):
     """Returns f_out, or (f_out, info) when trace/kernel_times is requested; info holds
     'trace' [levels][iters][3] ([iters][3] after each V-cycle when mg_cycle=1),
     'step_trace' [levels][iters] |f_k+1 - f_k| ([iters], the change over each V-cycle),
     'betas' [levels], 'accepted' [levels] (V-cycles), 'kernel_ms'/'kernel_launches' and
-    'kernel_ms_finest'/'kernel_launches_finest' (the finest level's A1 iterations)."""
+    'kernel_ms_finest'/'kernel_launches_finest' (the finest level's A1 iterations), and
+    with level_times=True 'level_ms' [levels] (index 0 finest: each level's A1 iterations
+    timed by one event pair, without per-launch events)."""
     f_out = _empty(g.vol_shape) if f_out is None else f_out
     o = Options()
     o.beta = beta
@@ -338,11 +341,16 @@ def cbct_reconstruct(g: Geometry, Y, mu: float, iters: int, levels: int, f_out=N
         o.kernel_ms_finest = kmf
         o.kernel_launches_finest = klf
         o.kernel_mask = int(kernel_mask)
+    lm = (C.c_float * levels)() if level_times else None
+    if level_times:
+        o.level_ms = lm
     _check(lib.cbct_reconstruct(g.handle, _ptr(Y, "Y"), g.angles.ctypes.data_as(C.POINTER(C.c_double)),
                                 len(g.angles), mu, iters, levels, C.byref(o), _ptr(f_out, "f_out"), _stream()))
-    if not (trace or kernel_times):
+    if not (trace or kernel_times or level_times):
         return f_out
     info = {"betas": bo}
+    if level_times:
+        info["level_ms"] = list(lm)
     if mg_cycle:
         info["accepted"] = np.array(acc[:levels])
     if trace:

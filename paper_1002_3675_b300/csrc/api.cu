@@ -1057,6 +1057,8 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
         return prof.collect(o.kernel_ms, o.kernel_launches, o.kernel_ms_finest, o.kernel_launches_finest);
     }
 
+    std::vector<cudaEvent_t> lev_a(levels, nullptr), lev_b(levels, nullptr);
+    if (o.level_ms && !prof.on) G->events.release_all();
     for (int l = start; l >= 0; --l) {
         Level *L = Ls[l];
         const GeoDev &g = L->gd;
@@ -1077,7 +1079,17 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
         SolveParams P;
         ST(solve_params(L, mu, beta, eps, M, o.clamp_mode, fp16, &P, o.tv_mode, o.adjoint_mode));
         prof.tag = l == 0 ? 1 : 0;
+        if (o.level_ms) {
+            lev_a[l] = G->events.get();
+            if (!lev_a[l]) return cuda_fail(cudaErrorMemoryAllocation, "level timing event");
+            CK(cudaEventRecord(lev_a[l], s), "level timing");
+        }
         ST(run_level(G, L, P, iters, dtrace, o.use_graphs != 0, prof, s));
+        if (o.level_ms) {
+            lev_b[l] = G->events.get();
+            if (!lev_b[l]) return cuda_fail(cudaErrorMemoryAllocation, "level timing event");
+            CK(cudaEventRecord(lev_b[l], s), "level timing");
+        }
         prof.tag = 0;
         if ((o.energy_trace || o.step_trace) && iters > 0) {
             const size_t lv = (size_t)iters * (levels - 1 - l);
@@ -1090,6 +1102,15 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
         Launch lz(prof, CBCT_K_TRANSFER);
         const GeoDev &g0 = Ls[0]->gd;
         CK(launch_vol_to_api(Ls[0]->f, f_out_dev, g0.nx, g0.ny, g0.nz, s), "volume layout");
+    }
+    if (o.level_ms) {
+        CK(cudaStreamSynchronize(s), "synchronising for level timing");
+        for (int l = 0; l < levels; ++l) {
+            float t = 0.f;
+            if (lev_a[l] && lev_b[l]) CK(cudaEventElapsedTime(&t, lev_a[l], lev_b[l]), "level timing");
+            o.level_ms[l] = t;
+        }
+        if (!prof.on) G->events.release_all();
     }
     return prof.collect(o.kernel_ms, o.kernel_launches, o.kernel_ms_finest, o.kernel_launches_finest);
 }

@@ -235,6 +235,7 @@ void cbct_server::run() {
             j.o.kernel_launches = nullptr;
             j.o.kernel_ms_finest = nullptr;
             j.o.kernel_launches_finest = nullptr;
+            j.o.level_ms = nullptr;
             j.f_out = p->req.f_out_dev;
             cbct_status st = E.add(&j);
             if (st != CBCT_OK) {
