@@ -86,7 +86,7 @@ OPS_PER_NNZ = {"backproject": 8.0, "project": 4.0}
 KERNEL_SOURCES = {
     "backproject": ("k_backproject", ["k_backproject.cu", "bp_tile.cuh"]),
     "project": ("k_project", ["k_project.cu", "project_tile.cuh"]),
-    "tv": ("k_tv_sweep", ["k_tv.cu", "tv_tile.cuh"]),
+    "tv": ("k_tv_x", ["k_tv.cu", "tv_tile.cuh", "tv_xmarch.cuh"]),
 }
 
 
@@ -457,7 +457,11 @@ def _gpu_line(args, cbct, torch, dev, G, case, cfg, Y, Y_host, f, f_host, res, w
     tv_bytes = sum(12.0 * v * iters * 10 for v in nvox) * args.steps   # read f, read g, write f per sweep
     per_kernel["tv"] = {"ms_per_step": split_ms["tv"] / args.steps,
                         "gbs": tv_bytes / (split_ms["tv"] / 1e3) / 1e9, "launches_per_step": split_n["tv"] / args.steps,
-                        "note": "HBM-equivalent rate: 12 B per voxel per prox sweep (10 sweeps per iteration)"}
+                        "note": "HBM-equivalent rate: 12 B per voxel per prox sweep (10 sweeps per iteration), "
+                                "whatever the number of sweeps fused per launch"}
+    pf_tv = profile_fields("tv", args.workload)
+    if pf_tv:
+        per_kernel["tv"]["profile"] = {k: v for k, v in pf_tv.items()}
     timing = ("CUDA events on the launching stream around every operation of the class, in a separate pass of "
               "the same steps (the headline steps carry no per-launch events); rates from the finest level's "
               "Algorithm A1 iterations, which run with nothing beside them")

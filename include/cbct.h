@@ -270,7 +270,9 @@ typedef struct {
 } cbct_request;
 cbct_status cbct_reconstruct_batch(const cbct_request *reqs, int n_reqs, int use_graphs, cudaStream_t stream);
 
-/* Launch shapes of one level (0 = the library's default); they change no result bit. */
+/* Launch shapes of one level (0 = the library's default); they change no bit of any
+ * volume (the float64 energy and step-norm sums may differ in their last bits, as the
+ * partial sums are grouped by tile). */
 typedef struct {
     int proj_threads;  /* projector block size: multiple of 32, >= 32 ceil(nv/32), <= 512 */
     int bp_vpl;        /* adjoint voxels per lane, 1..4                                */
@@ -285,6 +287,12 @@ typedef struct {
     int bp_layout;     /* adjoint lane layout: 1 consecutive voxels per lane, 2 interleaved
                           (0: interleaved when a warp's gathers would span 400 or more
                           detector rows)                                              */
+    int tv_sweeps;     /* TV prox of levels with z-columns of at most 96 voxels: prox sweeps
+                          fused per x-marching launch, 1 or 2 (0: 2); -1 selects the
+                          one-sweep-per-launch warp tiles instead (same volume bits)   */
+    int tv_warps;      /* x-marching TV: warps per block, 16 or 32 (0: 32 for two sweeps,
+                          16 for one); the block's output rows are warps - 2 sweeps + 1 */
+    int tv_planes;     /* x-marching TV: x-planes per block, >= 8 (0: from the size)   */
 } cbct_tuning;
 /* Time the candidate launch shapes of level `level` with CUDA events on `stream`
  * (synchronises), keep the fastest in the geometry and report it in *out. */

@@ -60,7 +60,7 @@ class Request(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("proj_threads", C.c_int), ("bp_vpl", C.c_int), ("bp_threads", C.c_int),
                 ("proj_ms", C.c_float), ("bp_ms", C.c_float), ("proj_smem", C.c_int), ("proj_levels", C.c_int),
-                ("bp_layout", C.c_int)]
+                ("bp_layout", C.c_int), ("tv_sweeps", C.c_int), ("tv_warps", C.c_int), ("tv_planes", C.c_int)]
 
 
 class ServerRequest(C.Structure):
@@ -402,13 +402,15 @@ def cbct_autotune(g: Geometry, level: int = 0) -> dict:
     t = Tuning()
     _check(lib.cbct_autotune(g.handle, level, C.byref(t), _stream()))
     return dict(proj_threads=t.proj_threads, proj_smem=t.proj_smem, bp_vpl=t.bp_vpl, bp_threads=t.bp_threads,
-                proj_ms=t.proj_ms, bp_ms=t.bp_ms, proj_levels=t.proj_levels, bp_layout=t.bp_layout)
+                proj_ms=t.proj_ms, bp_ms=t.bp_ms, proj_levels=t.proj_levels, bp_layout=t.bp_layout,
+                tv_sweeps=t.tv_sweeps, tv_warps=t.tv_warps, tv_planes=t.tv_planes)
 
 
 def cbct_set_tuning(g: Geometry, level: int, tuning: dict):
     t = Tuning(int(tuning.get("proj_threads", 0)), int(tuning.get("bp_vpl", 0)), int(tuning.get("bp_threads", 0)),
                0.0, 0.0, int(tuning.get("proj_smem", 0)), int(tuning.get("proj_levels", 0)),
-               int(tuning.get("bp_layout", 0)))
+               int(tuning.get("bp_layout", 0)), int(tuning.get("tv_sweeps", 0)), int(tuning.get("tv_warps", 0)),
+               int(tuning.get("tv_planes", 0)))
     _check(lib.cbct_set_tuning(g.handle, level, C.byref(t)))
 
 

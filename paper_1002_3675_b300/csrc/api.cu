@@ -67,6 +67,7 @@ TvArgs tv_args(const Level *L, const SolveParams &P) {
     a.aniso = P.tv_mode;
     a.jc = tv_rows_per_tile(a.nx, a.ny, a.nz);
     a.vz = tv_col_vz(a.nx, a.ny, a.nz);
+    tv_x_shape(a, L->tv_sweeps, L->tv_warps, L->tv_planes);
     return a;
 }
 
@@ -170,6 +171,22 @@ struct Launch {  // wraps one kernel launch with optional timing (on prof's stre
 cbct_status enqueue_prox(Level *L, const SolveParams &P, const float *src0, double *partial_e1, int *ne1,
                          double *partial_step, int *nstep, Prof &prof, cudaStream_t s) {
     const TvArgs ta = tv_args(L, P);
+    if (ta.xT > 0) {  // x-marching form: launches of up to xT fused sweeps
+        const XProxPlan pl = xprox_plan(ta, P.M, P.clamp_mode, src0, L->f, L->A, L->B, partial_e1 != nullptr,
+                                        partial_step != nullptr, vol_elems(L->gd));
+        for (const XLaunch &x : pl.launches) {
+            Launch l(prof, CBCT_K_TV);
+            CK(launch_tv_x(ta, x.T, x.clamp, x.fin, L->g, x.fout, x.e1 ? partial_e1 : nullptr,
+                           x.step ? partial_step : nullptr, s, nullptr),
+               "tv sweeps");
+        }
+        if (ne1) *ne1 = pl.n_e1;
+        if (nstep) *nstep = pl.n_step;
+        if (pl.step_fused || pl.result == L->f) return CBCT_OK;
+        Launch l(prof, CBCT_K_REDUCE);
+        CK(launch_step_copy(pl.result, L->f, vol_elems(L->gd), partial_step, s), "step");
+        return CBCT_OK;
+    }
     const bool fused = prox_step_fused(P.M, src0, L->f);
     const float *src = src0;
     for (int m = 0; m < P.M; ++m) {

@@ -218,8 +218,20 @@ k_step_batch(const StepItem *__restrict__ items, const long *__restrict__ start,
 static bool job_step_fused(const Job *j, const Level *L) {
     return prox_step_fused(j->P.M, j->P.clamp_mode == 0 ? L->f : L->g, L->f);
 }
-static int job_nstep(const Job *j, const Level *L) {
+// The x-marching prox plan of job j's current iteration (levels in that form).
+static XProxPlan job_xplan(const Job *j, Level *L) {
+    return xprox_plan(tv_args(L, j->P), j->P.M, j->P.clamp_mode, j->P.clamp_mode == 0 ? L->f : L->g, L->f, L->A,
+                      L->B, j->P.clamp_mode == 0, true, vol_elems(L->gd));
+}
+static int job_nstep(const Job *j, Level *L) {
+    if (tv_args(L, j->P).xT > 0) return job_xplan(j, L).n_step;
     return (int)(job_step_fused(j, L) ? tv_partials(L->nx, L->ny, L->nz) : step_partials(vol_elems(L->gd)));
+}
+// E1 partials of job j's iteration (literal clamp mode: the separate energy pass)
+static int job_ne1(const Job *j, Level *L) {
+    if (j->P.clamp_mode == 1) return (int)tv_energy_partials(L->nx, L->ny, L->nz);
+    if (tv_args(L, j->P).xT > 0) return job_xplan(j, L).n_e1;
+    return (int)tv_partials(L->nx, L->ny, L->nz);
 }
 
 // A TV sweep that fills the GPU by itself, or uses full-column tiles (which the batched
@@ -228,20 +240,7 @@ static bool tv_sweep_solo(int nx, int ny, int nz, long sms) {
     return (long)tv_blocks(nx, ny, nz) >= 16 * sms || tv_col_vz(nx, ny, nz) > 0;
 }
 
-// SM count of the current device, looked up once per device (atomics: the server's
-// worker threads call this concurrently).
-static int sm_count() {
-    static std::atomic<int> cache[64];
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) dev = 0;
-    int n = cache[dev].load(std::memory_order_relaxed);
-    if (n == 0) {
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
-        cache[dev].store(n, std::memory_order_relaxed);
-    }
-    return n;
-}
+static int sm_count() { return device_sm_count(); }
 
 #define ECK(call, what)                                      \
     do {                                                     \
@@ -384,8 +383,14 @@ cbct_status Engine::finish_level(Job *j) {
     return CBCT_OK;
 }
 
-// One TV item as a single-request sweep launch.
+// One TV item as a single-request launch (a sweep, or x-marching fused sweeps).
 static cbct_status launch_tv_item(const TvItem &it, cudaStream_t s) {
+    if (it.xT > 0) {
+        ECK(launch_tv_x(it.A, it.xT, it.xclamp, it.fin, it.g, it.fout, it.acc == TV_ACC_E1 ? it.partial : nullptr,
+                        it.acc == TV_ACC_STEP ? it.partial : nullptr, s, nullptr),
+            "tv sweeps");
+        return CBCT_OK;
+    }
     ECK(launch_tv_sweep(it.A, it.fin, it.g, it.fout, it.clamp != 0, it.acc == TV_ACC_E1 ? it.partial : nullptr, s,
                         nullptr, it.acc == TV_ACC_STEP ? it.partial : nullptr),
         "tv sweep");
@@ -480,8 +485,7 @@ cbct_status Engine::build_tables() {
                 ei.pe2 = L->partial;
                 ei.n2 = (int)np;
                 ei.pe1 = L->partial + np;
-                ei.n1 = (int)(j->P.clamp_mode == 1 ? tv_energy_partials(g.nx, g.ny, g.nz)
-                                                   : tv_partials(g.nx, g.ny, g.nz));
+                ei.n1 = job_ne1(j, L);
                 ei.pstep = step_region(L);
                 ei.nstep = job_nstep(j, L);
                 ei.inv_nv = j->P.inv_nv;
@@ -552,7 +556,7 @@ cbct_status Engine::build_tables() {
             ei.pe2 = L->partial;
             ei.n2 = (int)np;
             ei.pe1 = L->partial + np;
-            ei.n1 = (int)(j->P.clamp_mode == 1 ? tv_energy_partials(g.nx, g.ny, g.nz) : tv_partials(g.nx, g.ny, g.nz));
+            ei.n1 = job_ne1(j, L);
             ei.pstep = step_region(L);
             ei.nstep = job_nstep(j, L);
             ei.inv_nv = j->P.inv_nv;
@@ -604,12 +608,44 @@ cbct_status Engine::build_tables() {
         const float *src = j->P.clamp_mode == 0 ? L->f : L->g;
         const long nb = (long)tv_blocks(L->nx, L->ny, L->nz);
         const size_t np = project_partials(L->gd);
+        if (ta.xT > 0) {  // x-marching form: the single-request path's launches, solo
+            const XProxPlan pl = job_xplan(j, L);
+            for (const XLaunch &x : pl.launches) {
+                TvItem ti{};
+                ti.A = ta;
+                ti.fin = x.fin;
+                ti.g = L->g;
+                ti.fout = x.fout;
+                ti.clamp = 1;
+                ti.acc = x.e1 ? TV_ACC_E1 : x.step ? TV_ACC_STEP : TV_ACC_NONE;
+                ti.partial = x.step ? step_region(L) : L->partial + np;
+                ti.xT = x.T;
+                ti.xclamp = x.clamp;
+                if (chain) chain->tv.push_back(ti);
+                else solo_tv[0].push_back(ti);
+            }
+            if (chain) chain->step = StepItem{};
+            if (pl.step_fused || pl.result == L->f) continue;
+            StepItem si;
+            si.v = pl.result;
+            si.f = L->f;
+            si.partial = step_region(L);
+            si.n = (long)vol_elems(L->gd);
+            if (chain) {
+                chain->step = si;
+            } else {
+                hstep.push_back(si);
+                sstart.push_back(stot);
+                stot += (long)step_partials((size_t)si.n);
+            }
+            continue;
+        }
         const bool fused = job_step_fused(j, L);
         for (int m = 0; m < j->P.M; ++m) {
             const bool last = m == j->P.M - 1;
             float *dst = (last && fused) ? L->f : (m % 2 == 0) ? L->A : L->B;
             if (dst == src) dst = (dst == L->A) ? L->B : L->A;
-            TvItem ti;
+            TvItem ti{};
             ti.A = ta;
             ti.fin = src;
             ti.g = L->g;
@@ -1098,6 +1134,9 @@ extern "C" cbct_status cbct_autotune(cbct_geometry *G, int level, cbct_tuning *o
     out->bp_vpl = best_v;
     out->bp_threads = best_b;
     out->bp_layout = best_l;
+    out->tv_sweeps = L->tv_sweeps;
+    out->tv_warps = L->tv_warps;
+    out->tv_planes = L->tv_planes;
     out->proj_ms = best_p;
     out->bp_ms = best_q;
     return CBCT_OK;
@@ -1114,7 +1153,10 @@ extern "C" cbct_status cbct_set_tuning(cbct_geometry *G, int level, const cbct_t
     if ((t->proj_threads && (t->proj_threads < need || t->proj_threads > PROJ_MAX_THREADS || t->proj_threads % 32)) ||
         t->bp_vpl < 0 || t->bp_vpl > 4 ||
         (t->bp_threads && t->bp_threads != 64 && t->bp_threads != 128 && t->bp_threads != 256) ||
-        t->proj_levels < 0 || t->proj_levels > L->gd.nz || t->bp_layout < 0 || t->bp_layout > 2) {
+        t->proj_levels < 0 || t->proj_levels > L->gd.nz || t->bp_layout < 0 || t->bp_layout > 2 ||
+        t->tv_sweeps < -1 || t->tv_sweeps > 2 ||
+        (t->tv_warps && t->tv_warps != 16 && t->tv_warps != 32) ||
+        (t->tv_planes && t->tv_planes < 8)) {
         set_error("tuning values out of range");
         return CBCT_ERR_INVALID_ARG;
     }
@@ -1132,5 +1174,8 @@ extern "C" cbct_status cbct_set_tuning(cbct_geometry *G, int level, const cbct_t
     L->gd.bp_vpl = t->bp_vpl;
     L->gd.bp_threads = t->bp_threads;
     L->gd.bp_layout = t->bp_layout;
+    L->tv_sweeps = t->tv_sweeps;
+    L->tv_warps = t->tv_warps;
+    L->tv_planes = t->tv_planes;
     return CBCT_OK;
 }

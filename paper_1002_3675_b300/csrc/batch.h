@@ -44,6 +44,8 @@ struct TvItem {
     double *partial;
     int clamp;
     int acc;  // TV_ACC_NONE, TV_ACC_E1 or TV_ACC_STEP
+    int xT;            // > 0: one x-marching launch of xT sweeps (solo only), clamping per xclamp
+    unsigned xclamp;
 };
 
 struct VecItem {  // power-iteration helpers on one volume

@@ -93,6 +93,7 @@ struct Level {
     size_t partial_len = 0;
     double lambda = 0.0;          // cached lambda_max(P^T P) (0 = unknown)
     int lambda_iters = 0;
+    int tv_sweeps = 0, tv_warps = 0, tv_planes = 0;  // x-marching TV launch shape (0 = default)
     float *mg = nullptr;          // V-cycle volumes: linear term, restricted iterate, 2 scratch
     double *mg_partial = nullptr; // V-cycle dot-product partials
 };
@@ -128,6 +129,7 @@ struct cbct_geometry {
 namespace cbct {
 
 void set_error(const char *fmt, ...);
+int device_sm_count();  // SMs of the current device (cached per device)
 cbct_status cuda_fail(cudaError_t e, const char *what);
 
 // level management (geometry.cu)
@@ -170,6 +172,9 @@ struct TvArgs {
     int aniso;               // 0: isotropic E1, 1: anisotropic E1
     int jc;                  // rows per warp tile of the sweep (tv_rows_per_tile; 0: per voxel)
     int vz;                  // full-column tiles: voxels per lane in z (tv_col_vz; 0: 32-voxel z-blocks)
+    // x-marching fused sweeps (tv_xmarch.cuh; xT = 0: not used): sweeps per launch (1 or 2),
+    // warps per block, planes per block
+    int xT, xW, xLX;
 };
 // Forms of the TV sweep, chosen from the sizes alone (so every launch of a level, alone
 // or batched, uses the same tiles):
@@ -192,6 +197,39 @@ __host__ __device__ __forceinline__ int tv_rows_per_tile(int nx, int ny, int nz)
     }
     return (long)nx * ((ny + 15) / 16) * ((nz + 31) / 32) >= 8192 ? 16 : 0;
 }
+// x-marching form of a level (tv_xmarch.cuh), from the sizes and the level's launch-shape
+// overrides (0 = default): whole z-columns of at most 96 voxels and enough tiles to fill
+// the GPU.  Writes the shape into a (xT = 0 when the form does not apply).
+void tv_x_shape(TvArgs &a, int sweeps, int warps, int planes);
+// One launch of the x-marching form: T (1 or 2) consecutive sweeps fin -> fout, sweep t
+// clamping when bit t of clamp is set; partial_e1: E1 partials of fin; partial_step: the
+// partials of (fout_new - f_k)^2 with f_k in fout on entry.  *nblocks_out: partials written.
+cudaError_t launch_tv_x(const TvArgs &a, int T, unsigned clamp, const float *fin, const float *g, float *fout,
+                        double *partial_e1, double *partial_step, cudaStream_t s, int *nblocks_out);
+// Partials one x-marching launch of T sweeps writes (the block count).
+size_t tv_x_partials(const TvArgs &a, int T);
+// Upper bound of tv_x_partials over every shape the level may take (workspace sizing).
+size_t tv_x_partials_max(int nx, int ny, int nz);
+// The launches of a whole prox (M sweeps) in the x-marching form, from src0: launches of
+// up to a.xT sweeps ping-ponging through A and B, the last one writing f (f_k+1 over f_k)
+// unless its input is f itself.  Shared by the single-request path and the batch engine,
+// so both issue the same launches.
+struct XLaunch {
+    int T;
+    unsigned clamp;          // bit t: sweep t clamps at 0
+    const float *fin;
+    float *fout;
+    bool e1, step;           // accumulators of this launch
+};
+struct XProxPlan {
+    std::vector<XLaunch> launches;
+    const float *result;     // where the last launch leaves f_k+1
+    bool step_fused;         // the last launch forms the step partials (it overwrites f_k)
+    int n_e1, n_step;        // partials of the E1 launch and of the step norm (a step copy's
+                             // step_partials when not fused)
+};
+XProxPlan xprox_plan(const TvArgs &a, int M, int clamp_mode, const float *src0, float *f, float *A, float *B,
+                     bool want_e1, bool want_step, size_t nvox);
 // One prox sweep fin -> fout.  partial_e1: the E1 partials of fin; partial_step (fout
 // then holds f_k and is overwritten in place): the partials of (fout_new - f_k)^2.  At
 // most one of the two; tv_partials values either way.
@@ -226,6 +264,7 @@ size_t step_partials(size_t n);
 // the step-norm partials inside a level's partials buffer (after the projector's and
 // the TV sweep's)
 double *step_region(Level *L);
+size_t tv_region_len(const Level *L);
 // The last of M prox sweeps from src0 writes f_k+1 over f_k in place and forms the
 // step-norm partials itself unless its input is f_k (M == 1 from f_k); then it goes
 // through a buffer and launch_step_copy.  Number of step partials either way:

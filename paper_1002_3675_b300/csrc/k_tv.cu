@@ -1,5 +1,11 @@
-// TV prox sweep launchers (single request).  The arithmetic is in tv_tile.cuh.
-#include "tv_tile.cuh"
+// TV prox sweep launchers (single request).  The arithmetic is in tv_tile.cuh and,
+// for the x-marching fused sweeps, tv_xmarch.cuh.
+#include <float.h>
+
+#include <algorithm>
+#include <atomic>
+
+#include "tv_xmarch.cuh"
 
 namespace cbct {
 
@@ -66,6 +72,142 @@ k_tv_energy(TvArgs A, const float *__restrict__ fin, double *__restrict__ partia
         for (int w = 0; w < TV_THREADS / 32; ++w) s += red[w];
         partial[blockIdx.x] = s;
     }
+}
+
+// ---- x-marching fused sweeps -------------------------------------------------------
+// 64 registers per thread at most (1024 threads, or two blocks of 512, per SM).
+template <int T, int VZ, int W, bool ANISO>
+__global__ void __launch_bounds__(32 * W, 1024 / (32 * W))
+k_tv_x(TvArgs A, TvXArgs X, const float *__restrict__ fin, const float *__restrict__ g, float *__restrict__ fout,
+       double *__restrict__ partial) {
+    extern __shared__ float tvx_sm[];
+    tv_x_tile<T, VZ, W, ANISO>(A, X, fin, g, fout, partial, tvx_sm, blockIdx.x);
+}
+
+// Warps per block (16 or 32) and output rows: W = by + 2T - 1.
+static int tvx_warps(const TvArgs &a, int T) { return a.xW > 0 ? a.xW : (T == 2 ? 32 : 16); }
+
+static TvXArgs tvx_args(const TvArgs &a, int T) {
+    TvXArgs x;
+    x.W = tvx_warps(a, T);
+    x.by = x.W - 2 * T + 1;
+    x.lx = a.xLX;
+    x.nyt = (a.ny + x.by - 1) / x.by;
+    x.clamp = 0;
+    x.e1 = x.step = 0;
+    return x;
+}
+
+size_t tv_x_partials(const TvArgs &a, int T) {
+    const TvXArgs x = tvx_args(a, T);
+    return (size_t)x.nyt * ((a.nx + x.lx - 1) / x.lx);
+}
+
+// Shapes: W in {16, 32} warps with T in {1, 2} (so by >= 13) and planes >= 8.
+size_t tv_x_partials_max(int nx, int ny, int nz) {
+    (void)nz;
+    return (size_t)((ny + 12) / 13) * ((nx + 7) / 8);
+}
+
+void tv_x_shape(TvArgs &a, int sweeps, int warps, int planes) {
+    a.xT = a.xW = a.xLX = 0;
+    // columns of at most 96 voxels in whole lanes, enough tiles, eps^2 a normal float (the
+    // tile's ftz reciprocal square root)
+    if (!(tvx_vz(a.nz) && (long)a.nx * ((a.ny + 3) / 4) >= 8192) || sweeps < 0 || !(a.eps2 >= FLT_MIN)) return;
+    a.xT = (sweeps == 1 || sweeps == 2) ? sweeps : 2;
+    a.xW = (warps == 16 || warps == 32) ? warps : 0;
+    // planes per block: one wave of blocks (one 1024-thread block, or two of 512, per
+    // SM) with the x-range split as little as that allows (every block recomputes the
+    // planes its sweeps need beyond its own: fewer, longer blocks waste less; timed on
+    // B300 for 512x512x96 and 256x256x{48,64})
+    int lx = planes >= 8 ? planes : 0;
+    if (!lx) {
+        const int W = tvx_warps(a, a.xT), by = W - 2 * a.xT + 1;
+        const long nyt = (a.ny + by - 1) / by;
+        const long slots = (long)device_sm_count() * (W == 16 ? 2 : 1);
+        const long nxc = std::max<long>(1, slots / nyt);
+        lx = (int)std::max<long>(8, (a.nx + nxc - 1) / nxc);
+    }
+    a.xLX = std::min(lx, a.nx);
+}
+
+template <int T, int VZ, int W, bool ANISO>
+static cudaError_t launch_x4(const TvArgs &a, const TvXArgs &x, const float *fin, const float *g, float *fout,
+                             double *p, cudaStream_t s, unsigned nblk) {
+    const size_t smem = tvx_smem_floats(T, W, VZ) * sizeof(float);
+    static std::atomic<bool> attr_set[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set[dev]) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_tv_x<T, VZ, W, ANISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
+    k_tv_x<T, VZ, W, ANISO><<<nblk, 32 * W, smem, s>>>(a, x, fin, g, fout, p);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int T, int VZ, bool ANISO>
+static cudaError_t launch_x3(const TvArgs &a, const TvXArgs &x, const float *fin, const float *g, float *fout,
+                             double *p, cudaStream_t s, unsigned nblk) {
+    if (x.W == 16) return launch_x4<T, VZ, 16, ANISO>(a, x, fin, g, fout, p, s, nblk);
+    return launch_x4<T, VZ, 32, ANISO>(a, x, fin, g, fout, p, s, nblk);
+}
+
+template <int T, bool ANISO>
+static cudaError_t launch_x2(const TvArgs &a, const TvXArgs &x, const float *fin, const float *g, float *fout,
+                             double *p, cudaStream_t s, unsigned nblk) {
+    const int vz = tvx_vz(a.nz);
+    if (vz == 1) return launch_x3<T, 1, ANISO>(a, x, fin, g, fout, p, s, nblk);
+    if (vz == 2) return launch_x3<T, 2, ANISO>(a, x, fin, g, fout, p, s, nblk);
+    return launch_x3<T, 3, ANISO>(a, x, fin, g, fout, p, s, nblk);
+}
+
+cudaError_t launch_tv_x(const TvArgs &a, int T, unsigned clamp, const float *fin, const float *g, float *fout,
+                        double *partial_e1, double *partial_step, cudaStream_t s, int *nblocks_out) {
+    if (a.xT == 0 || !tvx_vz(a.nz) || (T != 1 && T != 2) || fin == fout || (partial_e1 && partial_step))
+        return cudaErrorInvalidValue;
+    TvXArgs x = tvx_args(a, T);
+    if (x.by < 1 || x.lx < 1 || (x.W != 16 && x.W != 32)) return cudaErrorInvalidValue;
+    x.clamp = clamp;
+    x.e1 = partial_e1 != nullptr;
+    x.step = partial_step != nullptr;
+    double *p = partial_e1 ? partial_e1 : partial_step;
+    const unsigned nblk = (unsigned)tv_x_partials(a, T);
+    if (nblocks_out) *nblocks_out = (int)nblk;
+    if (T == 1) return a.aniso ? launch_x2<1, true>(a, x, fin, g, fout, p, s, nblk)
+                               : launch_x2<1, false>(a, x, fin, g, fout, p, s, nblk);
+    return a.aniso ? launch_x2<2, true>(a, x, fin, g, fout, p, s, nblk)
+                   : launch_x2<2, false>(a, x, fin, g, fout, p, s, nblk);
+}
+
+XProxPlan xprox_plan(const TvArgs &a, int M, int clamp_mode, const float *src0, float *f, float *A, float *B,
+                     bool want_e1, bool want_step, size_t nvox) {
+    XProxPlan pl;
+    const float *src = src0;
+    for (int m0 = 0; m0 < M;) {
+        XLaunch x;
+        x.T = std::min(a.xT, M - m0);
+        const bool last = m0 + x.T == M;
+        x.fout = (last && src != f) ? f : (src == A ? B : A);
+        x.fin = src;
+        x.clamp = 0;
+        for (int t = 0; t < x.T; ++t)
+            if (clamp_mode == 0 || m0 + t == M - 1) x.clamp |= 1u << t;
+        x.e1 = want_e1 && m0 == 0;
+        x.step = want_step && last && x.fout == f;
+        pl.launches.push_back(x);
+        src = x.fout;
+        m0 += x.T;
+    }
+    pl.result = src;
+    pl.step_fused = !pl.launches.empty() && pl.launches.back().step;
+    pl.n_e1 = pl.launches.empty() ? 0 : (int)tv_x_partials(a, pl.launches.front().T);
+    pl.n_step = pl.step_fused ? (int)tv_x_partials(a, pl.launches.back().T) : (int)step_partials(nvox);
+    return pl;
 }
 
 size_t tv_partials(int nx, int ny, int nz) {

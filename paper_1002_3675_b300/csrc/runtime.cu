@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "cbct_internal.h"
 
@@ -292,9 +293,9 @@ cbct_status ensure_workspace(Level *L, bool need_half) {
     if (need_half && !L->Yh && (st = dmalloc((void **)&L->Yh, nr * 2, "half data")) != CBCT_OK) return st;
     // [projector partials][TV partials][step-norm partials]; the power iteration
     // reuses the front of the same buffer
-    size_t need = project_partials(L->gd) +
-                  std::max(tv_partials(L->nx, L->ny, L->nz), tv_energy_partials(L->nx, L->ny, L->nz)) +
-                  std::max(step_partials(nvox), tv_partials(L->nx, L->ny, L->nz));
+    size_t need = project_partials(L->gd) + tv_region_len(L) +
+                  std::max({step_partials(nvox), tv_partials(L->nx, L->ny, L->nz),
+                            tv_x_partials_max(L->nx, L->ny, L->nz)});
     size_t dp = 2 * ((nvox + 255) / 256) + 16;
     if (dp > need) need = dp;
     need += 64;
@@ -307,10 +308,29 @@ cbct_status ensure_workspace(Level *L, bool need_half) {
     return CBCT_OK;
 }
 
-double *step_region(Level *L) {
-    return L->partial + project_partials(L->gd) +
-           std::max(tv_partials(L->nx, L->ny, L->nz), tv_energy_partials(L->nx, L->ny, L->nz));
+// Length of the TV (E1) partials region of a level's partials buffer: enough for every
+// sweep form and x-marching launch shape the level may take.
+size_t tv_region_len(const Level *L) {
+    return std::max({tv_partials(L->nx, L->ny, L->nz), tv_energy_partials(L->nx, L->ny, L->nz),
+                     tv_x_partials_max(L->nx, L->ny, L->nz)});
 }
+
+// SM count of the current device, looked up once per device (atomics: the server's
+// worker threads call this concurrently).
+int device_sm_count() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n == 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+        cache[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
+double *step_region(Level *L) { return L->partial + project_partials(L->gd) + tv_region_len(L); }
 
 cbct_status ensure_mg_workspace(Level *L) {
     const size_t nvox = vol_elems(L->gd);

@@ -120,7 +120,7 @@ __host__ __device__ __forceinline__ long tv_warp_tiles(int nx, int ny, int nz) {
 // neighbour equals c where the difference is zero): the py/pz pieces D_d f * w_d, the
 // -(sum_d p_d / h_d) part of the divergence and the voxel's E1 term
 struct TvOwn {
-    float py, pz, div, e1;
+    float px, py, pz, div, e1;
 };
 template <bool E1, bool ANISO>
 __device__ __forceinline__ TvOwn tv_own(const TvArgs &A, float c, float fxp, float fyp, float fzp) {
@@ -132,6 +132,7 @@ __device__ __forceinline__ TvOwn tv_own(const TvArgs &A, float c, float fxp, flo
     if (ANISO) {
         const float qx = __fmaf_rn(gx, gx, A.eps2), qy = __fmaf_rn(gy, gy, A.eps2), qz = __fmaf_rn(gz, gz, A.eps2);
         const float rx = rsqrtf(qx), ry = rsqrtf(qy), rz = rsqrtf(qz);
+        o.px = __fmul_rn(gx, rx);
         o.py = __fmul_rn(gy, ry);
         o.pz = __fmul_rn(gz, rz);
         o.div = -__fmaf_rn(__fmul_rn(gx, rx), A.ihx, __fmaf_rn(o.py, A.ihy, __fmul_rn(o.pz, A.ihz)));
@@ -139,6 +140,7 @@ __device__ __forceinline__ TvOwn tv_own(const TvArgs &A, float c, float fxp, flo
     } else {
         const float q0 = __fmaf_rn(gx, gx, __fmaf_rn(gy, gy, __fmaf_rn(gz, gz, A.eps2)));
         const float n0 = rsqrtf(q0);
+        o.px = __fmul_rn(gx, n0);
         o.py = __fmul_rn(gy, n0);
         o.pz = __fmul_rn(gz, n0);
         o.div = -__fmul_rn(__fmaf_rn(gx, A.ihx, __fmaf_rn(gy, A.ihy, __fmul_rn(gz, A.ihz))), n0);
