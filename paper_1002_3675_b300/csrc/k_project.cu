@@ -7,14 +7,14 @@
 
 namespace cbct {
 
-template <int MODE>
+template <int MODE, bool VEC>
 __global__ void __launch_bounds__(PROJ_MAX_THREADS, 2)
 k_project(GeoDev G, const float *__restrict__ vol, const float *__restrict__ y32,
           const __half *__restrict__ y16, float *__restrict__ out, double *__restrict__ partial, int kr0, int kr1,
           int carry) {
     extern __shared__ float smem[];
-    project_tile(G, MODE, vol, y32, y16, out, partial, blockIdx.x, blockIdx.y, blockIdx.z, smem, kr0, kr1,
-                 (carry & 1) != 0, (carry & 2) != 0);
+    project_tile<VEC>(G, MODE, vol, y32, y16, out, partial, blockIdx.x, blockIdx.y, blockIdx.z, smem, kr0, kr1,
+                      (carry & 1) != 0, (carry & 2) != 0);
 }
 
 // Levels per launch: G.proj_levels if set, else the whole volume in one launch while it fits comfortably in the
@@ -56,21 +56,31 @@ cudaError_t launch_project(const GeoDev &g, const float *vol, const float *y32, 
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_set[dev]) {
-        cudaFuncSetAttribute(k_project<PROJ_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, PROJ_SMEM);
-        cudaFuncSetAttribute(k_project<PROJ_RESID32>, cudaFuncAttributeMaxDynamicSharedMemorySize, PROJ_SMEM);
-        cudaFuncSetAttribute(k_project<PROJ_RESID16>, cudaFuncAttributeMaxDynamicSharedMemorySize, PROJ_SMEM);
-        cudaFuncSetAttribute(k_project<PROJ_SCALED>, cudaFuncAttributeMaxDynamicSharedMemorySize, PROJ_SMEM);
-        cudaFuncSetAttribute(k_project<PROJ_RAW32>, cudaFuncAttributeMaxDynamicSharedMemorySize, PROJ_SMEM);
-        cudaFuncSetAttribute(k_project<PROJ_RAW16>, cudaFuncAttributeMaxDynamicSharedMemorySize, PROJ_SMEM);
+#define CBCT_PROJ_ATTR(M)                                                                                    \
+    cudaFuncSetAttribute(k_project<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, PROJ_SMEM);      \
+    cudaFuncSetAttribute(k_project<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, PROJ_SMEM)
+        CBCT_PROJ_ATTR(PROJ_PLAIN);
+        CBCT_PROJ_ATTR(PROJ_RESID32);
+        CBCT_PROJ_ATTR(PROJ_RESID16);
+        CBCT_PROJ_ATTR(PROJ_SCALED);
+        CBCT_PROJ_ATTR(PROJ_RAW32);
+        CBCT_PROJ_ATTR(PROJ_RAW16);
+#undef CBCT_PROJ_ATTR
         attr_set[dev] = true;
     }
-    const dim3 grid = project_grid(g), block((unsigned)project_threads(g));
+    // z-columns in 16-byte pieces (and slabs starting at multiples of 4 levels), and room
+    // for 4 levels of running sums at the longest cell sequence: 4 levels per lane
+    const int slots = g.nx + g.ny + 1;
     const int R = project_levels_per_launch(g);
+    const bool vec = (g.nz & 3) == 0 && (R & 3) == 0 &&
+                     (smem / 4 - proj_list_floats(slots)) / (slots + (slots + CHUNK - 1) / CHUNK) >= 4;
+    const dim3 grid = project_grid(g), block((unsigned)project_threads(g));
     for (int k0 = 0; k0 < g.nz; k0 += R) {
         const int k1 = std::min(g.nz, k0 + R);
         const int carry = (k0 > 0 ? 1 : 0) | (k1 < g.nz ? 2 : 0);
-#define CBCT_PROJ_LAUNCH(M) \
-    k_project<M><<<grid, block, smem, s>>>(g, vol, y32, y16, out, partial, k0, k1, carry)
+#define CBCT_PROJ_LAUNCH(M)                                                                 \
+    if (vec) k_project<M, true><<<grid, block, smem, s>>>(g, vol, y32, y16, out, partial, k0, k1, carry); \
+    else k_project<M, false><<<grid, block, smem, s>>>(g, vol, y32, y16, out, partial, k0, k1, carry)
         switch (mode) {
             case PROJ_PLAIN: CBCT_PROJ_LAUNCH(PROJ_PLAIN); break;
             case PROJ_RESID32: CBCT_PROJ_LAUNCH(PROJ_RESID32); break;

@@ -137,11 +137,14 @@ using namespace proj_detail;
 constexpr int PROJ_SMEM = 110 * 1024;   // largest size used
 constexpr int PROJ_SMEM_MIN = 16 * 1024;
 constexpr int PROJ_MAX_THREADS = 512;
-// prefix chunks of 48 segments: a whole number of 8-load batches, and about one chunk per
-// warp for the 250-730 segments of a column at 256 to 512 threads (timed on B300 against
-// 16, 32, 40 and 64: 64 was 1.6 % slower on 512x512x96, the others slower still)
-constexpr int CHUNK = 48;
+// prefix chunks of 16 segments: the running sums of a chunk are a chain of dependent
+// additions whose loads go out 4 (float4) or 8 at a time, and the chunk offsets are a
+// chain over the chunks, so short chunks keep both chains short while every warp of the
+// block gets chunks (timed on B300 for 512x512x96: 8, 12, 16, 24 segments 2.51, 2.32,
+// 2.28, 2.33 ms per projection; 48 segments with one level per lane took 2.57 ms)
+constexpr int CHUNK = 16;
 constexpr int PROJ_BATCH = 8;           // voxel loads in flight per thread
+constexpr int PROJ_VBATCH = 4;          // 16-byte voxel loads in flight per thread (4 levels each)
 
 // Projector block size (rows per tile): G.proj_threads if valid, else the default: one
 // thread per row up to 128 rows, 256 threads up to 256 rows, 512 above (timed on B300
@@ -158,9 +161,13 @@ __host__ __device__ __forceinline__ int proj_threads_of(const GeoDev &g) {
 // SM; 228 KB of shared memory per SM, 1 KB of it reserved per block), at most
 // PROJ_SMEM.  Larger tables hold whole 32-level bands for longer cell sequences (4 x 56
 // KB at 256 threads: 2.3 % faster than 4 x 55 KB on 256x256x64).
+// Floats before the chunk offsets: the segment list (exit t and z-column offset per
+// slot), rounded up to 16 bytes so that the running sums can be stored as float4.
+__host__ __device__ __forceinline__ int proj_list_floats(int slots) { return (2 * slots + 3) & ~3; }
+
 __host__ __device__ __forceinline__ int proj_smem_of(const GeoDev &g) {
     const int slots = g.nx + g.ny + 1;
-    const int least = (4 * (3 * slots + (slots + CHUNK - 1) / CHUNK) + 15) & ~15;  // one level per band
+    const int least = (4 * (proj_list_floats(slots) + slots + (slots + CHUNK - 1) / CHUNK) + 15) & ~15;  // one level per band
     if (g.proj_smem >= least && g.proj_smem <= PROJ_SMEM && g.proj_smem % 16 == 0) return g.proj_smem;
     const int blocks = max(1, 65536 / (64 * proj_threads_of(g)));
     const int fit = ((228 * 1024) / blocks - 1024) & ~1023;
@@ -214,6 +221,29 @@ __device__ __forceinline__ float eval_c(const float *C, const float *coff, int n
 // carries every ray's running sum in out: carry_in starts from out instead of 0,
 // carry_out stores the sum there and skips the epilogue.  The levels are added in the
 // same ascending order either way, so the split does not change a bit of the result.
+// One ray's z-geometry: height at O, cot(phi), and the levels between its xy entry and
+// exit (with a level of margin on each side; an empty range when klo > khi).
+struct RayZ {
+    float zO, cotp;
+    int klo, khi;
+};
+__device__ __forceinline__ RayZ ray_levels(const GeoDev &G, const ColumnRay &c, const float4 rz) {
+    RayZ r{rz.x, rz.y, 0, -1};
+    const float tanp = rz.w;
+    if (r.cotp != 0.f) {
+        const float za = __fmaf_rn(c.tin, tanp, r.zO), zb = __fmaf_rn(c.tout, tanp, r.zO);
+        r.klo = max((int)floorf((fminf(za, zb) - G.z0) * G.inv_hz) - 1, 0);
+        r.khi = min((int)floorf((fmaxf(za, zb) - G.z0) * G.inv_hz) + 1, G.nz - 1);
+    } else {
+        const int k0 = (int)floorf((r.zO - G.z0) * G.inv_hz);
+        if (k0 >= 0 && k0 < G.nz) r.klo = r.khi = k0;
+    }
+    return r;
+}
+
+// VEC: the running sums take 4 levels per lane (float4) where the z-columns come in
+// 16-byte pieces; the sums are the same additions in the same order either way.
+template <bool VEC = false>
 __device__ __forceinline__ void project_tile(const GeoDev &G, const int mode, const float *__restrict__ vol,
                                              const float *__restrict__ y32, const __half *__restrict__ y16,
                                              float *__restrict__ out, double *__restrict__ partial, const int a,
@@ -225,7 +255,6 @@ __device__ __forceinline__ void project_tile(const GeoDev &G, const int mode, co
     const int max_chunks = (slots + CHUNK - 1) / CHUNK;
     float *seg_t = smem;                          // exit t of each segment
     int *seg_off = (int *)(smem + slots);         // z-column offset of each segment's cell
-    float *coff = smem + 2 * slots;               // [chunk][level - band start]
     const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = T >> 5;
     const ColumnRay c = column_setup(G, ia, a);
 
@@ -257,17 +286,12 @@ __device__ __forceinline__ void project_tile(const GeoDev &G, const int mode, co
     const int b = zc * T + tid;
     const bool valid = b < G.nv;
     const float4 rz = G.ray_z[(size_t)a * G.nv + (valid ? b : G.nv - 1)];
-    const float zO = rz.x, cotp = rz.y, secp = rz.z, tanp = rz.w;
+    const float zO = rz.x, cotp = rz.y, secp = rz.z;
     int klo = 0, khi = -1;
     if (valid && S > 0) {
-        if (cotp != 0.f) {
-            const float za = __fmaf_rn(c.tin, tanp, zO), zb = __fmaf_rn(c.tout, tanp, zO);
-            klo = max((int)floorf((fminf(za, zb) - G.z0) * G.inv_hz) - 1, 0);
-            khi = min((int)floorf((fmaxf(za, zb) - G.z0) * G.inv_hz) + 1, G.nz - 1);
-        } else {
-            const int k0 = (int)floorf((zO - G.z0) * G.inv_hz);
-            if (k0 >= 0 && k0 < G.nz) klo = khi = k0;
-        }
+        const RayZ r0 = ray_levels(G, c, rz);
+        klo = r0.klo;
+        khi = r0.khi;
     }
     const float scale = S > 0 && c.tout > c.tin ? (float)S / (c.tout - c.tin) : 0.f;
     const size_t o = ((size_t)ia * G.nu + a) * G.nv + (valid ? b : 0);
@@ -275,10 +299,15 @@ __device__ __forceinline__ void project_tile(const GeoDev &G, const int mode, co
     __syncthreads();
 
     // ---- 2./3. bands of z-levels: running slice integrals, then the rays ---------------
-    const int c_cap = proj_smem_of(G) / 4 - 2 * slots;
+    float *coff = smem + proj_list_floats(slots);           // [chunk][level - band start]
+    const int c_cap = proj_smem_of(G) / 4 - proj_list_floats(slots);
     const int nr = kr1 - kr0;
+    // (VEC: the launcher checked that the z-columns come in 16-byte pieces, that the
+    // level range starts at a multiple of 4 and that 4 levels fit; bands then start at
+    // multiples of 4)
     int kband = S > 0 ? max(1, min(nr, c_cap / (S + max_chunks))) : nr;
     if (kband >= 32 && kband < nr) kband &= ~31;  // whole 32-level groups: full warps, aligned loads
+    else if (VEC && kband < nr) kband = max(4, kband & ~3);
     for (int kb = kr0; kb < kr1 && S > 0; kb += kband) {
         const int nk = min(kband, kr1 - kb);
         float *C = coff + max_chunks * nk;        // [s][kk], chunk-local running sums
@@ -286,35 +315,87 @@ __device__ __forceinline__ void project_tile(const GeoDev &G, const int mode, co
         //    each load is a contiguous piece of a z-column
         const int nkg = (nk + 31) >> 5;
         const int nch = (S + CHUNK - 1) / CHUNK;
-        for (int w = warp; w < nkg * nch; w += nwarp) {
-            const int kk = (w % nkg) * 32 + lane, ch = w / nkg;
-            if (kk >= nk) continue;
-            const int s0 = ch * CHUNK, s1 = min(S, s0 + CHUNK);
-            float run = 0.f, tp = s0 > 0 ? seg_t[s0 - 1] : c.tin;
-            for (int q = s0; q < s1; q += PROJ_BATCH) {
-                float v[PROJ_BATCH], tq[PROJ_BATCH];
+        if (VEC) {
+            // 4 levels per lane (16-byte loads and stores), min(nk, 32)/4 lanes per
+            // segment, so one warp instruction serves several chunks; per level the same
+            // additions in the same order as the scalar form below
+            const int L4 = min(nk, 32) >> 2, Gc = 32 / L4;
+            const int gi = lane / L4, q4 = lane - gi * L4;
+            const int ncg = (nch + Gc - 1) / Gc;
+            for (int w = warp; w < nkg * ncg; w += nwarp) {
+                const int kk = (w % nkg) * 32 + 4 * q4, ch = (w / nkg) * Gc + gi;
+                const bool on = gi < Gc && ch < nch && kk < nk;
+                const int s0 = ch * CHUNK, s1 = on ? min(S, s0 + CHUNK) : s0;
+                float4 run = make_float4(0.f, 0.f, 0.f, 0.f);
+                float tp = (s1 > s0 && s0 > 0) ? seg_t[s0 - 1] : c.tin;
+                for (int q = s0; q < s1; q += PROJ_VBATCH) {
+                    float4 v[PROJ_VBATCH];
+                    float tq[PROJ_VBATCH];
 #pragma unroll
-                for (int u = 0; u < PROJ_BATCH; ++u) {
-                    if (q + u < s1) {
-                        tq[u] = seg_t[q + u];
-                        v[u] = __ldg(vol + seg_off[q + u] + kb + kk);
+                    for (int u = 0; u < PROJ_VBATCH; ++u) {
+                        if (q + u < s1) {
+                            tq[u] = seg_t[q + u];
+                            v[u] = __ldg(reinterpret_cast<const float4 *>(vol + seg_off[q + u] + kb + kk));
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < PROJ_VBATCH; ++u) {
+                        if (q + u < s1) {
+                            const float dt = tq[u] - tp;
+                            run.x = __fmaf_rn(dt, v[u].x, run.x);
+                            run.y = __fmaf_rn(dt, v[u].y, run.y);
+                            run.z = __fmaf_rn(dt, v[u].z, run.z);
+                            run.w = __fmaf_rn(dt, v[u].w, run.w);
+                            tp = tq[u];
+                            *reinterpret_cast<float4 *>(C + (q + u) * nk + kk) = run;
+                        }
                     }
                 }
+            }
+        } else {
+            for (int w = warp; w < nkg * nch; w += nwarp) {
+                const int kk = (w % nkg) * 32 + lane, ch = w / nkg;
+                if (kk >= nk) continue;
+                const int s0 = ch * CHUNK, s1 = min(S, s0 + CHUNK);
+                float run = 0.f, tp = s0 > 0 ? seg_t[s0 - 1] : c.tin;
+                for (int q = s0; q < s1; q += PROJ_BATCH) {
+                    float v[PROJ_BATCH], tq[PROJ_BATCH];
 #pragma unroll
-                for (int u = 0; u < PROJ_BATCH; ++u) {
-                    if (q + u < s1) {
-                        run = __fmaf_rn(tq[u] - tp, v[u], run);
-                        tp = tq[u];
-                        C[(q + u) * nk + kk] = run;
+                    for (int u = 0; u < PROJ_BATCH; ++u) {
+                        if (q + u < s1) {
+                            tq[u] = seg_t[q + u];
+                            v[u] = __ldg(vol + seg_off[q + u] + kb + kk);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < PROJ_BATCH; ++u) {
+                        if (q + u < s1) {
+                            run = __fmaf_rn(tq[u] - tp, v[u], run);
+                            tp = tq[u];
+                            C[(q + u) * nk + kk] = run;
+                        }
                     }
                 }
             }
         }
         __syncthreads();
-        // chunk offsets: coff[ch][kk] = sum of the totals of chunks before ch
+        // chunk offsets: coff[ch][kk] = sum of the totals of chunks before ch, added in
+        // chunk order (the totals loaded four at a time, so that the chain of additions
+        // does not wait on each load)
         for (int kk = tid; kk < nk; kk += T) {
             float o = 0.f;
-            for (int ch = 0; ch < nch; ++ch) {
+            int ch = 0;
+            for (; ch + 4 <= nch; ch += 4) {
+                float tt[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) tt[u] = C[(min(S, (ch + u + 1) * CHUNK) - 1) * nk + kk];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    coff[(ch + u) * nk + kk] = o;
+                    o += tt[u];
+                }
+            }
+            for (; ch < nch; ++ch) {
                 coff[ch * nk + kk] = o;
                 o += C[(min(S, (ch + 1) * CHUNK) - 1) * nk + kk];
             }
