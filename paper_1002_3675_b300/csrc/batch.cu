@@ -445,7 +445,7 @@ cbct_status Engine::build_tables() {
         const int vpl0 = (g.bp_vpl >= 1 && g.bp_vpl <= 4) ? g.bp_vpl : bp_default_vpl(g);
         const long wt0 = vpl0 == 1 ? bp_warp_tiles<1>(g) : vpl0 == 2 ? bp_warp_tiles<2>(g)
                                                          : vpl0 == 3 ? bp_warp_tiles<3>(g) : bp_warp_tiles<4>(g);
-        const long eblocks0 = (long)((vol_elems(g) + EQ2_THREADS - 1) / EQ2_THREADS);
+        const long eblocks0 = eq2_tiles(g);
         const bool indep = ptiles >= 8 * sms && (eq2 ? eblocks0 >= 16 * sms : wt0 >= 64 * sms) &&
                            (power || tv_sweep_solo(g.nx, g.ny, g.nz, sms));
         if (indep) {  // the whole tick of this job on a side stream
@@ -507,7 +507,7 @@ cbct_status Engine::build_tables() {
             ei.out = L->g;
             ei.cscale = j->P.c_eq2;
             ei.mode = BP_STEP;
-            const long eblocks = (long)((vol_elems(g) + EQ2_THREADS - 1) / EQ2_THREADS);
+            const long eblocks = eq2_tiles(g);
             if (eblocks >= 16 * sms) {
                 solo_eq.push_back(ei);
             } else {

@@ -10,9 +10,15 @@
 // centres (samples outside the pixel grid count as 0).  Since L = l dsd / depth
 // (depth = distance along the central ray), the weight is dsd^2 l / depth^3.
 //
-// Layouts: volume [nx][ny][nz] (z fastest), residual [na][nu][nv] (v fastest).  One
-// thread per voxel; the 32 lanes of a warp are consecutive voxels of one z-column, so
-// they share the imager column pair (a0, a0 + 1) of every view and read nearby rows.
+// Layouts: volume [nx][ny][nz] (z fastest), residual [na][nu][nv] (v fastest).  A warp
+// owns one z-column (i, j), its lane l holding the voxels k = l + 32 v (v < VZ), so the
+// 32 VZ voxels of the column share everything that depends on the column and the view
+// alone (the depth and its reciprocal, u*, the imager column pair (a0, a0 + 1) and its
+// weight, the horizontal distance to the source), computed once per view; per voxel
+// remain v*, the bilinear taps of two imager rows, l and the weight.  The reciprocal
+// and the reciprocal square root are the hardware's approximate ones (relative error
+// about 2^-22, far inside the operator's 1e-5 parity); every other rounding is spelled
+// out, so the value does not depend on the kernel this body is inlined into.
 #pragma once
 
 #include "cbct_internal.h"
@@ -20,64 +26,133 @@
 namespace cbct {
 
 constexpr int EQ2_THREADS = 256;
+constexpr int EQ2_COLS = EQ2_THREADS / 32;   // z-columns per block (one per warp)
+constexpr int EQ2_MAX_VZ = 4;                // voxels per lane: z-blocks of 128 voxels
+
+// blocks of one launch (tiles of the batched kernel)
+__host__ __device__ __forceinline__ long eq2_tiles(const GeoDev &g) {
+    return ((long)g.nx * g.ny + EQ2_COLS - 1) / EQ2_COLS;
+}
 
 // lerp with explicit roundings: a + t (b - a) as t b + (a - t a)
 __device__ __forceinline__ float eq2_lerp(float a, float b, float t) { return __fmaf_rn(t, b, __fmaf_rn(-t, a, a)); }
 
-// Voxel idx (internal layout) of B r, without the dV/(du dv) factor.  Every rounding is
-// spelled out, so the value does not depend on the kernel this body is inlined into.
-__device__ __forceinline__ float eq2_voxel(const GeoDev &G, const float *__restrict__ r, size_t idx) {
-    const int k = (int)(idx % (size_t)G.nz);
-    const size_t t = idx / (size_t)G.nz;
-    const int j = (int)(t % (size_t)G.ny);
-    const int i = (int)(t / (size_t)G.ny);
-    // voxel centre
-    const float x = __fmaf_rn((float)i + 0.5f, G.hx, G.x0);
-    const float y = __fmaf_rn((float)j + 0.5f, G.hy, G.y0);
-    const float z = __fmaf_rn((float)k + 0.5f, G.hz, G.z0);
-    const float dsd2 = __fmul_rn(G.dsd, G.dsd);
-    const float z2 = __fmul_rn(z, z);
-    const float dz = __fmul_rn(G.dsd, z);
-    const size_t plane = (size_t)G.nu * G.nv;
-    float acc = 0.f;
-    for (int ia = 0; ia < G.na; ++ia) {
-        const float2 cs = __ldg(G.view + ia);  // cos, sin
-        // depth along the central ray and offsets along u and v, scaled to the imager
-        const float depth = __fsub_rn(G.dso, __fmaf_rn(x, cs.x, __fmul_rn(y, cs.y)));
-        const float inv = __frcp_rn(depth);
-        const float us = __fmul_rn(__fmul_rn(G.dsd, __fmaf_rn(y, cs.x, -__fmul_rn(x, cs.y))), inv);
-        const float vs = __fmul_rn(dz, inv);
-        const float fa = __fmaf_rn(us, G.inv_du, G.cu);
-        const float fb = __fmaf_rn(vs, G.inv_dv, G.cv);
-        // weight L^3 / (L0 l^2) = dsd^2 l / depth^3
-        const float ex = __fmaf_rn(-G.dso, cs.x, x), ey = __fmaf_rn(-G.dso, cs.y, y);
-        const float l = __fsqrt_rn(__fmaf_rn(ex, ex, __fmaf_rn(ey, ey, z2)));
-        const float w = __fmul_rn(__fmul_rn(dsd2, l), __fmul_rn(inv, __fmul_rn(inv, inv)));
-        // bilinear interpolation, zero outside the pixel grid
-        const float a0f = floorf(fa), b0f = floorf(fb);
-        const float ta = __fsub_rn(fa, a0f), tb = __fsub_rn(fb, b0f);
-        const int a0 = (int)a0f, b0 = (int)b0f;
-        const float *rv = r + (size_t)ia * plane;
-        const bool a0in = a0 >= 0 && a0 < G.nu, a1in = a0 + 1 >= 0 && a0 + 1 < G.nu;
-        const bool b0in = b0 >= 0 && b0 < G.nv, b1in = b0 + 1 >= 0 && b0 + 1 < G.nv;
-        const float r00 = (a0in && b0in) ? __ldg(rv + (size_t)a0 * G.nv + b0) : 0.f;
-        const float r01 = (a0in && b1in) ? __ldg(rv + (size_t)a0 * G.nv + b0 + 1) : 0.f;
-        const float r10 = (a1in && b0in) ? __ldg(rv + (size_t)(a0 + 1) * G.nv + b0) : 0.f;
-        const float r11 = (a1in && b1in) ? __ldg(rv + (size_t)(a0 + 1) * G.nv + b0 + 1) : 0.f;
-        const float val = eq2_lerp(eq2_lerp(r00, r01, tb), eq2_lerp(r10, r11, tb), ta);
-        acc = __fmaf_rn(w, val, acc);
-    }
-    return acc;
+__device__ __forceinline__ float eq2_rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float eq2_rsqrt(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
-// One block of EQ2_THREADS voxels: out = scale * B r (plain) or fin - cscale * B r (step).
+// The voxels k = kz0 + lane + 32 v (v < VZ) of column (i, j): acc[v] = (B r)_k without the
+// dV/(du dv) factor.
+template <int VZ>
+__device__ __forceinline__ void eq2_column(const GeoDev &G, const float *__restrict__ r, int i, int j, int kz0,
+                                           float *acc) {
+    const int lane = threadIdx.x & 31;
+    const float x = __fmaf_rn((float)i + 0.5f, G.hx, G.x0);
+    const float y = __fmaf_rn((float)j + 0.5f, G.hy, G.y0);
+    float z[VZ], z2[VZ];
+#pragma unroll
+    for (int v = 0; v < VZ; ++v) {
+        z[v] = __fmaf_rn((float)(kz0 + lane + 32 * v) + 0.5f, G.hz, G.z0);
+        z2[v] = __fmul_rn(z[v], z[v]);
+        acc[v] = 0.f;
+    }
+    const float dsd2 = __fmul_rn(G.dsd, G.dsd);
+    const size_t plane = (size_t)G.nu * G.nv;
+    for (int ia = 0; ia < G.na; ++ia) {
+        const float2 cs = __ldg(G.view + ia);  // cos, sin
+        // depth along the central ray, u* in pixels, and the column pair
+        const float depth = __fsub_rn(G.dso, __fmaf_rn(x, cs.x, __fmul_rn(y, cs.y)));
+        const float inv = eq2_rcp(depth);
+        const float us = __fmul_rn(__fmul_rn(G.dsd, __fmaf_rn(y, cs.x, -__fmul_rn(x, cs.y))), inv);
+        const float fa = __fmaf_rn(us, G.inv_du, G.cu);
+        const float a0f = floorf(fa);
+        const float ta = __fsub_rn(fa, a0f);
+        const int a0 = (int)a0f;
+        const bool a0in = a0 >= 0 && a0 < G.nu, a1in = a0 + 1 >= 0 && a0 + 1 < G.nu;
+        // v* = dsd z / depth in pixels; weight L^3 / (L0 l^2) = dsd^2 l / depth^3
+        const float sv = __fmul_rn(__fmul_rn(G.dsd, inv), G.inv_dv);
+        const float wc = __fmul_rn(dsd2, __fmul_rn(inv, __fmul_rn(inv, inv)));
+        const float ex = __fmaf_rn(-G.dso, cs.x, x), ey = __fmaf_rn(-G.dso, cs.y, y);
+        const float e2 = __fmaf_rn(ex, ex, __fmul_rn(ey, ey));
+        const float *rv0 = r + (size_t)ia * plane + (size_t)(a0in ? a0 : 0) * G.nv;
+        const float *rv1 = r + (size_t)ia * plane + (size_t)(a1in ? a0 + 1 : 0) * G.nv;
+        // the whole column's taps inside the imager (v* is linear in z): no per-voxel
+        // checks (the same values as the checked form)
+        const float fb_lo = __fmaf_rn(fminf(z[0], z[VZ - 1]), sv, G.cv);
+        const float fb_hi = __fmaf_rn(fmaxf(z[0], z[VZ - 1]), sv, G.cv);
+        // (every lane votes: the vote is outside any condition; the z-block test is the
+        // same for the whole warp)
+        const bool inside = a0 >= 0 && a0 + 1 < G.nu && fb_lo >= 0.f && fb_hi < (float)(G.nv - 1) &&
+                            kz0 + 32 * VZ <= G.nz;
+        const bool all_inside = __all_sync(0xffffffffu, inside);
+        if (all_inside) {
+#pragma unroll
+            for (int v = 0; v < VZ; ++v) {
+                const float fb = __fmaf_rn(z[v], sv, G.cv);
+                const float b0f = floorf(fb);
+                const float tb = __fsub_rn(fb, b0f);
+                const int b0 = (int)b0f;
+                const float r00 = __ldg(rv0 + b0), r01 = __ldg(rv0 + b0 + 1);
+                const float r10 = __ldg(rv1 + b0), r11 = __ldg(rv1 + b0 + 1);
+                const float val = eq2_lerp(eq2_lerp(r00, r01, tb), eq2_lerp(r10, r11, tb), ta);
+                const float l2 = __fadd_rn(e2, z2[v]);
+                const float w = __fmul_rn(wc, __fmul_rn(l2, eq2_rsqrt(l2)));   // dsd^2 depth^-3 l
+                acc[v] = __fmaf_rn(w, val, acc[v]);
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < VZ; ++v) {
+                const float fb = __fmaf_rn(z[v], sv, G.cv);
+                const float b0f = floorf(fb);
+                const float tb = __fsub_rn(fb, b0f);
+                const int b0 = (int)b0f;
+                const bool b0in = b0 >= 0 && b0 < G.nv, b1in = b0 + 1 >= 0 && b0 + 1 < G.nv;
+                // bilinear interpolation, zero outside the pixel grid
+                const float r00 = (a0in && b0in) ? __ldg(rv0 + b0) : 0.f;
+                const float r01 = (a0in && b1in) ? __ldg(rv0 + b0 + 1) : 0.f;
+                const float r10 = (a1in && b0in) ? __ldg(rv1 + b0) : 0.f;
+                const float r11 = (a1in && b1in) ? __ldg(rv1 + b0 + 1) : 0.f;
+                const float val = eq2_lerp(eq2_lerp(r00, r01, tb), eq2_lerp(r10, r11, tb), ta);
+                const float l2 = __fadd_rn(e2, z2[v]);
+                const float w = __fmul_rn(wc, __fmul_rn(l2, eq2_rsqrt(l2)));   // dsd^2 depth^-3 l
+                acc[v] = __fmaf_rn(w, val, acc[v]);
+            }
+        }
+    }
+}
+
+// Block blk (EQ2_COLS z-columns, one per warp): out = cscale * B' r (plain) or
+// fin - cscale * B' r (step), B' being B without its dV/(du dv) factor.
 __device__ __forceinline__ void eq2_block(const GeoDev &G, const float *__restrict__ r,
                                           const float *__restrict__ fin, float *__restrict__ out, float cscale,
                                           int mode, long blk) {
-    const size_t idx = (size_t)blk * EQ2_THREADS + threadIdx.x;
-    if (idx >= vol_elems(G)) return;
-    const float acc = eq2_voxel(G, r, idx);
-    out[idx] = mode == BP_STEP ? __fmaf_rn(-cscale, acc, __ldg(fin + idx)) : __fmul_rn(cscale, acc);
+    const long col = blk * EQ2_COLS + (threadIdx.x >> 5);
+    if (col >= (long)G.nx * G.ny) return;
+    const int i = (int)(col / G.ny), j = (int)(col % G.ny);
+    const int lane = threadIdx.x & 31;
+    const size_t base = (size_t)col * G.nz;     // internal layout: (i, j, k) at (i ny + j) nz + k
+    for (int kz0 = 0; kz0 < G.nz; kz0 += 32 * EQ2_MAX_VZ) {
+        const int vz = min(EQ2_MAX_VZ, (G.nz - kz0 + 31) / 32);
+        float acc[EQ2_MAX_VZ] = {0.f, 0.f, 0.f, 0.f};
+        if (vz == 1) eq2_column<1>(G, r, i, j, kz0, acc);
+        else if (vz == 2) eq2_column<2>(G, r, i, j, kz0, acc);
+        else if (vz == 3) eq2_column<3>(G, r, i, j, kz0, acc);
+        else eq2_column<4>(G, r, i, j, kz0, acc);
+#pragma unroll
+        for (int v = 0; v < EQ2_MAX_VZ; ++v) {
+            const int k = kz0 + lane + 32 * v;
+            if (v >= vz || k >= G.nz) continue;
+            const size_t idx = base + k;
+            out[idx] = mode == BP_STEP ? __fmaf_rn(-cscale, acc[v], __ldg(fin + idx)) : __fmul_rn(cscale, acc[v]);
+        }
+    }
 }
 
 }  // namespace cbct

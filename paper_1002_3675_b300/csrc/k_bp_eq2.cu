@@ -11,7 +11,7 @@ k_bp_eq2(GeoDev G, const float *__restrict__ r, const float *__restrict__ fin, f
 
 cudaError_t launch_backproject_eq2(const GeoDev &g, const float *r, const float *fin, float *out, float cscale,
                                    int mode, cudaStream_t s) {
-    const size_t nb = (vol_elems(g) + EQ2_THREADS - 1) / EQ2_THREADS;
+    const long nb = eq2_tiles(g);
     k_bp_eq2<<<(unsigned)nb, EQ2_THREADS, 0, s>>>(g, r, fin, out, cscale, mode);
     count_launch();
     return cudaGetLastError();
