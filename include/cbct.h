@@ -358,17 +358,19 @@ void cbct_debug_fail_next_allocations(int n);
 
 /* E1 energy of a volume without allocating anything.  The paper has no
  * counterpart: this entry point exists for callers that cannot call cudaMalloc --
- * code running while a stream is captured into a CUDA graph, real-time or embedded
- * hosts that forbid allocation after start-up, plug-ins that must leave the device
- * heap alone -- and therefore cannot create a cbct_geometry.
+ * real-time or embedded hosts that forbid allocation after start-up, plug-ins that
+ * must leave the device heap alone -- and therefore cannot create a cbct_geometry.
  * Writes *e1_dev = TV_eps(f) / (nx ny nz) (device float64, isotropic; same
- * definition and value as element 1 of cbct_energy with tv_mode 0) for f_dev, a [nz][ny][nx] float32 device
- * volume with spacings hx, hy, hz.  Asynchronous on `stream`.
+ * definition and value as element 1 of cbct_energy with tv_mode 0; eps >= 0, eps = 0
+ * the unsmoothed TV) for f_dev, a [nz][ny][nx] float32 device volume (4-byte
+ * aligned) with spacings hx, hy, hz.  Asynchronous on `stream`.
  * Scratch: a 1 MiB array inside the library, reserved on every GPU that loads the
  * library until the process exits; hence volumes above CBCT_NOALLOC_MAX_VOXELS are
  * rejected with CBCT_ERR_INVALID_ARG.  The first call on a device looks up that
  * array's device address (with that device current); make that first call before
- * any stream capture.  Calls share the array: calls that may overlap on the GPU
+ * any stream capture.  The address is kept for the life of the process: after a
+ * device reset (cudaDeviceReset) it is stale, and this entry point must not be called
+ * on that device again.  Calls share the array: calls that may overlap on the GPU
  * (other streams, other host threads) race and must be serialised by the caller.
  * No cudaMalloc, cudaFree or allocating library routine is called. */
 cbct_status cbct_tv_energy_noalloc(int nx, int ny, int nz, double hx, double hy, double hz, double eps,

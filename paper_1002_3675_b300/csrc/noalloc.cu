@@ -1,8 +1,8 @@
 // E1 energy without any allocation: cbct_tv_energy_noalloc.
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is being
-// captured into a CUDA graph, real-time or embedded hosts that forbid allocation
-// after start-up, and plug-ins that must not touch the process's device heap.
+// Some callers cannot call cudaMalloc: real-time or embedded hosts that forbid
+// allocation after start-up, and plug-ins that must not touch the process's device
+// heap.
 // They cannot create a cbct_geometry (whose workspaces are allocated), yet may
 // still want the TV energy of a volume they own.  This entry point serves them: it
 // is a variant of the library's E1 reduction (the per-block float64 partial sums
@@ -15,6 +15,8 @@
 // reads is written earlier in the same call (stream order), so nothing needs
 // clearing between calls, but calls whose work overlaps on the GPU (different
 // streams, or different host threads) race on it and must be serialised.
+#include <math.h>
+
 #include <mutex>
 
 #include "cbct_internal.h"
@@ -79,7 +81,10 @@ __global__ void k_tv_energy_static_final(const double *__restrict__ partials, in
     if (threadIdx.x == 0) *out = sh[0] * inv_nv;
 }
 
-// Once per device, with that device current: the device address of the scratch.
+// Once per device, with that device current: the device address of the scratch.  The
+// address is kept for the life of the process; a device reset (cudaDeviceReset) unloads
+// the library's module, after which the kept address is stale and this entry point must
+// not be called again on that device.
 cbct_status partials_for_current_device(double **out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -115,12 +120,14 @@ extern "C" cbct_status cbct_tv_energy_noalloc(int nx, int ny, int nz, double hx,
                         nx, ny, nz, nvox, CBCT_NOALLOC_MAX_VOXELS);
         return CBCT_ERR_INVALID_ARG;
     }
-    if (!(hx > 0) || !(hy > 0) || !(hz > 0) || !(eps > 0)) {
-        cbct::set_error("cbct_tv_energy_noalloc: spacings and eps must be > 0");
+    // eps = 0 is the unsmoothed TV (the square root is taken in float64), as in cbct_energy
+    if (!(hx > 0) || !(hy > 0) || !(hz > 0) || !(eps >= 0) || !isfinite(eps)) {
+        cbct::set_error("cbct_tv_energy_noalloc: spacings must be > 0 and eps finite and >= 0");
         return CBCT_ERR_INVALID_ARG;
     }
-    if (!f_dev || ((uintptr_t)f_dev & 15u) || !e1_dev || ((uintptr_t)e1_dev & 7u)) {
-        cbct::set_error("cbct_tv_energy_noalloc: f_dev must be 16-byte and e1_dev 8-byte aligned device pointers");
+    // (the kernel reads f one float at a time: 4-byte alignment suffices)
+    if (!f_dev || ((uintptr_t)f_dev & 3u) || !e1_dev || ((uintptr_t)e1_dev & 7u)) {
+        cbct::set_error("cbct_tv_energy_noalloc: f_dev must be 4-byte and e1_dev 8-byte aligned device pointers");
         return CBCT_ERR_INVALID_ARG;
     }
     double *partials = nullptr;

@@ -1,8 +1,7 @@
 """The allocation-free E1 entry point (cbct_tv_energy_noalloc) through the C ABI.
 
-It serves callers that cannot call cudaMalloc: code running while a stream is being
-captured into a CUDA graph, real-time hosts that forbid allocation after start-up,
-plug-ins that must leave the device heap alone.  Its only scratch is a static array
+It serves callers that cannot call cudaMalloc: real-time hosts that forbid allocation
+after start-up, plug-ins that must leave the device heap alone.  Its only scratch is a static array
 inside the library, shared by all calls.  Here two calls in a row -- a large volume,
 then a smaller one, so stale partial sums of the first call would show up in the
 second -- must each give the E1 that the allocating entry point (cbct_energy)
@@ -45,6 +44,16 @@ def test_noalloc_e1_matches_allocating_entry_point(cuda):
         ref = cbct.cbct_energy(G, Y, f, case["mu"], eps)[1]
         got = _noalloc_e1(cbct, torch, g, f, eps)
         assert abs(got - ref) <= E_TOL * abs(ref), (name, got, ref)
+    # eps = 0 (the unsmoothed TV) and a volume starting 4 bytes into its buffer, as for
+    # a view into a larger tensor
+    g = synth.make_case("small")["geom"]
+    buf = torch.tensor((rng.uniform(size=g["nz"] * g["ny"] * g["nx"] + 1) * 0.02).astype(np.float32), device="cuda")
+    f = buf[1:].view(g["nz"], g["ny"], g["nx"])
+    G = cbct.cbct_geometry_create(g)
+    ref0 = cbct.cbct_energy(G, torch.zeros((len(g["angles"]), g["nv"], g["nu"]), device="cuda"), f.clone(),
+                            1.0, 0.0)[1]
+    got0 = _noalloc_e1(cbct, torch, g, f, 0.0)
+    assert abs(got0 - ref0) <= E_TOL * abs(ref0), (got0, ref0)
 
 
 def test_noalloc_rejects_volumes_beyond_the_static_scratch(cuda):
