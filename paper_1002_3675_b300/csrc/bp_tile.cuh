@@ -83,6 +83,27 @@ __host__ __device__ __forceinline__ long bp_warp_tiles(const GeoDev &G) {
 // a broadcast.  The sums are taken in the same order as a pair-by-pair walk.
 constexpr int BP_REC_PER_WARP = 64;  // float4 records of one warp
 
+// Order of the xy-cells over the warp tiles: super-tiles of BP_SUPER x BP_SUPER cells
+// (i rows of super-tiles, j fastest inside a row; ragged at the far edges), cells j
+// fastest inside a super-tile.  The warps in flight then cover a compact patch of cells,
+// whose footprint on each view's imager is a narrow band of columns, instead of a strip
+// across the whole volume that touches most columns of most views: the row sums and
+// residuals they gather stay in L2.  The order changes no result bit (every warp's
+// voxels depend on that warp alone).
+constexpr int BP_SUPER = 64;
+// (32-bit arithmetic: a geometry has fewer than 2^31 voxels, so fewer cells)
+__host__ __device__ __forceinline__ void bp_cell_of(const GeoDev &G, int q, int &i, int &j) {
+    const int row = BP_SUPER * G.ny;                // cells in one row of super-tiles
+    const int R = q / row;
+    const int wi = min(BP_SUPER, G.nx - R * BP_SUPER);
+    const int off = q - R * row;
+    const int C = off / (wi * BP_SUPER);
+    const int wj = min(BP_SUPER, G.ny - C * BP_SUPER);
+    const int rem = off - C * wi * BP_SUPER;
+    i = R * BP_SUPER + rem / wj;
+    j = C * BP_SUPER + rem % wj;
+}
+
 template <int VPL, bool IL>
 __device__ __forceinline__ void bp_warp(const GeoDev &G, const int mode, const float *__restrict__ rs,
                                          const float *__restrict__ fin, float *__restrict__ out, const float c,
@@ -91,9 +112,9 @@ __device__ __forceinline__ void bp_warp(const GeoDev &G, const int mode, const f
     const int lane = threadIdx.x & 31;
     const int nkc = (G.nz + 32 * VPL - 1) / (32 * VPL);
     const int kc = (int)(wtile % nkc);
-    const long colid = wtile / nkc;
-    const int j = (int)(colid % G.ny);
-    const int i = (int)(colid / G.ny);
+    int i, j;
+    bp_cell_of(G, (int)(wtile / nkc), i, j);
+    const long colid = (long)i * G.ny + j;
     const int base = kc * 32 * VPL + (IL ? lane : lane * VPL);  // voxel v: base + (IL ? 32 v : v)
     constexpr int VS = IL ? 32 : 1;
     float acc[VPL];

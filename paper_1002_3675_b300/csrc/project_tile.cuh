@@ -311,7 +311,7 @@ __device__ __forceinline__ void project_tile(const GeoDev &G, const int mode, co
     for (int kb = kr0; kb < kr1 && S > 0; kb += kband) {
         const int nk = min(kband, kr1 - kb);
         float *C = coff + max_chunks * nk;        // [s][kk], chunk-local running sums
-        // 2. warps over (32-level group, 48-segment chunk) pairs; lanes over levels, so
+        // 2. warps over (32-level group, 16-segment chunk) pairs; lanes over levels, so
         //    each load is a contiguous piece of a z-column
         const int nkg = (nk + 31) >> 5;
         const int nch = (S + CHUNK - 1) / CHUNK;
