@@ -49,9 +49,6 @@ struct GeoDev {
     const float4 *ray_z;         // [nu][nv]  zO, cot(phi), sec(phi), tan(phi)  (cot = 0: v = 0)
     const float2 *ray_zc;        // [nu][nv]  zO, cot(phi) (same values; the adjoint's table)
     const float2 *col;           // [nu]      D = |d_xy|, t_S (source-to-O distance)
-    const unsigned *cell_start;  // [nx*ny+1] first entry of each xy-cell (i ny + j) in pairs
-    const unsigned *pairs;       // (view << 15 | column) of every detector column whose ray plane
-                                 // meets the cell, per cell in view then column order
     const float2 *view;          // [na]      cos, sin
     float2 *rowsum;              // [na][nu][nv+1] running sums of the scaled residual along each
                                  // detector column, as double-float (hi, lo) float32 pairs (workspace)

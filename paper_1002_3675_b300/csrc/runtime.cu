@@ -156,70 +156,13 @@ static cbct_status build_level(const cbct_geometry *G, int level, Level *L) {
             ray_e[(size_t)ia * nu + a] = make_float2((float)ex, (float)ey);
         }
     }
-    // Detector columns whose ray plane meets each xy-cell, per view: the interval
-    // spanned by the cell's four projected corners, widened by 0.01 pixel (the rays
-    // outside it meet the cell in a zero-length set); the adjoint's candidates, listed
-    // per cell as packed (view << 15 | column) in view order, then column order.
-    const size_t ncell = (size_t)L->nx * L->ny;
-    std::vector<unsigned> cell_start(ncell + 1, 0u);
-    std::vector<short2> arange((size_t)na * ncell);
-    {
-        const double x0 = -0.5 * L->nx * L->hx, y0 = -0.5 * L->ny * L->hy;
-        for (int ia = 0; ia < na; ++ia) {
-            const double c = cos(G->angles[ia]), sn = sin(G->angles[ia]);
-            for (int i = 0; i < L->nx; ++i)
-                for (int j = 0; j < L->ny; ++j) {
-                    double amin = 1e300, amax = -1e300;
-                    for (int q = 0; q < 4; ++q) {
-                        const double px = x0 + (i + (q & 1)) * L->hx, py = y0 + (j + (q >> 1)) * L->hy;
-                        const double u = L->dsd * (py * c - px * sn) / (L->dso - (px * c + py * sn));
-                        const double av = u / L->du + cu;
-                        amin = std::min(amin, av);
-                        amax = std::max(amax, av);
-                    }
-                    int lo = (int)ceil(amin - 0.01), hi = (int)floor(amax + 0.01);
-                    lo = std::max(lo, 0);
-                    hi = std::min(hi, nu - 1);
-                    if (hi < lo) {  // no column meets the cell: an empty range
-                        lo = 1;
-                        hi = 0;
-                    }
-                    arange[(size_t)ia * ncell + (size_t)i * L->ny + j] = make_short2((short)lo, (short)hi);
-                }
-        }
-    }
-    if (na >= (1 << 17)) {
-        set_error("level %d: %d views above the adjoint's limit 131071", level, na);
-        return CBCT_ERR_INVALID_ARG;
-    }
-    size_t npairs = 0;
-    for (size_t cell = 0; cell < ncell; ++cell) {
-        cell_start[cell] = (unsigned)npairs;
-        for (int ia = 0; ia < na; ++ia) {
-            const short2 ar = arange[(size_t)ia * ncell + cell];
-            if (ar.y >= ar.x) npairs += (size_t)(ar.y - ar.x + 1);
-        }
-        if (npairs >= (1ull << 32) - 1) {
-            set_error("level %d: adjoint candidate table above 2^32 entries", level);
-            return CBCT_ERR_INVALID_ARG;
-        }
-    }
-    cell_start[ncell] = (unsigned)npairs;
-    std::vector<unsigned> pairs(npairs);
-    for (size_t cell = 0, q = 0; cell < ncell; ++cell)
-        for (int ia = 0; ia < na; ++ia) {
-            const short2 ar = arange[(size_t)ia * ncell + cell];
-            for (int a = ar.x; a <= ar.y; ++a) pairs[q++] = ((unsigned)ia << 15) | (unsigned)a;
-        }
     size_t o_xy = 0;
     size_t o_e = align_up(o_xy + ray_xy.size() * sizeof(float4));
     size_t o_z = align_up(o_e + ray_e.size() * sizeof(float2));
     size_t o_zc = align_up(o_z + ray_z.size() * sizeof(float4));
     size_t o_col = align_up(o_zc + ray_zc.size() * sizeof(float2));
     size_t o_view = align_up(o_col + col.size() * sizeof(float2));
-    size_t o_cs = align_up(o_view + view.size() * sizeof(float2));
-    size_t o_pr = align_up(o_cs + cell_start.size() * sizeof(unsigned));
-    size_t total = align_up(o_pr + std::max<size_t>(pairs.size(), 1) * sizeof(unsigned));
+    size_t total = align_up(o_view + view.size() * sizeof(float2));
     cbct_status st = dmalloc(&L->tables, total, "ray tables");
     if (st != CBCT_OK) return st;
     char *base = (char *)L->tables;
@@ -230,10 +173,6 @@ static cbct_status build_level(const cbct_geometry *G, int level, Level *L) {
     if (e == cudaSuccess) e = cudaMemcpy(base + o_zc, ray_zc.data(), ray_zc.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(base + o_col, col.data(), col.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(base + o_view, view.data(), view.size() * sizeof(float2), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(base + o_cs, cell_start.data(), cell_start.size() * sizeof(unsigned), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !pairs.empty())
-        e = cudaMemcpy(base + o_pr, pairs.data(), pairs.size() * sizeof(unsigned), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "uploading ray tables");
 
     GeoDev &g = L->gd;
@@ -253,8 +192,6 @@ static cbct_status build_level(const cbct_geometry *G, int level, Level *L) {
     g.ray_zc = (const float2 *)(base + o_zc);
     g.col = (const float2 *)(base + o_col);
     g.view = (const float2 *)(base + o_view);
-    g.cell_start = (const unsigned *)(base + o_cs);
-    g.pairs = (const unsigned *)(base + o_pr);
     return CBCT_OK;
 }
 
