@@ -668,13 +668,19 @@ def run_batch(args, world, rank, local):
     sampler = ClockSampler(local) if rank == 0 else None
     barrier(world)
     seq_s, bat_s = [], []
+    # (NVTX ranges name the two halves of a timed step, so that a profiler can take the
+    # launches of one of them: ncu --nvtx --nvtx-include "batched_step/")
     for _ in range(args.steps):
+        torch.cuda.nvtx.range_push("sequential_step")
         seq_s.append(sum(_sequential(cbct, reqs, stream)))
+        torch.cuda.nvtx.range_pop()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("batched_step")
         e0.record(stream)
         cbct.cbct_reconstruct_batch(batch, use_graphs=True)
         e1.record(stream)
         e1.synchronize()
+        torch.cuda.nvtx.range_pop()
         bat_s.append(e0.elapsed_time(e1) / 1e3)
     barrier(world)
     clocks = sampler.stop() if sampler else None
