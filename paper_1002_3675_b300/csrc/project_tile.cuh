@@ -241,15 +241,6 @@ __device__ __forceinline__ RayZ ray_levels(const GeoDev &G, const ColumnRay &c, 
     return r;
 }
 
-// 16-byte asynchronous copy global -> shared (cp.async, cached in L2 only); both
-// addresses 16-byte aligned
-__device__ __forceinline__ void proj_cp16(float *dst, const float *src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void proj_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void proj_cp_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
 // VEC: the running sums take 4 levels per lane (float4) where the z-columns come in
 // 16-byte pieces; the sums are the same additions in the same order either way.
 template <bool VEC = false>
@@ -320,50 +311,44 @@ __device__ __forceinline__ void project_tile(const GeoDev &G, const int mode, co
     for (int kb = kr0; kb < kr1 && S > 0; kb += kband) {
         const int nk = min(kband, kr1 - kb);
         float *C = coff + max_chunks * nk;        // [s][kk], chunk-local running sums
-        // 2. running slice integrals of the band's levels (scalar form: warps over
-        //    (32-level group, 16-segment chunk) pairs, lanes over levels, so each load is a
-        //    contiguous piece of a z-column)
+        // 2. warps over (32-level group, 16-segment chunk) pairs; lanes over levels, so
+        //    each load is a contiguous piece of a z-column
         const int nkg = (nk + 31) >> 5;
         const int nch = (S + CHUNK - 1) / CHUNK;
         if (VEC) {
-            // 4 levels per 16-byte piece.  (a) The band's voxel values go into C with
-            // asynchronous 16-byte copies issued by every thread (no register staging,
-            // all in flight at once: one L2 round trip per band); (b) one thread per
-            // (chunk, level quad) turns them into chunk-local running sums in place.  Per
-            // level the additions are those of the scalar form below, in the same order.
-            // Threads take (segment or chunk, quad) pairs: the quads in blocks of at most T,
-            // per = T / nqb threads on each quad of a block (threads >= per nqb idle).
-            const int nq = nk >> 2;
-            for (int qb = 0; qb < nq; qb += T) {
-                const int nqb = min(T, nq - qb);
-                const int per = T / nqb, q = qb + tid % nqb, r0 = tid / nqb;
-                if (r0 < per)
-                    for (int sg = r0; sg < S; sg += per)
-                        proj_cp16(C + sg * nk + 4 * q, vol + seg_off[sg] + kb + 4 * q);
-            }
-            proj_cp_commit();
-            proj_cp_wait();
-            __syncthreads();
-            for (int qb = 0; qb < nq; qb += T) {
-                const int nqb = min(T, nq - qb);
-                const int per = T / nqb, q = qb + tid % nqb, r0 = tid / nqb;
-                if (r0 >= per) continue;
-                for (int ch = r0; ch < nch; ch += per) {
-                    const int s0 = ch * CHUNK, s1 = min(S, s0 + CHUNK);
-                    float4 run = make_float4(0.f, 0.f, 0.f, 0.f);
-                    float tp = s0 > 0 ? seg_t[s0 - 1] : c.tin;
-#pragma unroll 4
-                    for (int sg = s0; sg < s1; ++sg) {
-                        float4 *cp = reinterpret_cast<float4 *>(C + sg * nk + 4 * q);
-                        const float4 v = *cp;
-                        const float tq = seg_t[sg];
-                        const float dt = tq - tp;
-                        run.x = __fmaf_rn(dt, v.x, run.x);
-                        run.y = __fmaf_rn(dt, v.y, run.y);
-                        run.z = __fmaf_rn(dt, v.z, run.z);
-                        run.w = __fmaf_rn(dt, v.w, run.w);
-                        tp = tq;
-                        *cp = run;
+            // 4 levels per lane (16-byte loads and stores), min(nk, 32)/4 lanes per
+            // segment, so one warp instruction serves several chunks; per level the same
+            // additions in the same order as the scalar form below
+            const int L4 = min(nk, 32) >> 2, Gc = 32 / L4;
+            const int gi = lane / L4, q4 = lane - gi * L4;
+            const int ncg = (nch + Gc - 1) / Gc;
+            for (int w = warp; w < nkg * ncg; w += nwarp) {
+                const int kk = (w % nkg) * 32 + 4 * q4, ch = (w / nkg) * Gc + gi;
+                const bool on = gi < Gc && ch < nch && kk < nk;
+                const int s0 = ch * CHUNK, s1 = on ? min(S, s0 + CHUNK) : s0;
+                float4 run = make_float4(0.f, 0.f, 0.f, 0.f);
+                float tp = (s1 > s0 && s0 > 0) ? seg_t[s0 - 1] : c.tin;
+                for (int q = s0; q < s1; q += PROJ_VBATCH) {
+                    float4 v[PROJ_VBATCH];
+                    float tq[PROJ_VBATCH];
+#pragma unroll
+                    for (int u = 0; u < PROJ_VBATCH; ++u) {
+                        if (q + u < s1) {
+                            tq[u] = seg_t[q + u];
+                            v[u] = __ldg(reinterpret_cast<const float4 *>(vol + seg_off[q + u] + kb + kk));
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < PROJ_VBATCH; ++u) {
+                        if (q + u < s1) {
+                            const float dt = tq[u] - tp;
+                            run.x = __fmaf_rn(dt, v[u].x, run.x);
+                            run.y = __fmaf_rn(dt, v[u].y, run.y);
+                            run.z = __fmaf_rn(dt, v[u].z, run.z);
+                            run.w = __fmaf_rn(dt, v[u].w, run.w);
+                            tp = tq[u];
+                            *reinterpret_cast<float4 *>(C + (q + u) * nk + kk) = run;
+                        }
                     }
                 }
             }
