@@ -112,8 +112,10 @@ size_t tv_x_partials_max(int nx, int ny, int nz) {
 void tv_x_shape(TvArgs &a, int sweeps, int warps, int planes) {
     a.xT = a.xW = a.xLX = 0;
     // columns of at most 96 voxels in whole lanes, enough tiles, eps^2 a normal float (the
-    // tile's ftz reciprocal square root)
-    if (!(tvx_vz(a.nz) && (long)a.nx * ((a.ny + 3) / 4) >= 8192) || sweeps < 0 || !(a.eps2 >= FLT_MIN)) return;
+    // tile's ftz reciprocal square root).  Down to 128x128 planes (half a wave of blocks)
+    // the fused sweeps still beat ten one-sweep launches: timed on B300 for the 128x128x32
+    // coarse level of 256x256x64, the TV class of a reconstruction 13.65 -> 12.74 ms
+    if (!(tvx_vz(a.nz) && (long)a.nx * ((a.ny + 3) / 4) >= 2048) || sweeps < 0 || !(a.eps2 >= FLT_MIN)) return;
     a.xT = (sweeps == 1 || sweeps == 2) ? sweeps : 2;
     a.xW = (warps == 16 || warps == 32) ? warps : 0;
     // planes per block: one wave of blocks (one 1024-thread block, or two of 512, per
