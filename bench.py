@@ -36,7 +36,8 @@ Other modes print their own line:
   ``--mix batch16`` for the 16 requests above, ``--mix small`` for small scans).
 * ``--mode vcycle``: V-cycles (mg_cycle 1) against the cascade on the workload: time
   per reconstruction and the energy of Eq. 1 each reaches.
-* ``--mode kernels``: a profiler target (finest-level iterations with a fixed beta).
+* ``--mode kernels``: a profiler target (finest-level iterations with a fixed beta;
+  with ``--adjoint-mode 1`` through the Eq. 2 adjoint).
 """
 from __future__ import annotations
 
@@ -881,7 +882,12 @@ def run_kernels(args, world, rank, local):
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    cbct.cbct_fbs(G, Y, mu, beta, eps, 10, 0, args.steps, f, tv_mode=args.tv_mode)
+    if args.adjoint_mode:
+        # the Eq. 2 adjoint: one level of the cascade with the same fixed beta
+        cbct.cbct_reconstruct(G, Y, mu, args.steps, 1, f_out=f, beta=beta, eps=eps, inner_iters=10,
+                              tv_mode=args.tv_mode, adjoint_mode=args.adjoint_mode)
+    else:
+        cbct.cbct_fbs(G, Y, mu, beta, eps, 10, 0, args.steps, f, tv_mode=args.tv_mode)
     e1.record(stream)
     e1.synchronize()
     if rank == 0:

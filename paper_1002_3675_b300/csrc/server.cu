@@ -74,7 +74,8 @@ size_t geometry_bytes(const cbct_geometry_desc &d, int n_angles, int levels, boo
         const size_t nu = (d.nu + s - 1) / s, nv = (d.nv + s - 1) / s;
         const size_t vol = nx * ny * nz, sino = (size_t)n_angles * nu * nv;
         total += 4 * vol * 4 + sino * (4 + 4 + (fp16 ? 2 : 0));  // f, g, A, B; rs, Y, Yh
-        total += (size_t)n_angles * nu * 24 + nu * nv * 24 + (size_t)n_angles * nx * ny * 4;  // tables
+        total += (size_t)n_angles * nu * 24 + nu * nv * 24 + (size_t)n_angles * 8;  // ray tables
+        total += (size_t)n_angles * nu * (nv + 1) * 8;                            // adjoint row sums
         total += (sino / 32 + vol / 128 + 4096) * 8;                                             // partials
     }
     return total + (1 << 20);
