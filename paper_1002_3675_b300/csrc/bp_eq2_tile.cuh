@@ -65,64 +65,78 @@ __device__ __forceinline__ void eq2_column(const GeoDev &G, const float *__restr
     }
     const float dsd2 = __fmul_rn(G.dsd, G.dsd);
     const size_t plane = (size_t)G.nu * G.nv;
-    for (int ia = 0; ia < G.na; ++ia) {
-        const float2 cs = __ldg(G.view + ia);  // cos, sin
-        // depth along the central ray, u* in pixels, and the column pair
-        const float depth = __fsub_rn(G.dso, __fmaf_rn(x, cs.x, __fmul_rn(y, cs.y)));
-        const float inv = eq2_rcp(depth);
-        const float us = __fmul_rn(__fmul_rn(G.dsd, __fmaf_rn(y, cs.x, -__fmul_rn(x, cs.y))), inv);
-        const float fa = __fmaf_rn(us, G.inv_du, G.cu);
-        const float a0f = floorf(fa);
-        const float ta = __fsub_rn(fa, a0f);
-        const int a0 = (int)a0f;
-        const bool a0in = a0 >= 0 && a0 < G.nu, a1in = a0 + 1 >= 0 && a0 + 1 < G.nu;
-        // v* = dsd z / depth in pixels; weight L^3 / (L0 l^2) = dsd^2 l / depth^3
-        const float sv = __fmul_rn(__fmul_rn(G.dsd, inv), G.inv_dv);
-        const float wc = __fmul_rn(dsd2, __fmul_rn(inv, __fmul_rn(inv, inv)));
-        const float ex = __fmaf_rn(-G.dso, cs.x, x), ey = __fmaf_rn(-G.dso, cs.y, y);
-        const float e2 = __fmaf_rn(ex, ex, __fmul_rn(ey, ey));
-        const float *rv0 = r + (size_t)ia * plane + (size_t)(a0in ? a0 : 0) * G.nv;
-        const float *rv1 = r + (size_t)ia * plane + (size_t)(a1in ? a0 + 1 : 0) * G.nv;
-        // the whole column's taps inside the imager (v* is linear in z): no per-voxel
-        // checks (the same values as the checked form)
-        const float fb_lo = __fmaf_rn(fminf(z[0], z[VZ - 1]), sv, G.cv);
-        const float fb_hi = __fmaf_rn(fmaxf(z[0], z[VZ - 1]), sv, G.cv);
-        // (every lane votes: the vote is outside any condition; the z-block test is the
-        // same for the whole warp)
-        const bool inside = a0 >= 0 && a0 + 1 < G.nu && fb_lo >= 0.f && fb_hi < (float)(G.nv - 1) &&
-                            kz0 + 32 * VZ <= G.nz;
-        const bool all_inside = __all_sync(0xffffffffu, inside);
-        if (all_inside) {
-#pragma unroll
-            for (int v = 0; v < VZ; ++v) {
-                const float fb = __fmaf_rn(z[v], sv, G.cv);
-                const float b0f = floorf(fb);
-                const float tb = __fsub_rn(fb, b0f);
-                const int b0 = (int)b0f;
-                const float r00 = __ldg(rv0 + b0), r01 = __ldg(rv0 + b0 + 1);
-                const float r10 = __ldg(rv1 + b0), r11 = __ldg(rv1 + b0 + 1);
-                const float val = eq2_lerp(eq2_lerp(r00, r01, tb), eq2_lerp(r10, r11, tb), ta);
-                const float l2 = __fadd_rn(e2, z2[v]);
-                const float w = __fmul_rn(wc, __fmul_rn(l2, eq2_rsqrt(l2)));   // dsd^2 depth^-3 l
-                acc[v] = __fmaf_rn(w, val, acc[v]);
-            }
-        } else {
-#pragma unroll
-            for (int v = 0; v < VZ; ++v) {
-                const float fb = __fmaf_rn(z[v], sv, G.cv);
-                const float b0f = floorf(fb);
-                const float tb = __fsub_rn(fb, b0f);
-                const int b0 = (int)b0f;
-                const bool b0in = b0 >= 0 && b0 < G.nv, b1in = b0 + 1 >= 0 && b0 + 1 < G.nv;
-                // bilinear interpolation, zero outside the pixel grid
-                const float r00 = (a0in && b0in) ? __ldg(rv0 + b0) : 0.f;
-                const float r01 = (a0in && b1in) ? __ldg(rv0 + b0 + 1) : 0.f;
-                const float r10 = (a1in && b0in) ? __ldg(rv1 + b0) : 0.f;
-                const float r11 = (a1in && b1in) ? __ldg(rv1 + b0 + 1) : 0.f;
-                const float val = eq2_lerp(eq2_lerp(r00, r01, tb), eq2_lerp(r10, r11, tb), ta);
-                const float l2 = __fadd_rn(e2, z2[v]);
-                const float w = __fmul_rn(wc, __fmul_rn(l2, eq2_rsqrt(l2)));   // dsd^2 depth^-3 l
-                acc[v] = __fmaf_rn(w, val, acc[v]);
+    // The column quantities of a view are the same for every lane: lane l computes those
+    // of view vb + l for a group of 32 views (the same expressions), and the warp takes
+    // each view's in turn from its lane.  The fast-path test of a view (every tap of the
+    // column on the imager) needs only the column's lowest and highest voxel, since v*
+    // grows with z (sv > 0: the depth is positive).
+    const float zlo = __fmaf_rn((float)kz0 + 0.5f, G.hz, G.z0);
+    const float zhi = __fmaf_rn((float)(kz0 + 31 + 32 * (VZ - 1)) + 0.5f, G.hz, G.z0);
+    for (int vb = 0; vb < G.na; vb += 32) {
+        float g_ta = 0.f, g_sv = 0.f, g_wc = 0.f, g_e2 = 0.f;
+        int g_a0 = -2, g_in = 0;
+        if (vb + lane < G.na) {
+            const float2 cs = __ldg(G.view + vb + lane);  // cos, sin
+            // depth along the central ray, u* in pixels, and the column pair
+            const float depth = __fsub_rn(G.dso, __fmaf_rn(x, cs.x, __fmul_rn(y, cs.y)));
+            const float inv = eq2_rcp(depth);
+            const float us = __fmul_rn(__fmul_rn(G.dsd, __fmaf_rn(y, cs.x, -__fmul_rn(x, cs.y))), inv);
+            const float fa = __fmaf_rn(us, G.inv_du, G.cu);
+            const float a0f = floorf(fa);
+            g_ta = __fsub_rn(fa, a0f);
+            g_a0 = (int)a0f;
+            // v* = dsd z / depth in pixels; weight L^3 / (L0 l^2) = dsd^2 l / depth^3
+            g_sv = __fmul_rn(__fmul_rn(G.dsd, inv), G.inv_dv);
+            g_wc = __fmul_rn(dsd2, __fmul_rn(inv, __fmul_rn(inv, inv)));
+            const float ex = __fmaf_rn(-G.dso, cs.x, x), ey = __fmaf_rn(-G.dso, cs.y, y);
+            g_e2 = __fmaf_rn(ex, ex, __fmul_rn(ey, ey));
+            g_in = g_a0 >= 0 && g_a0 + 1 < G.nu && __fmaf_rn(zlo, g_sv, G.cv) >= 0.f &&
+                   __fmaf_rn(zhi, g_sv, G.cv) < (float)(G.nv - 1) && kz0 + 32 * VZ <= G.nz;
+        }
+        const int nview = min(32, G.na - vb);
+        for (int jv = 0; jv < nview; ++jv) {
+            const int ia = vb + jv;
+            const float ta = __shfl_sync(0xffffffffu, g_ta, jv);
+            const float sv = __shfl_sync(0xffffffffu, g_sv, jv);
+            const float wc = __shfl_sync(0xffffffffu, g_wc, jv);
+            const float e2 = __shfl_sync(0xffffffffu, g_e2, jv);
+            const int a0 = __shfl_sync(0xffffffffu, g_a0, jv);
+            const bool all_inside = __shfl_sync(0xffffffffu, g_in, jv) != 0;
+            const bool a0in = a0 >= 0 && a0 < G.nu, a1in = a0 + 1 >= 0 && a0 + 1 < G.nu;
+            const float *rv0 = r + (size_t)ia * plane + (size_t)(a0in ? a0 : 0) * G.nv;
+            const float *rv1 = r + (size_t)ia * plane + (size_t)(a1in ? a0 + 1 : 0) * G.nv;
+            if (all_inside) {
+    #pragma unroll
+                for (int v = 0; v < VZ; ++v) {
+                    const float fb = __fmaf_rn(z[v], sv, G.cv);
+                    const float b0f = floorf(fb);
+                    const float tb = __fsub_rn(fb, b0f);
+                    const int b0 = (int)b0f;
+                    const float r00 = __ldg(rv0 + b0), r01 = __ldg(rv0 + b0 + 1);
+                    const float r10 = __ldg(rv1 + b0), r11 = __ldg(rv1 + b0 + 1);
+                    const float val = eq2_lerp(eq2_lerp(r00, r01, tb), eq2_lerp(r10, r11, tb), ta);
+                    const float l2 = __fadd_rn(e2, z2[v]);
+                    const float w = __fmul_rn(wc, __fmul_rn(l2, eq2_rsqrt(l2)));   // dsd^2 depth^-3 l
+                    acc[v] = __fmaf_rn(w, val, acc[v]);
+                }
+            } else {
+    #pragma unroll
+                for (int v = 0; v < VZ; ++v) {
+                    const float fb = __fmaf_rn(z[v], sv, G.cv);
+                    const float b0f = floorf(fb);
+                    const float tb = __fsub_rn(fb, b0f);
+                    const int b0 = (int)b0f;
+                    const bool b0in = b0 >= 0 && b0 < G.nv, b1in = b0 + 1 >= 0 && b0 + 1 < G.nv;
+                    // bilinear interpolation, zero outside the pixel grid
+                    const float r00 = (a0in && b0in) ? __ldg(rv0 + b0) : 0.f;
+                    const float r01 = (a0in && b1in) ? __ldg(rv0 + b0 + 1) : 0.f;
+                    const float r10 = (a1in && b0in) ? __ldg(rv1 + b0) : 0.f;
+                    const float r11 = (a1in && b1in) ? __ldg(rv1 + b0 + 1) : 0.f;
+                    const float val = eq2_lerp(eq2_lerp(r00, r01, tb), eq2_lerp(r10, r11, tb), ta);
+                    const float l2 = __fadd_rn(e2, z2[v]);
+                    const float w = __fmul_rn(wc, __fmul_rn(l2, eq2_rsqrt(l2)));   // dsd^2 depth^-3 l
+                    acc[v] = __fmaf_rn(w, val, acc[v]);
+                }
             }
         }
     }
