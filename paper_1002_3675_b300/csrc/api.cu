@@ -234,7 +234,7 @@ cbct_status enqueue_iteration(cbct_geometry *G, Level *L, const SolveParams &P, 
     {
         Launch l(prof, CBCT_K_BACKPROJECT);
         if (eq2)
-            CK(launch_backproject_eq2(gd, L->rs, L->f, L->g, P.c_eq2, BP_STEP, s), "eq2 backprojection");
+            CK(launch_backproject_eq2(gd, L->rs, L->eq2p, L->f, L->g, P.c_eq2, BP_STEP, s), "eq2 backprojection");
         else
             CK(launch_backproject(gd, L->rs, L->f, L->g, P.c, BP_STEP, s), "backprojection");
     }
@@ -770,9 +770,11 @@ cbct_status cbct_backproject_eq2(cbct_geometry *G, const float *y_dev, float *f_
     Level *L;
     ST(ensure_level(G, 0, &L));
     ST(ensure_workspace(L, false));
+    ST(ensure_eq2_pad(L, s));
     const GeoDev &g = L->gd;
     CK(launch_sino_to_internal(y_dev, L->rs, nullptr, nullptr, g.na, g.nu, g.nv, s), "sinogram layout");
-    CK(launch_backproject_eq2(g, L->rs, nullptr, L->A, (float)eq2_scale(L), BP_PLAIN, s), "eq2 backprojection");
+    CK(launch_backproject_eq2(g, L->rs, L->eq2p, nullptr, L->A, (float)eq2_scale(L), BP_PLAIN, s),
+       "eq2 backprojection");
     CK(launch_vol_to_api(L->A, f_dev, g.nx, g.ny, g.nz, s), "volume layout");
     return CBCT_OK;
 }
@@ -947,6 +949,7 @@ cbct_status cbct_reconstruct(cbct_geometry *G, const float *Y_dev, const double 
     for (int l = 0; l < levels; ++l) {
         ST(ensure_level(G, l, &Ls[l]));
         ST(ensure_workspace(Ls[l], fp16));
+        if (o.adjoint_mode == 1) ST(ensure_eq2_pad(Ls[l], s));
     }
     double *dtrace;
     ST(get_trace(G, TRACE_W * (size_t)std::max(iters, 1), &dtrace));

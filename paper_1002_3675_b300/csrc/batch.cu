@@ -104,7 +104,7 @@ k_eq2_batch(const Eq2Item *__restrict__ items, const long *__restrict__ start, i
         const int r = find_item(start, n, t);
         copy_words(&it, items + r, sizeof(Eq2Item), threadIdx.x, blockDim.x);
         __syncthreads();
-        eq2_block(it.G, it.r, it.fin, it.out, it.cscale, it.mode, t - start[r]);
+        eq2_block(it.G, it.r, false, it.fin, it.out, it.cscale, it.mode, t - start[r]);
         __syncthreads();
     }
 }
@@ -805,7 +805,7 @@ static cbct_status launch_chain(const Engine::Chain &c, cudaStream_t s) {
                        nullptr),
         "projection");
     if (c.eq2)
-        ECK(launch_backproject_eq2(c.eq.G, c.eq.r, c.eq.fin, c.eq.out, c.eq.cscale, c.eq.mode, s), "eq2 backprojection");
+        ECK(launch_backproject_eq2(c.eq.G, c.eq.r, nullptr, c.eq.fin, c.eq.out, c.eq.cscale, c.eq.mode, s), "eq2 backprojection");
     else
         ECK(launch_backproject(c.bp.G, c.bp.rs, c.bp.fin, c.bp.out, c.bp.c, c.bp.mode, s), "backprojection");
     if (c.power) {  // the same partition and trees as the batched helpers
@@ -856,7 +856,7 @@ cbct_status Engine::launch_stages() {
     for (const BpItem &it : solo_bp)
         ECK(launch_backproject(it.G, it.rs, it.fin, it.out, it.c, it.mode, s), "backprojection");
     for (const Eq2Item &it : solo_eq)
-        ECK(launch_backproject_eq2(it.G, it.r, it.fin, it.out, it.cscale, it.mode, s), "eq2 backprojection");
+        ECK(launch_backproject_eq2(it.G, it.r, nullptr, it.fin, it.out, it.cscale, it.mode, s), "eq2 backprojection");
     for (int v = 0; v < 4; ++v)  // column running sums the batched gathers read
         for (const BpItem &it : hbp[v]) ECK(launch_row_prefix(it.G, it.rs, s), "row sums");
     for (int v = 0; v < 4; ++v) {

@@ -50,7 +50,14 @@ __device__ __forceinline__ float eq2_rsqrt(float x) {
 
 // The voxels k = kz0 + lane + 32 v (v < VZ) of column (i, j): acc[v] = (B r)_k without the
 // dV/(du dv) factor.
-template <int VZ>
+//
+// PAD: r is the residual with a zero border, [na][nu + 2][nv + 2] with pixel (a, b) at
+// (a + 1, b + 1) (eq2_pad), so that the taps of a voxel need no checks: its row index is
+// clamped to [-1, nv - 1] (a voxel below or above the imager reads any row pair and is
+// given the value 0), and a view whose column pair lies wholly off the imager is skipped
+// (its taps are all 0, and adding w * 0 to an accumulator that started at +0 changes no
+// bit).  The taps read are the same numbers, so the result is the same either way.
+template <int VZ, bool PAD>
 __device__ __forceinline__ void eq2_column(const GeoDev &G, const float *__restrict__ r, int i, int j, int kz0,
                                            float *acc) {
     const int lane = threadIdx.x & 31;
@@ -102,6 +109,27 @@ __device__ __forceinline__ void eq2_column(const GeoDev &G, const float *__restr
             const float e2 = __shfl_sync(0xffffffffu, g_e2, jv);
             const int a0 = __shfl_sync(0xffffffffu, g_a0, jv);
             const bool all_inside = __shfl_sync(0xffffffffu, g_in, jv) != 0;
+            if constexpr (PAD) {
+                if (a0 < -1 || a0 > G.nu - 1) continue;  // (warp-uniform)
+                const float *rv0 = r + ((size_t)ia * (G.nu + 2) + (a0 + 1)) * (G.nv + 2) + 1;
+                const float *rv1 = rv0 + (G.nv + 2);
+#pragma unroll
+                for (int v = 0; v < VZ; ++v) {
+                    const float fb = __fmaf_rn(z[v], sv, G.cv);
+                    const float b0f = floorf(fb);
+                    const float tb = __fsub_rn(fb, b0f);
+                    const int b0 = (int)b0f;
+                    const int bc = min(max(b0, -1), G.nv - 1);
+                    const float r00 = __ldg(rv0 + bc), r01 = __ldg(rv0 + bc + 1);
+                    const float r10 = __ldg(rv1 + bc), r11 = __ldg(rv1 + bc + 1);
+                    float val = eq2_lerp(eq2_lerp(r00, r01, tb), eq2_lerp(r10, r11, tb), ta);
+                    if (bc != b0) val = 0.f;
+                    const float l2 = __fadd_rn(e2, z2[v]);
+                    const float w = __fmul_rn(wc, __fmul_rn(l2, eq2_rsqrt(l2)));   // dsd^2 depth^-3 l
+                    acc[v] = __fmaf_rn(w, val, acc[v]);
+                }
+                continue;
+            }
             const bool a0in = a0 >= 0 && a0 < G.nu, a1in = a0 + 1 >= 0 && a0 + 1 < G.nu;
             const float *rv0 = r + (size_t)ia * plane + (size_t)(a0in ? a0 : 0) * G.nv;
             const float *rv1 = r + (size_t)ia * plane + (size_t)(a1in ? a0 + 1 : 0) * G.nv;
@@ -144,7 +172,8 @@ __device__ __forceinline__ void eq2_column(const GeoDev &G, const float *__restr
 
 // Block blk (EQ2_COLS z-columns, one per warp): out = cscale * B' r (plain) or
 // fin - cscale * B' r (step), B' being B without its dV/(du dv) factor.
-__device__ __forceinline__ void eq2_block(const GeoDev &G, const float *__restrict__ r,
+// pad: r is the zero-bordered residual (eq2_column's PAD form).
+__device__ __forceinline__ void eq2_block(const GeoDev &G, const float *__restrict__ r, bool pad,
                                           const float *__restrict__ fin, float *__restrict__ out, float cscale,
                                           int mode, long blk) {
     const long col = blk * EQ2_COLS + (threadIdx.x >> 5);
@@ -155,10 +184,17 @@ __device__ __forceinline__ void eq2_block(const GeoDev &G, const float *__restri
     for (int kz0 = 0; kz0 < G.nz; kz0 += 32 * EQ2_MAX_VZ) {
         const int vz = min(EQ2_MAX_VZ, (G.nz - kz0 + 31) / 32);
         float acc[EQ2_MAX_VZ] = {0.f, 0.f, 0.f, 0.f};
-        if (vz == 1) eq2_column<1>(G, r, i, j, kz0, acc);
-        else if (vz == 2) eq2_column<2>(G, r, i, j, kz0, acc);
-        else if (vz == 3) eq2_column<3>(G, r, i, j, kz0, acc);
-        else eq2_column<4>(G, r, i, j, kz0, acc);
+        if (pad) {
+            if (vz == 1) eq2_column<1, true>(G, r, i, j, kz0, acc);
+            else if (vz == 2) eq2_column<2, true>(G, r, i, j, kz0, acc);
+            else if (vz == 3) eq2_column<3, true>(G, r, i, j, kz0, acc);
+            else eq2_column<4, true>(G, r, i, j, kz0, acc);
+        } else {
+            if (vz == 1) eq2_column<1, false>(G, r, i, j, kz0, acc);
+            else if (vz == 2) eq2_column<2, false>(G, r, i, j, kz0, acc);
+            else if (vz == 3) eq2_column<3, false>(G, r, i, j, kz0, acc);
+            else eq2_column<4, false>(G, r, i, j, kz0, acc);
+        }
 #pragma unroll
         for (int v = 0; v < EQ2_MAX_VZ; ++v) {
             const int k = kz0 + lane + 32 * v;

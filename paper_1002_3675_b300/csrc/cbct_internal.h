@@ -91,6 +91,7 @@ struct Level {
     double lambda = 0.0;          // cached lambda_max(P^T P) (0 = unknown)
     int lambda_iters = 0;
     int tv_sweeps = 0, tv_warps = 0, tv_planes = 0;  // x-marching TV launch shape (0 = default)
+    float *eq2p = nullptr;        // zero-bordered residual for the Eq. 2 adjoint, [na][nu+2][nv+2]
     float *mg = nullptr;          // V-cycle volumes: linear term, restricted iterate, 2 scratch
     double *mg_partial = nullptr; // V-cycle dot-product partials
 };
@@ -133,6 +134,8 @@ cbct_status cuda_fail(cudaError_t e, const char *what);
 cbct_status ensure_level(cbct_geometry *G, int level, Level **out);
 cbct_status ensure_workspace(Level *L, bool need_half);
 cbct_status ensure_mg_workspace(Level *L);
+// L->eq2p for the Eq. 2 adjoint, its border zeroed on stream s at allocation
+cbct_status ensure_eq2_pad(Level *L, cudaStream_t s);
 void free_level(Level *L);
 
 // kernel launchers (return cudaError_t of the launch)
@@ -154,9 +157,11 @@ cudaError_t launch_row_prefix(const GeoDev &g, const float *rs, cudaStream_t s);
 int project_threads(const GeoDev &g);
 
 // Eq. 2 adjoint: out = cscale * B' r (BP_PLAIN) or fin - cscale * B' r (BP_STEP), where
-// B' is B without its dV/(du dv) factor and r = P f - Y unscaled.
-cudaError_t launch_backproject_eq2(const GeoDev &g, const float *r, const float *fin, float *out, float cscale,
-                                   int mode, cudaStream_t s);
+// B' is B without its dV/(du dv) factor and r = P f - Y unscaled.  padded (or null): a
+// zero-bordered [na][nu + 2][nv + 2] workspace (ensure_eq2_pad); r is copied into its
+// interior first and the gather reads its taps without bounds checks (the same result).
+cudaError_t launch_backproject_eq2(const GeoDev &g, const float *r, float *padded, const float *fin, float *out,
+                                   float cscale, int mode, cudaStream_t s);
 double eq2_scale(const Level *L);  // dV / (du dv)
 int bp_default_vpl(const GeoDev &g);
 // Whether the adjoint's lanes hold interleaved voxels (bp_tile.cuh) with vpl voxels per lane.

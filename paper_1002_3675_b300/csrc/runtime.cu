@@ -82,6 +82,7 @@ void free_level(Level *L) {
     cudaFree(L->partial);
     cudaFree(L->mg);
     cudaFree(L->mg_partial);
+    cudaFree(L->eq2p);
     delete L;
 }
 
@@ -211,6 +212,20 @@ cbct_status ensure_level(cbct_geometry *G, int level, Level **out) {
         G->levels[level] = L;
     }
     *out = G->levels[level];
+    return CBCT_OK;
+}
+
+cbct_status ensure_eq2_pad(Level *L, cudaStream_t s) {
+    if (L->eq2p) return CBCT_OK;
+    const size_t bytes = (size_t)L->na * (L->nu + 2) * (L->nv + 2) * sizeof(float);
+    const cbct_status st = dmalloc((void **)&L->eq2p, bytes, "Eq. 2 padded residual");
+    if (st != CBCT_OK) return st;
+    const cudaError_t e = cudaMemsetAsync(L->eq2p, 0, bytes, s);
+    if (e != cudaSuccess) {
+        cudaFree(L->eq2p);
+        L->eq2p = nullptr;
+        return cuda_fail(e, "zeroing the Eq. 2 padded residual");
+    }
     return CBCT_OK;
 }
 

@@ -66,7 +66,7 @@ bool same_geometry(const Slot &s, const cbct_geometry_desc &d, const std::vector
 }
 
 // Device bytes a geometry needs for `levels` levels (tables and workspaces).
-size_t geometry_bytes(const cbct_geometry_desc &d, int n_angles, int levels, bool fp16) {
+size_t geometry_bytes(const cbct_geometry_desc &d, int n_angles, int levels, bool fp16, bool eq2) {
     size_t total = 0;
     for (int l = 0; l < levels; ++l) {
         const int s = 1 << l;
@@ -76,6 +76,7 @@ size_t geometry_bytes(const cbct_geometry_desc &d, int n_angles, int levels, boo
         total += 4 * vol * 4 + sino * (4 + 4 + (fp16 ? 2 : 0));  // f, g, A, B; rs, Y, Yh
         total += (size_t)n_angles * nu * 24 + nu * nv * 24 + (size_t)n_angles * 8;  // ray tables
         total += (size_t)n_angles * nu * (nv + 1) * 8;                            // adjoint row sums
+        if (eq2) total += (size_t)n_angles * (nu + 2) * (nv + 2) * 4;              // Eq. 2 padded residual
         total += (sino / 32 + vol / 128 + 4096) * 8;                                             // partials
     }
     return total + (1 << 20);
@@ -153,7 +154,7 @@ bool cbct_server::try_admit(const std::shared_ptr<Pending> &p, std::unique_lock<
             slots[q].busy = true;
             return true;
         }
-    const size_t need = geometry_bytes(r.desc, r.n_angles, r.levels, r.opts.sino_fp16 != 0);
+    const size_t need = geometry_bytes(r.desc, r.n_angles, r.levels, r.opts.sino_fp16 != 0, r.opts.adjoint_mode == 1);
     if (need > budget) return false;  // rejected at submit; never admitted
     int free_slot = -1;
     for (size_t q = 0; q < slots.size(); ++q)
@@ -330,7 +331,8 @@ extern "C" cbct_status cbct_server_submit(cbct_server *S, const cbct_server_requ
     cbct_status st = validate_request(&probe, req->Y_dev, req->mu, req->iters, req->levels, &req->opts,
                                       req->f_out_dev);
     if (st != CBCT_OK) return st;
-    const size_t need = geometry_bytes(req->desc, req->n_angles, req->levels, req->opts.sino_fp16 != 0);
+    const size_t need =
+        geometry_bytes(req->desc, req->n_angles, req->levels, req->opts.sino_fp16 != 0, req->opts.adjoint_mode == 1);
     if (need > S->budget) {
         set_error("request needs about %zu bytes of device memory, above the server budget of %zu", need, S->budget);
         return CBCT_ERR_BUSY;
