@@ -103,6 +103,21 @@ def test_project_large_sampled_rays(lib):
     assert (y[:, 150:234, 200:312] > 0).all()
 
 
+def test_project_large_two_full_views(lib):
+    # every ray of two whole views (2 x 512 x 384) of the large workload, projected on the
+    # GPU with all 40 views and by the oracle with those two views alone
+    g = synth.geometry_for(synth.CONFIGS["large"])
+    rng = np.random.default_rng(27)
+    f = (rng.uniform(size=(96, 512, 512)) * 0.02).astype(np.float32)
+    G = lib.cbct_geometry_create(g)
+    y = host(lib.cbct_project(G, dev(f)))
+    views = [3, 26]   # 27 and 234 degrees: columns in every direction of the xy-grid
+    ref = oracle.project(dict(g, angles=g["angles"][views]), f.astype(np.float64))
+    got = y[views]
+    assert rel(got, ref) <= P_TOL, rel(got, ref)
+    assert np.abs(got - ref).max() <= P_TOL * np.abs(ref).max()
+
+
 def test_projection_split_over_level_launches_is_bitwise_identical(lib):
     """A projection run as consecutive launches over slabs of z-levels (the default for
     volumes larger than the L2 cache) equals the single launch bit for bit, in every
@@ -215,6 +230,31 @@ def test_backproject_large_sampled_voxels(lib):
         i, j, k = rng.integers(0, 512), rng.integers(0, 512), rng.integers(0, 96)
         ref = oracle.backproject_voxel(g, y64, int(i), int(j), int(k))
         assert abs(bt[k, j, i] - ref) <= P_TOL * scale, (i, j, k, bt[k, j, i], ref)
+
+
+def test_backproject_large_central_slab(lib):
+    # every voxel of the 4 central z-levels of 512x512x96 from the full large imager (40
+    # views of 512x384): a volume of nz = 4 has the same voxel centres as levels 46-49, and
+    # a voxel's adjoint value depends on that voxel's intersections alone.
+    # Gated on positive data.  Each float32 intersection length is a difference of plane
+    # crossings up to 181 mm from the ray's foot, so it carries an absolute error of a few
+    # 1e-5 mm (a few 1e-5 of a 0.5 mm chord), more for the nearly horizontal rays of the
+    # central levels, which graze the z-planes.  In a sum of positive terms these errors
+    # average out below the gate; zero-mean data (normal, printed) cancel the sum itself
+    # and leave them at about 1.5e-5 of its norm.  The largest single deviation, at voxels
+    # next to the z = 0 plane that the central rows' rays graze, is printed too.
+    g = synth.geometry_for(synth.CONFIGS["large"])
+    rng = np.random.default_rng(28)
+    G = lib.cbct_geometry_create(g)
+    slab = dict(g, nz=4)
+    y = rng.uniform(0.5, 1.5, size=(40, 384, 512)).astype(np.float32)
+    got = host(lib.cbct_backproject(G, dev(y)))[46:50]
+    ref = oracle.backproject(slab, y.astype(np.float64))
+    assert rel(got, ref) <= P_TOL, rel(got, ref)   # the adjoint's gate (relative L2)
+    print(f"large central slab: max |diff| / max |P^T y| = {np.abs(got - ref).max() / np.abs(ref).max():.1e}")
+    yn = rng.normal(size=(40, 384, 512)).astype(np.float32)
+    gn = host(lib.cbct_backproject(G, dev(yn)))[46:50]
+    print(f"large central slab, zero-mean data: rel L2 {rel(gn, oracle.backproject(slab, yn.astype(np.float64))):.2e}")
 
 
 def test_gpu_adjoint_identity(lib):
