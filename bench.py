@@ -80,7 +80,7 @@ CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.ac
 # length: 1 sub, accumulate: 1 fma, advance: 1 fma).  Neither kernel does per-nonzero
 # work (running slice integrals, a plane sweep over running sums), so both are
 # normalised rates, not floors of these kernels.
-OPS_PER_NNZ_SURVEY = 5.0
+OPS_PER_NNZ_PLAN = 5.0
 OPS_PER_NNZ = {"backproject": 8.0, "project": 4.0}
 # Sources of each timed kernel; the DRAM traffic recorded in profiles/ counts only while
 # they are unchanged since the capture.
@@ -447,7 +447,7 @@ def _gpu_line(args, cbct, torch, dev, G, case, cfg, Y, Y_host, f, f_host, res, w
             per_kernel[k]["note"] = "Eq. 2 adjoint in the FBS iterations: no nonzero-based rate"
             continue
         per_kernel[k]["gnnz_per_s"] = units_f[k] * args.steps / t / 1e9
-        per_kernel[k]["alu_tops_survey_basis"] = units_f[k] * args.steps * OPS_PER_NNZ_SURVEY / t / 1e12
+        per_kernel[k]["alu_tops_plan_basis"] = units_f[k] * args.steps * OPS_PER_NNZ_PLAN / t / 1e12
         per_kernel[k]["alu_tops_kernel_basis"] = units_f[k] * args.steps * OPS_PER_NNZ[k] / t / 1e12
         pf = profile_fields(k, args.workload)
         if "l2_bytes_per_launch" in pf:
@@ -468,16 +468,16 @@ def _gpu_line(args, cbct, torch, dev, G, case, cfg, Y, Y_host, f, f_host, res, w
               "Algorithm A1 iterations, which run with nothing beside them")
     if dom in ("project", "backproject"):
         pk = per_kernel[dom]
-        ach = pk["alu_tops_survey_basis"]
+        ach = pk["alu_tops_plan_basis"]
         pf = profile_fields(dom, args.workload)
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tlane-op/s",
                 "frac": ach / alu_peak, "traffic": pf.get("traffic_bytes_per_launch"),
                 "launch_ms": pk["ms_per_operation"], "timing": timing,
-                "basis": f"{OPS_PER_NNZ_SURVEY:.0f} lane-ops per nonzero (the measurement plan's floor) x the "
+                "basis": f"{OPS_PER_NNZ_PLAN:.0f} lane-ops per nonzero (the measurement plan's floor) x the "
                          f"finest level's exact nnz ({nnz[0]}) per operation; peak = {sm_count} SMs x 128 FP32 "
                          f"lanes x {clock_mhz:.0f} MHz (median SM clock in the timed region). Normalised rate: "
                          "the kernel does no per-nonzero work",
-                "basis_survey": {"ops_per_nnz": OPS_PER_NNZ_SURVEY, "frac": ach / alu_peak},
+                "basis_survey": {"ops_per_nnz": OPS_PER_NNZ_PLAN, "frac": ach / alu_peak},
                 "basis_kernel": {"ops_per_nnz": OPS_PER_NNZ[dom],
                                  "frac": pk["alu_tops_kernel_basis"] / alu_peak},
                 "l2_gbs": pk.get("l2_gbs"), "issue_active_pct": pk.get("issue_active_pct"),
@@ -508,8 +508,8 @@ def _gpu_line(args, cbct, torch, dev, G, case, cfg, Y, Y_host, f, f_host, res, w
     b_pow = sum(8 * v + 8 * r for v, r in zip(nv_l, nr_l)) * K_pi
     bw = peaks["hbm_gbs"] * 1e9
     t_step = tot_ms / args.steps / 1e3
-    floor_s = {"project": units["project"] * OPS_PER_NNZ_SURVEY / (alu_peak * 1e12),
-               "backproject": units["backproject"] * OPS_PER_NNZ_SURVEY / (alu_peak * 1e12),
+    floor_s = {"project": units["project"] * OPS_PER_NNZ_PLAN / (alu_peak * 1e12),
+               "backproject": units["backproject"] * OPS_PER_NNZ_PLAN / (alu_peak * 1e12),
                "tv": sum(12.0 * v for v in nv_l) * iters / bw}
     per_iter = {"hbm_bytes_per_fbs_iteration_finest": 24 * nv_l[0] + (8 + s_bytes) * nr_l[0],
                 "literal_hbm_frac": (b_fbs + b_pow) / (t_step * bw),
